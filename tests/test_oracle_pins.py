@@ -1,0 +1,410 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix
+(no GPU). Each test names the passage or closed form it follows."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.order_conditions import max_violation
+
+
+# --------------------------------------------------------------------------
+# transforms: brute-force DFT of the definition y^(k) = 1/N sum y(r) e^{-ik.r}
+# --------------------------------------------------------------------------
+def _dft_half(x):
+    nz, ny, nx = x.shape
+    out = np.zeros((nz, ny, nx // 2 + 1), dtype=complex)
+    z, y, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for a in range(nz):
+        for b in range(ny):
+            for c in range(nx // 2 + 1):
+                ph = np.exp(-2j * np.pi * (a * z / nz + b * y / ny + c * xx / nx))
+                out[a, b, c] = np.sum(x * ph) / x.size
+    return out
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 10, 12), (4, 6, 10)])
+def test_transform_matches_bruteforce_dft(shape, params):
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(shape)
+    m = oracle.Model(shape, params)
+    ref = _dft_half(x)
+    got = m.to_k(x[None])[0]
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref)) * 10
+    back = m.to_r(got[None])[0]
+    assert np.max(np.abs(back - x)) <= 1e-13
+
+
+def test_wavenumbers_definition():
+    d = 0.5
+    k = oracle.wavenumbers(8, d, False)
+    assert np.allclose(k, 2 * np.pi / (8 * d) * np.array([0, 1, 2, 3, 4, -3, -2, -1]))
+    kh = oracle.wavenumbers(8, d, True)
+    assert np.allclose(kh, 2 * np.pi / (8 * d) * np.arange(5))
+    assert k[4] == pytest.approx(math.pi / d)  # Nyquist taken as +pi/dx
+
+
+# --------------------------------------------------------------------------
+# ARK tables (Sec. 4.4): order conditions from two-colour rooted trees
+# --------------------------------------------------------------------------
+def test_ark4_order_conditions():
+    t = oracle.ark436l2sa()
+    assert max_violation(t.AE, t.AI, t.bE, t.bI, 4) < 1e-14
+    assert max_violation(t.AE, t.AI, t.btE, t.btI, 3) < 1e-14
+    # the embedding is genuinely of lower order
+    assert max_violation(t.AE, t.AI, t.btE, t.btI, 4) > 1e-6
+    # structure: explicit part strictly lower triangular, ESDIRK gamma = 1/4,
+    # explicit first stage, equal abscissae, stiffly accurate implicit part
+    assert np.all(np.triu(t.AE) == 0.0)
+    assert t.AI[0, 0] == 0.0 and np.all(np.diag(t.AI)[1:] == 0.25)
+    assert np.allclose(t.cE, t.cI, atol=1e-15)
+    assert np.allclose(t.bI, t.AI[-1], atol=0)
+
+
+def test_euler_table_is_first_order_only():
+    t = oracle.euler()
+    assert max_violation(t.AE, t.AI, t.bE, t.bI, 1) < 1e-15
+    assert max_violation(t.AE, t.AI, t.bE, t.bI, 2) > 0.1
+
+
+# --------------------------------------------------------------------------
+# linear stability of a small single Fourier mode about the uniform state
+# (stiff/non-stiff split of Eqs. composition and order)
+# --------------------------------------------------------------------------
+def _R(tab, zI, zE):
+    """Scalar-test-equation amplification written from the Butcher arrays:
+    R = 1 + (zI bI + zE bE)^T (I - zI AI - zE AE)^{-1} 1."""
+    s = tab.s
+    M = np.eye(s) - zI * tab.AI - zE * tab.AE
+    return 1.0 + (zI * tab.bI + zE * tab.bE) @ np.linalg.solve(M, np.ones(s))
+
+
+@pytest.mark.parametrize("meth", ["euler", "ark4"])
+@pytest.mark.parametrize("mode", [(1, 0, 0), (2, 3, 1), (4, 4, 4)])
+def test_single_mode_amplification(meth, mode, params):
+    shape = (8, 8, 8)
+    p = params
+    m = oracle.Model(shape, p)
+    tab = oracle.TABLES[meth]()
+    dt = 0.4
+    kx = 2 * np.pi * mode[0] / (8 * p["dx"])
+    ky = 2 * np.pi * mode[1] / (8 * p["dx"])
+    kz = 2 * np.pi * mode[2] / (8 * p["dx"])
+    k2 = kx * kx + ky * ky + kz * kz
+    D = 2 * p["A_m"] * m.M
+    # composition mode: linear exactly, no explicit part about phi = 0
+    y0 = synth.ic_mode(shape, p, 0, mode, 1e-3)
+    y1, _, _ = oracle.ark_step(m, m.to_k(y0), dt, tab)
+    amp = (m.to_r(y1)[0] - p["X_matrix"]) / (y0[0] - p["X_matrix"] + 1e-300)
+    idx = np.unravel_index(np.argmax(np.abs(y0[0] - p["X_matrix"])), shape)
+    assert amp[idx] == pytest.approx(_R(tab, -dt * D * k2, 0.0), rel=1e-10)
+    # order-parameter mode: stiff gradient term implicit, double-well slope
+    # 2 omega_bar explicit
+    y0 = synth.ic_mode(shape, p, 1, mode, 1e-8)
+    y1, _, _ = oracle.ark_step(m, m.to_k(y0), dt, tab)
+    r1 = m.to_r(y1)[1]
+    want = _R(tab, -dt * p["L"] * p["kappa_iso"] * k2, -dt * 2 * p["L"] * p["omega_bar"])
+    assert r1[idx] / y0[1][idx] == pytest.approx(want, rel=1e-6)
+
+
+def test_dispersion_continuum_limit(params):
+    """For dt -> 0 the Euler amplification per unit time approaches the
+    continuous growth rates -D k^2 (X) and -L (kappa k^2 + 2 omega_bar) (phi)."""
+    shape = (8, 8, 8)
+    m = oracle.Model(shape, params)
+    tab = oracle.euler()
+    dt = 1e-4
+    k2 = (2 * np.pi * 2 / (8 * params["dx"])) ** 2
+    y0 = synth.ic_mode(shape, params, 1, (2, 0, 0), 1e-8)
+    y1, _, _ = oracle.ark_step(m, m.to_k(y0), dt, tab)
+    rate = math.log(m.to_r(y1)[1][0, 0, 0] / y0[1][0, 0, 0]) / dt
+    want = -params["L"] * (params["kappa_iso"] * k2 + 2 * params["omega_bar"])
+    assert rate == pytest.approx(want, rel=1e-3)
+
+
+# --------------------------------------------------------------------------
+# elastic kernel (Eq. u_gov, homogeneous modulus)
+# --------------------------------------------------------------------------
+def test_elastic_isotropic_dilatation_closed_form():
+    C44 = 80.0
+    C12 = 120.0
+    C11 = C12 + 2 * C44  # isotropic
+    e0 = 0.01
+    p = dict(C11=C11, C12=C12, C44=C44, eps_star=[[e0, e0, e0, 0, 0, 0]] * 3)
+    rng = np.random.default_rng(3)
+    k = rng.standard_normal((3, 5, 4, 3))
+    B = oracle.elastic_B((k[0], k[1], k[2]), p)
+    lam, mu = C12, C44
+    K = lam + 2 * mu / 3
+    want = 12 * K * mu * e0 ** 2 / (lam + 2 * mu)
+    assert np.allclose(B, want, rtol=1e-13)
+
+
+def _plane_wave_energy(kdir, eps, C):
+    """Mean elastic energy density of h = cos(k.r) with eigenstrain eps h and
+    the displacement u = w sin(k.r) that minimises it (mechanical
+    equilibrium): 1/4 (S - eps):C:(S - eps) with S = sym(w (x) k)."""
+    k = np.asarray(kdir, float)
+    K = np.zeros((3, 3))
+    rhs = np.zeros(3)
+    for i in range(3):
+        for kk in range(3):
+            K[i, kk] = sum(C[i, j, kk, l] * k[j] * k[l] for j in range(3) for l in range(3))
+        rhs[i] = sum(C[i, j, kk, l] * eps[kk, l] * k[j] for j in range(3) for kk in range(3) for l in range(3))
+    w = np.linalg.solve(K, rhs)
+    S = 0.5 * (np.outer(w, k) + np.outer(k, w))
+    D = S - eps
+    return 0.25 * np.einsum("ij,ijkl,kl->", D, C, D)
+
+
+def test_elastic_cubic_kernel_equals_equilibrium_energy(params):
+    p = params
+    C = oracle.cubic_stiffness(p["C11"], p["C12"], p["C44"])
+    eps = [oracle.voigt_to_tensor(e) for e in p["eps_star"]]
+    rng = np.random.default_rng(11)
+    for _ in range(6):
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        B = oracle.elastic_B((np.array([[[n[0]]]]), np.array([[[n[1]]]]), np.array([[[n[2]]]])), p)[..., 0, 0, 0]
+        for v in range(3):
+            assert B[v, v] == pytest.approx(4 * _plane_wave_energy(n, eps[v], C), rel=1e-12)
+            for q in range(v + 1, 3):
+                both = 4 * _plane_wave_energy(n, eps[v] + eps[q], C)
+                assert B[v, v] + 2 * B[v, q] + B[q, q] == pytest.approx(both, rel=1e-12)
+    # B(0) = 0 (stress-free mean strain)
+    z = np.zeros((1, 1, 1))
+    assert np.all(oracle.elastic_B((z, z, z), p) == 0.0)
+
+
+# --------------------------------------------------------------------------
+# free energy closed forms (Sec. 4.1)
+# --------------------------------------------------------------------------
+def test_free_energy_uniform_states(params):
+    p = params
+    shape = (4, 4, 6)
+    m = oracle.Model(shape, p)
+    V = np.prod(shape) * p["dx"] ** 3
+    y = np.zeros((4,) + shape)
+    y[0] = 0.07
+    assert m.free_energy(m.to_k(y)) == pytest.approx(V * p["A_m"] * (0.07 - p["B_m0"]) ** 2, rel=1e-12)
+    # uniform order parameters: double well + pairwise barrier + KKS mixture
+    a, b = 0.3, 0.6
+    y[1], y[2] = a, b
+    h = oracle.h_interp
+    H = h(a) + h(b)
+    A = p["A_m"]
+    mu = (0.07 - H * p["B_v"] - (1 - H) * p["B_m0"]) * 2 * A  # equal curvatures
+    fch = H * A * (mu / (2 * A)) ** 2 + (1 - H) * A * (mu / (2 * A)) ** 2
+    fb = p["omega_bar"] * (a * a * (1 - a) ** 2 + b * b * (1 - b) ** 2) + p["omega_pair"][0] * a * b
+    # uniform h has only a DC mode, where B = 0
+    assert m.free_energy(m.to_k(y)) == pytest.approx(V * (fch + fb), rel=1e-12)
+
+
+def _slab(p, nx=384, dx=0.125):
+    q = dict(p, dx=dx, eps_c=0.0, eps_a=0.0)
+    q = synth.load_params(**{k: v for k, v in q.items() if k not in ("kappa", "eps_star", "omega_pair")})
+    # X = B_m + h(phi)(B_v - B_m) makes the KKS chemical potential vanish
+    # for equal curvatures, so the double well alone shapes the profile
+    y = synth.ic_slab(nx, 4, 4, q, 12.0, 36.0,
+                      lambda ph: q["B_m0"] + oracle.h_interp(ph) * (q["B_v"] - q["B_m0"]))
+    return q, y
+
+
+def test_free_energy_of_equilibrium_slab(params):
+    """Two planar interfaces: F = 2 sigma A, sigma = sqrt(2 kappa omega_bar)/6
+    for the double well with gradient coefficient kappa/2."""
+    q, y = _slab(params)
+    m = oracle.Model(y.shape[1:], q)
+    A = 4 * 4 * q["dx"] ** 2
+    sigma = math.sqrt(2 * q["kappa_iso"] * q["omega_bar"]) / 6.0
+    assert m.free_energy(m.to_k(y)) == pytest.approx(2 * sigma * A, rel=1e-9)
+
+
+def test_equilibrium_slab_is_stationary(params):
+    """The tanh profile with mu = 0 is an equilibrium: the full right-hand
+    side vanishes to within the interaction of the two interfaces
+    (~exp(-d / (sqrt(2) l)) = exp(-24) for d = 24 nm), and 100 ARK4 steps keep
+    the profile."""
+    q, y = _slab(params)
+    m = oracle.Model(y.shape[1:], q)
+    yh = m.to_k(y)
+    f = m.rhs_explicit(yh) + m.rhs_implicit(yh)
+    assert np.max(np.abs(m.to_r(f))) < 1e-10 * max(1.0, 1e11 * math.exp(-24.0))
+    tab = oracle.ark436l2sa()
+    for _ in range(100):
+        yh, _, _ = oracle.ark_step(m, yh, 1.0, tab)
+    assert np.max(np.abs(m.to_r(yh) - y)) < 1e-8
+
+
+# --------------------------------------------------------------------------
+# variational structure: the right-hand side is -L dF/dphi and div(M grad dF/dX)
+# --------------------------------------------------------------------------
+def test_rhs_is_variational_derivative_of_free_energy(params):
+    p = params
+    shape = (8, 8, 8)
+    rng = np.random.default_rng(5)
+    y = np.empty((4,) + shape)
+    y[0] = 0.06 + 0.01 * rng.standard_normal(shape)
+    y[1:] = rng.uniform(0.05, 0.95, size=(3,) + shape)
+    m = oracle.Model(shape, p)
+    yh = m.to_k(y)
+    tot = m.to_r(m.rhs_explicit(yh) + m.rhs_implicit(yh))
+    dV = p["dx"] ** 3
+    eps = 1e-6
+
+    def dF(field, idx):
+        yp = y.copy()
+        yp[(field,) + idx] += eps
+        ym = y.copy()
+        ym[(field,) + idx] -= eps
+        return (m.free_energy(m.to_k(yp)) - m.free_energy(m.to_k(ym))) / (2 * eps * dV)
+
+    for idx in [(0, 0, 0), (3, 5, 2), (7, 1, 6)]:
+        for v in range(3):
+            assert tot[1 + v][idx] == pytest.approx(-p["L"] * dF(1 + v, idx), rel=2e-6, abs=1e-9)
+    # composition: dX/dt = -M k^2 mu^ ; recover mu differences from the RHS
+    k2 = m.k2.copy()
+    k2[0, 0, 0] = 1.0
+    muh = -m.to_k(tot[0:1])[0] / (m.M * k2)
+    muh[0, 0, 0] = 0.0
+    mu = m.to_r(muh[None])[0]
+    a, b = (1, 2, 3), (6, 0, 4)
+    assert mu[a] - mu[b] == pytest.approx(dF(0, a) - dF(0, b), rel=2e-6)
+
+
+# --------------------------------------------------------------------------
+# conservation and dissipation
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("meth", ["euler", "ark4"])
+def test_composition_mean_conserved_bitwise(meth, params):
+    y = synth.ic_config1(16, 1, params, count=2)
+    m = oracle.Model(y.shape[1:], params)
+    yh = m.to_k(y)
+    dc = yh[0, 0, 0, 0]
+    tab = oracle.TABLES[meth]()
+    for _ in range(5):
+        yh, _, _ = oracle.ark_step(m, yh, 0.25, tab)
+        assert yh[0, 0, 0, 0] == dc
+
+
+def test_free_energy_decreases_first_order(params):
+    y = synth.ic_config1(32, 1, params)
+    m = oracle.Model(y.shape[1:], params)
+    yh = m.to_k(y)
+    F = m.free_energy(yh)
+    tab = oracle.euler()
+    for _ in range(50):
+        yh, _, _ = oracle.ark_step(m, yh, 0.05, tab)
+        F2 = m.free_energy(yh)
+        assert F2 <= F
+        F = F2
+
+
+def test_manual_chen_shen_equals_ark_euler(params):
+    """Sec. 2.3: the hand-written first-order scheme and the ARK form of ImEx
+    Euler give the same solution to rounding."""
+    y = synth.ic_config1(16, 1, params, count=2)
+    m = oracle.Model(y.shape[1:], params)
+    a = b = m.to_k(y)
+    for _ in range(10):
+        a, _, _ = oracle.ark_step(m, a, 0.25, oracle.euler())
+        b = oracle.chen_shen_euler(m, b, 0.25)
+    assert np.max(np.abs(a - b)) <= 1e-15 * np.max(np.abs(b))
+
+
+# --------------------------------------------------------------------------
+# WRMS norm and controller (Eqs. wrms_norm, wrms_weights)
+# --------------------------------------------------------------------------
+def test_wrms_definition():
+    v = np.array([1e-5, -2e-5, 0.0, 3e-5])
+    y = np.array([1.0, 0.5, 0.0, -2.0])
+    w = [1 / (1e-4 * abs(a) + 1e-8) for a in y]
+    want = math.sqrt(sum((a * b) ** 2 for a, b in zip(v, w)) / 4)
+    assert oracle.wrms(v, y, 1e-4, 1e-8) == pytest.approx(want, rel=1e-15)
+
+
+class _Scalar:
+    """y' = -y + y^2 split as f^I = -y, f^E = y^2; exact solution
+    y(t) = 1 / (1 + (1/y0 - 1) e^t)."""
+    lam = np.array([-1.0])
+
+    def rhs_explicit(self, y):
+        return y * y
+
+    def rhs_implicit(self, y):
+        return self.lam * y
+
+    def solve_implicit(self, g, r):
+        return r / (1.0 - g * self.lam)
+
+    def to_r(self, y):
+        return y
+
+
+@pytest.mark.parametrize("rtol", [1e-4, 1e-6])
+def test_adaptive_controller_scalar(rtol, params):
+    y0 = 0.5
+    tab = oracle.ark436l2sa()
+    y, t, log = oracle.advance(_Scalar(), np.array([y0]), 0.0, 6.0, tab, params, rtol, 1e-12, h0=0.01)
+    exact = 1.0 / (1.0 + (1.0 / y0 - 1.0) * math.exp(6.0))
+    assert t == pytest.approx(6.0, rel=1e-14)
+    assert abs(y[0] - exact) < 50 * rtol * abs(exact)
+    hs = [h for _, h, _, ok in log if ok]
+    assert max(hs) > 10 * 0.01  # the controller grew the step
+    for (t0, h, e, ok) in log:
+        assert ok == (e <= 1.0)
+
+
+def test_controller_formula(params):
+    c = oracle.Controller(params, 4)
+    h = c.accept(1.0, 0.5)
+    assert h == pytest.approx(min(params["eta_max"], params["safety"] * 0.5 ** (-params["k1"] / 4)))
+    h2 = c.reject(1.0, 16.0)
+    assert h2 == pytest.approx(max(params["eta_reject_min"], params["safety"] * 16.0 ** (-0.25)))
+    assert c.accept(1.0, 1e-12) == pytest.approx(1.0)  # growth capped at 1 after a rejection
+
+
+# --------------------------------------------------------------------------
+# temporal order (Sec. 2.3, Fig. 4a): first order for ImEx Euler, fourth order
+# for ARK4(3)6L[2]SA, measured on a smooth, non-stiff nonlinear state (coarse
+# 16^3 grid, dx = 2 nm, |phi_v phi_q| barrier off because |.| is not smooth
+# at phi = 0 and lowers the observed order)
+# --------------------------------------------------------------------------
+def _smooth_state(n=16, seed=3):
+    rng = np.random.default_rng(seed)
+    z, yy, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    y0 = np.zeros((4, n, n, n))
+    for f in range(4):
+        acc = np.zeros((n, n, n))
+        for _ in range(4):
+            mv = rng.integers(-2, 3, size=3)
+            ph = rng.uniform(0, 2 * np.pi)
+            acc += np.cos(2 * np.pi * (mv[0] * x + mv[1] * yy + mv[2] * z) / n + ph)
+        y0[f] = (0.1 + 0.02 * acc) if f == 0 else (0.5 + 0.1 * acc)
+    return y0
+
+
+def _run(m, yh, tab, dt, T):
+    for _ in range(int(round(T / dt))):
+        yh, _, _ = oracle.ark_step(m, yh, dt, tab, want_lte=False)
+    return m.to_r(yh)
+
+
+def test_temporal_order_euler_and_ark4():
+    p = synth.load_params(dx=2.0, omega_vq=0.0)
+    y0 = _smooth_state()
+    m = oracle.Model(y0.shape[1:], p)
+    yh0 = m.to_k(y0)
+    T = 8.0
+    ref = _run(m, yh0, oracle.ark436l2sa(), 1.0 / 32, T)
+
+    def slopes(tab, dts):
+        e = [np.sqrt(np.mean((_run(m, yh0, tab, dt, T) - ref) ** 2)) for dt in dts]
+        return [math.log(e[i] / e[i + 1]) / math.log(dts[i] / dts[i + 1]) for i in range(len(dts) - 1)]
+
+    for s in slopes(oracle.euler(), [0.5, 0.25, 0.125]):
+        assert 0.9 <= s <= 1.1
+    for s in slopes(oracle.ark436l2sa(), [1.0, 0.5, 0.25]):
+        assert s >= 3.5
