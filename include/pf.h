@@ -1,0 +1,201 @@
+/*
+ * pf.h -- C ABI of the GB300 pseudospectral ImEx-ARK phase-field hot path.
+ *
+ * The model is the KKS gamma'' precipitation model of the paper (Sec. 4.1):
+ * one conserved composition field X (Nb) and three non-conserved order
+ * parameters phi_1..3 (the gamma'' orientation variants), free energy
+ * F = int (f_b + f_el + f_ch) dV.  The state is integrated in reciprocal space
+ * (Sec. 4.2) with ImEx additive Runge-Kutta methods (Sec. 4.4, Eqs. imex_ode,
+ * ARK_method, ARK_embedding): the stiff linear terms of Eqs. composition and
+ * order are implicit, the rest explicit, and each implicit stage solve is a
+ * diagonal divide in k-space.
+ *
+ * Layouts (all row-major, x fastest):
+ *   real fields     double [4][nz][ny][nx]            field order X, phi_1, phi_2, phi_3
+ *   k-space vectors double complex [4][nz][ny][nx/2+1] (interleaved re, im)
+ *                   y^(k) = (1/N) sum_r y(r) exp(-i k.r), so the DC entry is
+ *                   the field mean; kx = 0..nx/2, ky/kz in FFT order.
+ *
+ * Errors: every int-returning call returns PF_OK (0) or a negative PF_E*
+ * code; pf_last_error() describes the last failure of a context.  A failed
+ * step leaves the last accepted state intact.  Non-CUDA errors leave the
+ * context usable.
+ *
+ * Ownership: a context owns every device buffer it allocates and frees them in
+ * pf_destroy.  Caller buffers are only read or written during a call.  All
+ * device work of a context is ordered on the CUDA stream given to pf_create.
+ */
+#ifndef PF_H
+#define PF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF_OK 0
+#define PF_EINVAL (-1)       /* bad argument (size, pointer, parameter)            */
+#define PF_ENOMEM (-2)       /* device or host allocation failed                   */
+#define PF_ECUDA (-3)        /* a CUDA runtime call failed                          */
+#define PF_ENONFINITE (-4)   /* NaN/Inf in the state or error estimate              */
+#define PF_ESTEPFAIL (-5)    /* step size fell below h_min or too many rejections  */
+#define PF_ETIMEOUT (-6)     /* a bounded device wait ran out                       */
+#define PF_EUNSUPPORTED (-7) /* grid size not 2,3,5-smooth/even, or method unknown */
+
+/* time integration methods (Sec. 4.4) */
+#define PF_EULER 1 /* ImEx (forward-backward) Euler, 1 RHS per step, no embedding */
+#define PF_ARK4 4  /* ARK4(3)6L[2]SA of Kennedy & Carpenter, 6 RHS per step, 3rd-order embedding */
+
+/* arithmetic of the transforms and right-hand side */
+#define PF_FP64 0     /* everything in FP64 */
+#define PF_FP32BULK 1 /* FFTs and nonlinear RHS in FP32; state, stage vectors,
+                         stage combinations, composition mean, WRMS norm and
+                         controller in FP64 */
+
+typedef struct pf_ctx pf_ctx;
+
+/* Periodic grid: each n even, 2,3,5-smooth, 4 <= n <= 1024; spacing in nm. */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+} pf_grid;
+
+/* Model constants (units nm, s, GPa, K) and integrator settings.
+ * Tensors use Voigt order (xx, yy, zz, yz, xz, xy) with tensor (not
+ * engineering) shear components. */
+typedef struct {
+    /* parabolic single-phase chemical free energies f^p = A0^p + A^p (X^p - B^p)^2
+       (Eq. f_ch_p read as parabolic) */
+    double A_m, A_v, A0_m, A0_v;
+    double B_m0, B_v, dBm_dT; /* B^m(T) = B_m0 + dBm_dT (T - T0) */
+    /* mobilities: M(T) = M0 exp(-Q/R (1/T - 1/T0)) (Eq. x_gov), L (Eq. phi_gov) */
+    double M0, Q_act, T, T0, L;
+    /* barrier terms of Eq. f_b */
+    double kappa[3][6];  /* gradient-energy tensor per variant [GPa nm^2] */
+    double omega_bar;    /* double-well height: omega_bar sum_v phi_v^2 (1-phi_v)^2 */
+    double omega_pair[3]; /* omega_12, omega_13, omega_23 of |phi_v phi_q| */
+    double pair_eps;      /* |x| of omega_vq |phi_v phi_q| is Huber-regularised with this
+                             width: d/dphi_v = omega_vq clip(phi_v phi_q / pair_eps, -1, 1) phi_q */
+    /* elasticity (Eq. u_gov, homogeneous cubic modulus) */
+    double C11, C12, C44;
+    double eps_star[3][6]; /* eigenstrain per variant */
+    /* integrator */
+    int method;    /* PF_EULER or PF_ARK4 */
+    int precision; /* PF_FP64 or PF_FP32BULK */
+    double rtol, atol; /* WRMS weights w = 1/(rtol |y| + atol) (Eq. wrms_weights) */
+    /* PI step-size controller (the paper uses ARKODE's; these constants are
+       proposed): h_new = h min(eta_max, max(eta_min, safety e^{-k1/q} e_prev^{k2/q})),
+       q = embedded order + 1; after a rejection h *= max(eta_reject_min,
+       safety e^{-1/q}) and the next growth is capped at 1. */
+    double h0, h_min, h_max;
+    int max_rejects;
+    double safety, k1, k2, eta_max, eta_min, eta_reject_min;
+} pf_params;
+
+typedef struct {
+    long long steps_accepted, steps_rejected;
+    long long rhs_evals;   /* explicit RHS evaluations (including rejected attempts) */
+    double t, h;           /* current time and next step size */
+    double last_wrms;      /* ||LTE||_WRMS of the last attempt */
+    double wall_s;         /* wall time inside pf_advance / pf_batch_advance */
+    long long point_stages; /* grid points x RHS evaluations */
+} pf_stats;
+
+/* Create a context on `cuda_stream` (a cudaStream_t, NULL = legacy default
+ * stream).  Validates sizes and parameters, allocates all device buffers,
+ * builds FFT plans and twiddle tables (FP64, computed on the host).
+ * Returns PF_EUNSUPPORTED for non-smooth/odd sizes. */
+int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, pf_ctx** out);
+void pf_destroy(pf_ctx* ctx);
+
+/* Set the state from real-space fields (layout above); `on_device` says
+ * whether `fields` is a device pointer.  Forward FFT in FP64, y = FFT/N. */
+int pf_set_state(pf_ctx* ctx, const double* fields, int on_device);
+/* Copy the real-space state out (inverse FFT in FP64). Caller owns `fields`. */
+int pf_get_state(pf_ctx* ctx, double* fields, int on_device);
+/* Copy the k-space state vector y (layout above) in or out. */
+int pf_set_state_hat(pf_ctx* ctx, const void* y_hat, int on_device);
+int pf_get_state_hat(pf_ctx* ctx, void* y_hat, int on_device);
+
+/* f^E(y): the explicit (non-stiff) right-hand side of Eqs. composition and
+ * order for a device k-space vector `y_hat`, written to device `fE_hat`
+ * (both complex128 ABI layout; may not alias).  Computed in the context's
+ * precision:
+ *   fE_X  = -M k^2 FT[mu - 2 A^m X]
+ *   fE_phi_v = -L FT[dfb/dphi_v + h'(phi_v)(f^v - f^m - mu (X^v - X^m)) + h'(phi_v) e_v]
+ * with e_v = IFFT[sum_q B_vq(k/|k|) FT[h(phi_q)]], B(0) = 0 (Sec. 4.1). */
+int pf_rhs_explicit(pf_ctx* ctx, const void* y_hat, void* fE_hat);
+
+/* Stage linear solve (Sec. 4.4, the SUNLinearSolver role): z = r / (1 - gamma
+ * lambda(k)) with lambda_X = -2 A^m M k^2, lambda_phi_v = -L k.kappa_v.k.
+ * Device complex128 vectors in ABI layout; r and z may alias. FP64. */
+int pf_solve_implicit(pf_ctx* ctx, double gamma, const void* r_hat, void* z_hat);
+
+/* One fixed step of size dt from the current state (always accepted).  If the
+ * method has an embedding and `lte_wrms_out` is non-NULL, the WRMS norm of
+ * the local error estimate (real space, all four fields, weights from the
+ * previous solution) is written there; else 0. */
+int pf_step(pf_ctx* ctx, double dt, double* lte_wrms_out);
+
+/* Adaptive integration to t_final (accept if ||LTE||_WRMS <= 1, PI
+ * controller).  Methods without an embedding take fixed steps of h0.
+ * `out` may be NULL. */
+int pf_advance(pf_ctx* ctx, double t_final, double rtol, double atol, pf_stats* out);
+
+/* As pf_advance, but stop after at most max_attempts step attempts
+ * (accepted or rejected); the clock and controller state carry over. */
+int pf_advance_attempts(pf_ctx* ctx, double t_final, double rtol, double atol, int max_attempts, pf_stats* out);
+
+/* Advance n independent contexts (same stream, same method and precision,
+ * any grid sizes) to t_final, each with its own step size and controller,
+ * the stages of all members issued together per pass.  `out` has n entries or
+ * is NULL. */
+int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, double atol, pf_stats* out);
+
+/* Total free energy F = int (f_b + f_el + f_ch) dV of the current state
+ * (Sec. 4.1), FP64. */
+int pf_free_energy(pf_ctx* ctx, double* F_out);
+
+/* Integrator clock (for checkpoint/resume). */
+int pf_get_time(pf_ctx* ctx, double* t, double* h);
+int pf_set_time(pf_ctx* ctx, double t, double h);
+int pf_get_stats(pf_ctx* ctx, pf_stats* out);
+/* Step attempts of the last pf_advance as (t, h, ||LTE||_WRMS, accepted)
+ * quadruples; writes at most max_attempts of them to buf (NULL allowed) and
+ * returns the total count.  Lets a caller replay the decision sequence. */
+int pf_get_attempts(pf_ctx* ctx, double* buf, int max_attempts);
+
+/* Kernel profiler: CUDA events around every launch of the step driver on the
+ * context's stream, with the algorithmic bytes of each launch (each field read
+ * or written once per pass as the method requires).  Kernel kinds: */
+#define PF_K_Z_STAGE 0    /* stage assembly + implicit solve + inverse z FFT   */
+#define PF_K_Y 1          /* y FFT (either direction)                           */
+#define PF_K_X_PHYS1 2    /* C2R x + real-space physics (h or full RHS) + R2C  */
+#define PF_K_X_PHYS2 3    /* C2R x of e_v + KKS/barrier RHS + R2C              */
+#define PF_K_Z_ELASTIC 4  /* forward z, Green's contraction, inverse z         */
+#define PF_K_Z_FWD 5      /* forward z + k-space scaling -> f^E                 */
+#define PF_K_Z_FINAL 6    /* step completion + embedded error + inverse z       */
+#define PF_K_X_WRMS 7     /* C2R x of the error + WRMS partial sums             */
+#define PF_K_REDUCE 8     /* deterministic WRMS reduction                       */
+#define PF_K_POINTWISE 9  /* stage assembly without a RHS evaluation            */
+#define PF_NKERNELS 10
+/* Turn the profiler on/off (clears pending records). */
+int pf_profile_enable(pf_ctx* ctx, int on);
+/* Synchronise and return, per kind, the summed event time (ms), algorithmic
+ * bytes and launch count since the last read (arrays of PF_NKERNELS; NULL
+ * allowed); clears the records. */
+int pf_profile_read(pf_ctx* ctx, double* ms, double* bytes, long long* launches);
+const char* pf_kernel_name(int kind);
+
+/* Host-side query of a method's Butcher arrays (row-major s x s, length-s
+ * vectors; bt/dt embedding NULL-able buffers).  Returns the stage count s,
+ * or PF_EUNSUPPORTED. Buffers must hold s*s (A) and s (b) doubles; s <= 8. */
+int pf_method_tableau(int method, double* AE, double* AI, double* bE, double* bI, double* btE, double* btI);
+
+/* Description of the last error of `ctx` (or of the last failed pf_create
+ * when ctx is NULL). Never NULL. */
+const char* pf_last_error(const pf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

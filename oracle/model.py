@@ -15,7 +15,9 @@ the readings:
 * composition stiff part lambda_X = -2 A^m M k^2, the rest explicit;
 * parabolic f^p = A0^p + A^p (X^p - B^p)^2 (Eq. f_ch_p read as squared);
 * barrier: omega_bar sum_v phi_v^2 (1 - phi_v)^2 (double-well reading of Eq. f_b);
-* sgn(0) = 0 in d|phi_v phi_q|/dphi_v;
+* the |x| of the pairwise barrier omega_vq |phi_v phi_q| is Huber-regularised
+  with width eps (A(x) = x^2/(2 eps) for |x| < eps, |x| - eps/2 beyond), so
+  d/dphi_v = omega_vq clip(phi_v phi_q / eps, -1, 1) phi_q is continuous;
 * one solute (Nb);
 * homogeneous modulus (iteration 0 of the Hu-Chen scheme), stress-free mean
   strain so that B(k = 0) = 0;
@@ -93,6 +95,7 @@ class Model:
         self.A0m, self.A0v = p["A0_m"], p["A0_v"]
         self.L = p["L"]
         self.wbar = p["omega_bar"]
+        self.pair_eps = p["pair_eps"]
         w12, w13, w23 = p["omega_pair"]
         self.omega = np.array([[0.0, w12, w13], [w12, 0.0, w23], [w13, w23, 0.0]])
         kx = wavenumbers(nx, d, True)
@@ -140,14 +143,20 @@ class Model:
         return H, mu, Xm, Xv, fm, fv
 
     def dfb_dphi(self, phi):
-        """Derivative of the local part of f_b: double well plus pairwise
-        |phi_v phi_q| barrier."""
+        """Derivative of the local part of f_b: double well plus the
+        (regularised) pairwise |phi_v phi_q| barrier."""
         out = 2.0 * self.wbar * phi * (1.0 - phi) * (1.0 - 2.0 * phi)
         for v in range(3):
             for q in range(3):
                 if q != v:
-                    out[v] = out[v] + self.omega[v, q] * np.sign(phi[v]) * np.abs(phi[q])
+                    slope = np.clip(phi[v] * phi[q] / self.pair_eps, -1.0, 1.0)
+                    out[v] = out[v] + self.omega[v, q] * slope * phi[q]
         return out
+
+    def pair_abs(self, x):
+        """Huber-regularised |x| of the pairwise barrier."""
+        e = self.pair_eps
+        return np.where(np.abs(x) < e, x * x / (2.0 * e), np.abs(x) - 0.5 * e)
 
     def elastic_potential(self, h):
         """e_v(r) = IFFT[sum_q B_vq(n) h^_q(k)] (homogeneous-modulus solution
@@ -193,7 +202,7 @@ class Model:
         local = self.wbar * (phi ** 2 * (1.0 - phi) ** 2).sum(axis=0)
         for v in range(3):
             for q in range(v + 1, 3):
-                local = local + self.omega[v, q] * np.abs(phi[v] * phi[q])
+                local = local + self.omega[v, q] * self.pair_abs(phi[v] * phi[q])
         local = local + H * fv + (1.0 - H) * fm
         F = local.sum() * self.dV
         nx = self.shape[2]

@@ -1,0 +1,945 @@
+// Host side of the phase-field library: contexts, FFT plans and twiddle
+// tables, the ImEx-ARK step driver (Sec. 4.4 of the paper), the adaptive step
+// controller, and the C ABI declared in include/pf.h.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "pf.h"
+#include "pf_internal.h"
+
+using namespace pf;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+const double kRgas = 8.314462618;
+
+thread_local char g_create_err[256] = "no error";
+
+// ---------------------------------------------------------------------------
+// Butcher tables (Sec. 4.4).  ImEx Euler as a 2-stage pair; ARK4(3)6L[2]SA of
+// Kennedy & Carpenter (2003), six stages, ESDIRK gamma = 1/4, third-order
+// embedding.  Entries are the published rationals.
+// ---------------------------------------------------------------------------
+struct Tableau {
+    int s = 0;
+    double AE[kMaxStages][kMaxStages] = {};
+    double AI[kMaxStages][kMaxStages] = {};
+    double bE[kMaxStages] = {}, bI[kMaxStages] = {};
+    double btE[kMaxStages] = {}, btI[kMaxStages] = {};
+    bool embedded = false;
+    int emb_order = 0;
+};
+
+bool make_tableau(int method, Tableau& t) {
+    t = Tableau();
+    if (method == PF_EULER) {
+        t.s = 2;
+        t.AE[1][0] = 1.0;
+        t.AI[1][1] = 1.0;
+        t.bE[0] = 1.0;
+        t.bI[1] = 1.0;
+        return true;
+    }
+    if (method == PF_ARK4) {
+        t.s = 6;
+        t.embedded = true;
+        t.emb_order = 3;
+        double (*E)[kMaxStages] = t.AE;
+        E[1][0] = 1.0 / 2.0;
+        E[2][0] = 13861.0 / 62500.0;
+        E[2][1] = 6889.0 / 62500.0;
+        E[3][0] = -116923316275.0 / 2393684061468.0;
+        E[3][1] = -2731218467317.0 / 15368042101831.0;
+        E[3][2] = 9408046702089.0 / 11113171139209.0;
+        E[4][0] = -451086348788.0 / 2902428689909.0;
+        E[4][1] = -2682348792572.0 / 7519795681897.0;
+        E[4][2] = 12662868775082.0 / 11960479115383.0;
+        E[4][3] = 3355817975965.0 / 11060851509271.0;
+        E[5][0] = 647845179188.0 / 3216320057751.0;
+        E[5][1] = 73281519250.0 / 8382639484533.0;
+        E[5][2] = 552539513391.0 / 3454668386233.0;
+        E[5][3] = 3354512671639.0 / 8306763924573.0;
+        E[5][4] = 4040.0 / 17871.0;
+        double (*I)[kMaxStages] = t.AI;
+        I[1][0] = 1.0 / 4.0;
+        I[1][1] = 1.0 / 4.0;
+        I[2][0] = 8611.0 / 62500.0;
+        I[2][1] = -1743.0 / 31250.0;
+        I[2][2] = 1.0 / 4.0;
+        I[3][0] = 5012029.0 / 34652500.0;
+        I[3][1] = -654441.0 / 2922500.0;
+        I[3][2] = 174375.0 / 388108.0;
+        I[3][3] = 1.0 / 4.0;
+        I[4][0] = 15267082809.0 / 155376265600.0;
+        I[4][1] = -71443401.0 / 120774400.0;
+        I[4][2] = 730878875.0 / 902184768.0;
+        I[4][3] = 2285395.0 / 8070912.0;
+        I[4][4] = 1.0 / 4.0;
+        const double b[6] = {82889.0 / 524892.0, 0.0, 15625.0 / 83664.0, 69875.0 / 102672.0, -2260.0 / 8211.0,
+                             1.0 / 4.0};
+        const double bt[6] = {4586570599.0 / 29645900160.0, 0.0, 178811875.0 / 945068544.0,
+                              814220225.0 / 1159782912.0, -3700637.0 / 11593932.0, 61727.0 / 225920.0};
+        for (int i = 0; i < 6; ++i) {
+            I[5][i] = b[i];
+            t.bE[i] = t.bI[i] = b[i];
+            t.btE[i] = t.btI[i] = bt[i];
+        }
+        return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// FFT plans
+// ---------------------------------------------------------------------------
+bool factor_radices(int n, AxisPlan& p) {
+    int m = n, a = 0, b = 0, c = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    while (m % 3 == 0) { m /= 3; ++b; }
+    while (m % 5 == 0) { m /= 5; ++c; }
+    if (m != 1) return false;
+    p.n = n;
+    p.nst = 0;
+    std::vector<int> r;
+    int n8 = a / 3, rem = a % 3;
+    if (rem == 1 && n8 > 0) {  // 2^(3k+1): prefer 4*4 over 8*2
+        --n8;
+        r.push_back(4);
+        r.push_back(4);
+    } else if (rem == 2) {
+        r.push_back(4);
+    } else if (rem == 1) {
+        r.push_back(2);
+    }
+    for (int i = 0; i < n8; ++i) r.insert(r.begin(), 8);
+    for (int i = 0; i < b; ++i) r.push_back(3);
+    for (int i = 0; i < c; ++i) r.push_back(5);
+    if ((int)r.size() > kMaxRadices) return false;
+    for (size_t i = 0; i < r.size(); ++i) p.rad[p.nst++] = r[i];
+    return true;
+}
+
+// exp(-2 pi i k / n) evaluated in extended precision with the angle reduced
+// to the first octant, then rounded to double.
+void twiddle_table(int n, std::vector<double2>& tw) {
+    tw.resize(n);
+    for (int k = 0; k < n; ++k) {
+        // angle = 2 pi k / n; reduce with exact integer arithmetic on 8k/n
+        const long double frac = (long double)k / (long double)n;  // in [0,1)
+        const long double th = 2.0L * 3.141592653589793238462643383279502884L * frac;
+        long double c = cosl(th), s = sinl(th);
+        // symmetric exact points
+        if (4 * k % n == 0) {
+            const int q = 4 * k / n;
+            c = (q == 0) ? 1.0L : (q == 2 ? -1.0L : 0.0L);
+            s = (q == 1) ? 1.0L : (q == 3 ? -1.0L : 0.0L);
+        }
+        tw[k] = make_double2((double)c, -(double)s);
+    }
+}
+
+bool smooth_even(int n) {
+    if (n < 4 || n > 1024 || (n & 1)) return false;
+    int m = n;
+    for (int p : {2, 3, 5})
+        while (m % p == 0) m /= p;
+    return m == 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct pf_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    pf_grid grid{};
+    pf_params prm{};
+    Tableau tab;
+    bool fp32 = false;
+    Geo g{};
+    Phys ph{};
+    // stage bookkeeping
+    bool need_fe[kMaxStages] = {};
+    bool alias_y[kMaxStages] = {};  // z_i == y_{n-1} exactly (explicit first stage)
+    // device memory
+    double *d_kx = nullptr, *d_ky = nullptr, *d_kz = nullptr;
+    double2* d_tw64[3] = {};
+    float2* d_tw32[3] = {};
+    double2* y = nullptr;
+    double2* ynew = nullptr;
+    double2* zhat[kMaxStages] = {};
+    void* fE[kMaxStages] = {};
+    void* W = nullptr;
+    void* H = nullptr;
+    void* R = nullptr;
+    void* R1 = nullptr;
+    double* partials = nullptr;
+    int npartials = 0;
+    double* d_scalar = nullptr;
+    double* h_scalar = nullptr;  // pinned
+    // integrator state
+    double t = 0.0, h = 0.0;
+    double e_prev = 1.0;
+    bool after_reject = false;
+    pf_stats st{};
+    std::vector<double> attempts;  // (t, h, e, accepted) quadruples of the last advance
+    // kernel profiler
+    bool prof_on = false;
+    struct Rec {
+        int kind;
+        cudaEvent_t e0, e1;
+        double bytes;
+    };
+    std::vector<Rec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_next = 0;
+    char err[256] = "no error";
+};
+
+namespace {
+
+int fail(pf_ctx* c, int code, const char* fmt, ...) {
+    char* dst = c ? c->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define PF_CUDA(ctx, call)                                                                        \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(ctx, PF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+cudaEvent_t prof_event(pf_ctx* c) {
+    if (c->prof_next == c->prof_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->prof_pool.push_back(e);
+    }
+    return c->prof_pool[c->prof_next++];
+}
+
+int check_launch(pf_ctx* c, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, PF_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+    return PF_OK;
+}
+
+void derive_phys(const pf_params& p, Phys& ph) {
+    ph = Phys();
+    ph.M = p.M0 * std::exp(-p.Q_act / kRgas * (1.0 / p.T - 1.0 / p.T0));
+    ph.Am = p.A_m;
+    ph.Av = p.A_v;
+    ph.A0m = p.A0_m;
+    ph.A0v = p.A0_v;
+    ph.Bm = p.B_m0 + p.dBm_dT * (p.T - p.T0);
+    ph.Bv = p.B_v;
+    ph.inv2Am = 1.0 / (2.0 * p.A_m);
+    ph.inv2Av = 1.0 / (2.0 * p.A_v);
+    ph.L = p.L;
+    ph.wbar = p.omega_bar;
+    ph.pair_eps = p.pair_eps;
+    ph.w[0][1] = ph.w[1][0] = p.omega_pair[0];
+    ph.w[0][2] = ph.w[2][0] = p.omega_pair[1];
+    ph.w[1][2] = ph.w[2][1] = p.omega_pair[2];
+    std::memcpy(ph.kap, p.kappa, sizeof(ph.kap));
+    ph.C44 = p.C44;
+    ph.Cmix = p.C12 + p.C44;
+    ph.Caniso = p.C11 - p.C12 - 2.0 * p.C44;
+    ph.elastic = 0;
+    for (int v = 0; v < 3; ++v)
+        for (int i = 0; i < 6; ++i)
+            if (p.eps_star[v][i] != 0.0) ph.elastic = 1;
+    // sigma* = C : eps* for cubic C (Voigt, tensor shear components)
+    for (int v = 0; v < 3; ++v) {
+        const double* e = p.eps_star[v];
+        const double tr = e[0] + e[1] + e[2];
+        for (int i = 0; i < 3; ++i) ph.sig[v][i] = (p.C11 - p.C12) * e[i] + p.C12 * tr;
+        for (int i = 3; i < 6; ++i) ph.sig[v][i] = 2.0 * p.C44 * e[i];
+    }
+    for (int v = 0; v < 3; ++v)
+        for (int q = 0; q < 3; ++q) {
+            const double* e = p.eps_star[v];
+            const double* s = ph.sig[q];
+            ph.cvq[v][q] = e[0] * s[0] + e[1] * s[1] + e[2] * s[2] + 2.0 * (e[3] * s[3] + e[4] * s[4] + e[5] * s[5]);
+        }
+}
+
+void free_all(pf_ctx* c) {
+    cudaFree(c->d_kx);
+    cudaFree(c->d_ky);
+    cudaFree(c->d_kz);
+    for (int i = 0; i < 3; ++i) {
+        cudaFree(c->d_tw64[i]);
+        cudaFree(c->d_tw32[i]);
+    }
+    cudaFree(c->y);
+    cudaFree(c->ynew);
+    for (int i = 0; i < kMaxStages; ++i) {
+        cudaFree(c->zhat[i]);
+        cudaFree(c->fE[i]);
+    }
+    cudaFree(c->W);
+    cudaFree(c->H);
+    cudaFree(c->R);
+    cudaFree(c->R1);
+    cudaFree(c->partials);
+    cudaFree(c->d_scalar);
+    if (c->h_scalar) cudaFreeHost(c->h_scalar);
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+    c->prof_pool.clear();
+}
+
+template <typename P>
+int dalloc(pf_ctx* c, P** p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PF_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    return PF_OK;
+}
+
+double2* fp64_scratch(pf_ctx* c) { return c->zhat[c->tab.s - 1]; }
+
+// Enqueue one attempted ImEx-ARK step of size dt from c->y into c->ynew; the
+// WRMS sum of the local error lands in c->d_scalar when want_lte.
+// Per-kernel CUDA-event timing with the algorithmic bytes of each launch
+// (what the method must read and write once: every field-pass counted once).
+struct ProfScope {
+    pf_ctx* c;
+    int kind;
+    double bytes;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(pf_ctx* c_, int kind_, double bytes_) : c(c_), kind(kind_), bytes(bytes_) {
+        if (c->prof_on) {
+            e0 = prof_event(c);
+            cudaEventRecord(e0, c->stream);
+        }
+    }
+    ~ProfScope() {
+        if (!c->prof_on) return;
+        cudaEvent_t e1 = prof_event(c);
+        cudaEventRecord(e1, c->stream);
+        c->prof_recs.push_back({kind, e0, e1, bytes});
+    }
+};
+
+template <typename T>
+int enqueue_step(pf_ctx* c, double dt, bool want_lte) {
+    using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+    const Geo& g = c->g;
+    const Phys& ph = c->ph;
+    const Tableau& tb = c->tab;
+    cudaStream_t s = c->stream;
+    const double NK = (double)g.NK, N = (double)g.N, cb = sizeof(T2), rb = sizeof(T);
+    double2* zp[kMaxStages];
+    for (int i = 0; i < tb.s; ++i) zp[i] = c->alias_y[i] ? c->y : c->zhat[i];
+    for (int i = 0; i < tb.s; ++i) {
+        StageTerms st{};
+        st.n = i;
+        double terms = 0;  // bytes per k entry read from earlier stages
+        for (int j = 0; j < i; ++j) {
+            st.z[j] = zp[j];
+            st.f[j] = c->fE[j];
+            st.cI[j] = dt * tb.AI[i][j];
+            st.cE[j] = dt * tb.AE[i][j];
+            terms += (st.cI[j] != 0.0 && !c->alias_y[j] ? 16.0 : 0.0) + (st.cE[j] != 0.0 ? (c->fp32 ? 8.0 : 16.0) : 0.0);
+        }
+        st.gamma = dt * tb.AI[i][i];
+        double2* zout = c->alias_y[i] ? nullptr : zp[i];
+        if (!c->need_fe[i]) {
+            if (zout) {
+                ProfScope p(c, PF_K_POINTWISE, 4 * NK * (16.0 + terms + 16.0));
+                launch_stage_pointwise(g, ph, c->y, st, c->fp32 ? 1 : 0, zout, s);
+            }
+            continue;
+        }
+        void* Ri = (i == 0) ? c->R1 : c->R;
+        {
+            ProfScope p(c, PF_K_Z_STAGE, 4 * NK * (16.0 + terms + (zout ? 16.0 : 0.0) + cb));
+            launch_z_stage<T>(g, ph, c->y, st, zout, c->W, s);
+        }
+        {
+            ProfScope p(c, PF_K_Y, 4 * NK * 2 * cb);
+            launch_y_pass<T>(g, c->W, 4, +1, s);
+        }
+        if (ph.elastic) {
+            {
+                ProfScope p(c, PF_K_X_PHYS1, 4 * NK * cb + 4 * N * rb + 3 * NK * cb);
+                launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->H, Ri, nullptr, nullptr, 0, 0, nullptr, nullptr, s);
+            }
+            {
+                ProfScope p(c, PF_K_Y, 3 * NK * 2 * cb);
+                launch_y_pass<T>(g, c->H, 3, -1, s);
+            }
+            {
+                ProfScope p(c, PF_K_Z_ELASTIC, 3 * NK * 2 * cb);
+                launch_z_elastic<T>(g, ph, c->H, s);
+            }
+            {
+                ProfScope p(c, PF_K_Y, 3 * NK * 2 * cb);
+                launch_y_pass<T>(g, c->H, 3, +1, s);
+            }
+            {
+                ProfScope p(c, PF_K_X_PHYS2, 3 * NK * cb + 4 * N * rb + 4 * NK * cb);
+                launch_x_pass<T>(g, ph, XM_PHYS2, c->H, c->W, nullptr, Ri, nullptr, 0, 0, nullptr, nullptr, s);
+            }
+        } else {
+            ProfScope p(c, PF_K_X_PHYS1, 8 * NK * cb + (i == 0 ? 4 * N * rb : 0.0));
+            launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->W, (i == 0) ? Ri : nullptr, nullptr, nullptr, 0, 0, nullptr,
+                             nullptr, s);
+        }
+        {
+            ProfScope p(c, PF_K_Y, 4 * NK * 2 * cb);
+            launch_y_pass<T>(g, c->W, 4, -1, s);
+        }
+        {
+            ProfScope p(c, PF_K_Z_FWD, 4 * NK * 2 * cb);
+            launch_z_fwd<T>(g, ph, c->W, c->fE[i], 1, s);
+        }
+    }
+    StageTerms bt{}, dtm{};
+    bt.n = dtm.n = tb.s;
+    double fterms = 0;
+    const bool lte = want_lte && tb.embedded;
+    for (int j = 0; j < tb.s; ++j) {
+        bt.z[j] = dtm.z[j] = zp[j];
+        bt.f[j] = dtm.f[j] = c->fE[j];
+        bt.cI[j] = dt * tb.bI[j];
+        bt.cE[j] = dt * tb.bE[j];
+        if (tb.embedded) {
+            dtm.cI[j] = dt * (tb.bI[j] - tb.btI[j]);
+            dtm.cE[j] = dt * (tb.bE[j] - tb.btE[j]);
+        }
+        const bool zI = bt.cI[j] != 0.0 || (lte && dtm.cI[j] != 0.0);
+        const bool fEn = bt.cE[j] != 0.0 || (lte && dtm.cE[j] != 0.0);
+        fterms += (zI && !(c->alias_y[j]) ? 16.0 : 0.0) + (fEn ? (c->fp32 ? 8.0 : 16.0) : 0.0);
+    }
+    {
+        ProfScope p(c, PF_K_Z_FINAL, 4 * NK * (16.0 + fterms + 16.0 + (lte ? cb : 0.0)));
+        launch_z_final<T>(g, ph, c->y, bt, dtm, lte ? 1 : 0, c->ynew, c->W, s);
+    }
+    if (lte) {
+        {
+            ProfScope p(c, PF_K_Y, 4 * NK * 2 * cb);
+            launch_y_pass<T>(g, c->W, 4, +1, s);
+        }
+        {
+            ProfScope p(c, PF_K_X_WRMS, 4 * NK * cb + 4 * N * rb);
+            launch_x_pass<T>(g, ph, XM_WRMS, c->W, nullptr, nullptr, c->R1, c->partials, c->prm.rtol, c->prm.atol,
+                             nullptr, nullptr, s);
+        }
+        {
+            const int nb = x_pass_blocks(g, sizeof(T) == 8);
+            ProfScope p(c, PF_K_REDUCE, nb * 8.0);
+            launch_reduce(c->partials, nb, 1.0 / (4.0 * (double)g.N), c->d_scalar, s);
+        }
+    }
+    return check_launch(c, "step kernels");
+}
+
+int step_once(pf_ctx* c, double dt, bool want_lte, double* e_out) {
+    int rc = c->fp32 ? enqueue_step<float>(c, dt, want_lte) : enqueue_step<double>(c, dt, want_lte);
+    if (rc) return rc;
+    int nrhs = 0;
+    for (int i = 0; i < c->tab.s; ++i) nrhs += c->need_fe[i] ? 1 : 0;
+    c->st.rhs_evals += nrhs;
+    c->st.point_stages += (long long)nrhs * c->g.N;
+    double e = 0.0;
+    if (want_lte && c->tab.embedded) {
+        PF_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        PF_CUDA(c, cudaStreamSynchronize(c->stream));
+        e = std::sqrt(c->h_scalar[0]);
+    }
+    if (e_out) *e_out = e;
+    return PF_OK;
+}
+
+// controller (mirrors the documented PI rule)
+double ctl_accept(pf_ctx* c, double h, double e) {
+    const pf_params& p = c->prm;
+    const double q = c->tab.emb_order + 1;
+    e = e < 1e-10 ? 1e-10 : e;
+    double eta = p.safety * std::pow(e, -p.k1 / q) * std::pow(c->e_prev, p.k2 / q);
+    const double cap = c->after_reject ? 1.0 : p.eta_max;
+    eta = std::fmin(cap, std::fmax(p.eta_min, eta));
+    c->e_prev = e;
+    c->after_reject = false;
+    return h * eta;
+}
+
+double ctl_reject(pf_ctx* c, double h, double e) {
+    const pf_params& p = c->prm;
+    c->after_reject = true;
+    if (!std::isfinite(e)) return h * 0.25;
+    const double q = c->tab.emb_order + 1;
+    return h * std::fmax(p.eta_reject_min, p.safety * std::pow(e, -1.0 / q));
+}
+
+}  // namespace
+
+namespace {
+template <typename T>
+int rhs_explicit_t(pf_ctx* c, const double2* yh, double2* out) {
+    const Geo& g = c->g;
+    const Phys& ph = c->ph;
+    cudaStream_t s = c->stream;
+    StageTerms none{};
+    launch_z_stage<T>(g, ph, yh, none, nullptr, c->W, s);
+    launch_y_pass<T>(g, c->W, 4, +1, s);
+    if (ph.elastic) {
+        launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->H, c->R, nullptr, nullptr, 0, 0, nullptr, nullptr, s);
+        launch_y_pass<T>(g, c->H, 3, -1, s);
+        launch_z_elastic<T>(g, ph, c->H, s);
+        launch_y_pass<T>(g, c->H, 3, +1, s);
+        launch_x_pass<T>(g, ph, XM_PHYS2, c->H, c->W, nullptr, c->R, nullptr, 0, 0, nullptr, nullptr, s);
+    } else {
+        launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->W, nullptr, nullptr, nullptr, 0, 0, nullptr, nullptr, s);
+    }
+    launch_y_pass<T>(g, c->W, 4, -1, s);
+    launch_z_fwd<T>(g, ph, c->W, out, 2, s);
+    return check_launch(c, "pf_rhs_explicit");
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err : g_create_err; }
+
+int pf_method_tableau(int method, double* AE, double* AI, double* bE, double* bI, double* btE, double* btI) {
+    Tableau t;
+    if (!make_tableau(method, t)) return PF_EUNSUPPORTED;
+    for (int i = 0; i < t.s; ++i) {
+        for (int j = 0; j < t.s; ++j) {
+            if (AE) AE[i * t.s + j] = t.AE[i][j];
+            if (AI) AI[i * t.s + j] = t.AI[i][j];
+        }
+        if (bE) bE[i] = t.bE[i];
+        if (bI) bI[i] = t.bI[i];
+        if (btE) btE[i] = t.embedded ? t.btE[i] : 0.0;
+        if (btI) btI[i] = t.embedded ? t.btI[i] : 0.0;
+    }
+    return t.s;
+}
+
+int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, pf_ctx** out) {
+    if (!grid || !params || !out) return fail(nullptr, PF_EINVAL, "pf_create: NULL argument");
+    *out = nullptr;
+    if (!smooth_even(grid->nx) || !smooth_even(grid->ny) || !smooth_even(grid->nz))
+        return fail(nullptr, PF_EUNSUPPORTED, "grid %dx%dx%d: each size must be even, 2,3,5-smooth, 4..1024",
+                    grid->nx, grid->ny, grid->nz);
+    if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
+        return fail(nullptr, PF_EINVAL, "grid spacing must be positive");
+    if (params->precision != PF_FP64 && params->precision != PF_FP32BULK)
+        return fail(nullptr, PF_EINVAL, "unknown precision %d", params->precision);
+    if (!(params->A_m > 0) || !(params->A_v > 0) || !(params->T > 0) || !(params->T0 > 0) || params->L < 0 ||
+        params->M0 < 0 || !(params->pair_eps > 0))
+        return fail(nullptr, PF_EINVAL, "invalid model constants (A_m, A_v, T, T0, pair_eps > 0; L, M0 >= 0)");
+    pf_ctx* c = new (std::nothrow) pf_ctx();
+    if (!c) return fail(nullptr, PF_ENOMEM, "host allocation failed");
+    if (!make_tableau(params->method, c->tab)) {
+        delete c;
+        return fail(nullptr, PF_EUNSUPPORTED, "unknown method %d", params->method);
+    }
+    cudaGetDevice(&c->dev);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->grid = *grid;
+    c->prm = *params;
+    c->fp32 = params->precision == PF_FP32BULK;
+    derive_phys(*params, c->ph);
+    const Tableau& tb = c->tab;
+    for (int i = 0; i < tb.s; ++i) {
+        bool nf = tb.bE[i] != 0.0 || (tb.embedded && tb.btE[i] != 0.0);
+        for (int k = i + 1; k < tb.s; ++k) nf = nf || tb.AE[k][i] != 0.0;
+        c->need_fe[i] = nf;
+        bool ex = tb.AI[i][i] == 0.0;
+        for (int j = 0; j < i; ++j) ex = ex && tb.AI[i][j] == 0.0 && tb.AE[i][j] == 0.0;
+        c->alias_y[i] = ex;
+    }
+    Geo& g = c->g;
+    g.nx = grid->nx;
+    g.ny = grid->ny;
+    g.nz = grid->nz;
+    g.nxh = g.nx / 2 + 1;
+    g.NK = (long long)g.nz * g.ny * g.nxh;
+    g.N = (long long)g.nz * g.ny * g.nx;
+    int rc = PF_OK;
+    // wave numbers k_m = 2 pi m / (n d), Nyquist +pi/d
+    auto ktab = [](int n, double d, bool half) {
+        std::vector<double> k(half ? n / 2 + 1 : n);
+        for (int i = 0; i < (int)k.size(); ++i) {
+            int m = i;
+            if (!half && i > n / 2) m = i - n;
+            k[i] = 2.0 * kPi * m / (n * d);
+        }
+        return k;
+    };
+    std::vector<double> kx = ktab(g.nx, grid->dx, true), ky = ktab(g.ny, grid->dy, false),
+                        kz = ktab(g.nz, grid->dz, false);
+    AxisPlan* plans[3] = {&g.px, &g.py, &g.pz};
+    const int ns[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+        if (!factor_radices(ns[a], *plans[a])) {
+            delete c;
+            return fail(nullptr, PF_EUNSUPPORTED, "cannot factor %d", ns[a]);
+        }
+    }
+    const size_t nk4 = 4 * (size_t)g.NK;
+    const size_t tsz = c->fp32 ? sizeof(float) : sizeof(double);
+    rc = rc ? rc : dalloc(c, &c->d_kx, kx.size() * sizeof(double));
+    rc = rc ? rc : dalloc(c, &c->d_ky, ky.size() * sizeof(double));
+    rc = rc ? rc : dalloc(c, &c->d_kz, kz.size() * sizeof(double));
+    for (int a = 0; a < 3 && !rc; ++a) {
+        rc = rc ? rc : dalloc(c, &c->d_tw64[a], ns[a] * sizeof(double2));
+        rc = rc ? rc : dalloc(c, &c->d_tw32[a], ns[a] * sizeof(float2));
+    }
+    rc = rc ? rc : dalloc(c, &c->y, nk4 * sizeof(double2));
+    rc = rc ? rc : dalloc(c, &c->ynew, nk4 * sizeof(double2));
+    for (int i = 0; i < tb.s && !rc; ++i) {
+        if (!c->alias_y[i]) rc = dalloc(c, &c->zhat[i], nk4 * sizeof(double2));
+        if (!rc && c->need_fe[i]) rc = dalloc(c, &c->fE[i], nk4 * 2 * tsz);
+    }
+    rc = rc ? rc : dalloc(c, &c->W, nk4 * 2 * tsz);
+    rc = rc ? rc : dalloc(c, &c->H, 3 * (size_t)g.NK * 2 * tsz);
+    rc = rc ? rc : dalloc(c, &c->R, 4 * (size_t)g.N * tsz);
+    rc = rc ? rc : dalloc(c, &c->R1, 4 * (size_t)g.N * tsz);
+    c->npartials = x_pass_blocks(g, 0) > x_pass_blocks(g, 1) ? x_pass_blocks(g, 0) : x_pass_blocks(g, 1);
+    if (energy_k_blocks(g) > c->npartials) c->npartials = energy_k_blocks(g);
+    rc = rc ? rc : dalloc(c, &c->partials, (size_t)c->npartials * sizeof(double));
+    rc = rc ? rc : dalloc(c, &c->d_scalar, 4 * sizeof(double));
+    if (!rc && cudaMallocHost((void**)&c->h_scalar, 4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(c, PF_ENOMEM, "cudaMallocHost failed");
+    }
+    if (rc) {
+        std::snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMemcpy(c->d_kx, kx.data(), kx.size() * sizeof(double), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(c->d_ky, ky.data(), ky.size() * sizeof(double), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(c->d_kz, kz.data(), kz.size() * sizeof(double), cudaMemcpyHostToDevice);
+    for (int a = 0; a < 3 && !e; ++a) {
+        std::vector<double2> tw;
+        twiddle_table(ns[a], tw);
+        std::vector<float2> tw32(tw.size());
+        for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+        e = cudaMemcpy(c->d_tw64[a], tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice);
+        e = e ? e : cudaMemcpy(c->d_tw32[a], tw32.data(), tw32.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        plans[a]->tw64 = c->d_tw64[a];
+        plans[a]->tw32 = c->d_tw32[a];
+    }
+    e = e ? e : cudaMemsetAsync(c->y, 0, nk4 * sizeof(double2), c->stream);
+    e = e ? e : cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        std::snprintf(g_create_err, sizeof g_create_err, "device setup: %s", cudaGetErrorString(e));
+        free_all(c);
+        delete c;
+        return PF_ECUDA;
+    }
+    g.kx = c->d_kx;
+    g.ky = c->d_ky;
+    g.kz = c->d_kz;
+    c->t = 0.0;
+    c->h = params->h0;
+    c->st.h = c->h;
+    *out = c;
+    return PF_OK;
+}
+
+void pf_destroy(pf_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->dev);
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+}
+
+int pf_set_state(pf_ctx* c, const double* fields, int on_device) {
+    if (!c || !fields) return fail(c, PF_EINVAL, "pf_set_state: NULL argument");
+    cudaSetDevice(c->dev);
+    const Geo& g = c->g;
+    double* real = reinterpret_cast<double*>(fp64_scratch(c));
+    const double* src = fields;
+    if (!on_device) {
+        PF_CUDA(c, cudaMemcpyAsync(real, fields, 4 * (size_t)g.N * sizeof(double), cudaMemcpyHostToDevice,
+                                   c->stream));
+        src = real;
+    }
+    launch_x_pass<double>(g, c->ph, XM_R2C_REAL, nullptr, c->ynew, nullptr, nullptr, nullptr, 0, 0, src, nullptr,
+                          c->stream);
+    launch_y_pass<double>(g, c->ynew, 4, -1, c->stream);
+    launch_z_fwd<double>(g, c->ph, c->ynew, c->y, 0, c->stream);
+    int rc = check_launch(c, "pf_set_state");
+    if (rc) return rc;
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PF_OK;
+}
+
+int pf_get_state(pf_ctx* c, double* fields, int on_device) {
+    if (!c || !fields) return fail(c, PF_EINVAL, "pf_get_state: NULL argument");
+    cudaSetDevice(c->dev);
+    const Geo& g = c->g;
+    StageTerms none{};
+    launch_z_stage<double>(g, c->ph, c->y, none, nullptr, c->ynew, c->stream);
+    launch_y_pass<double>(g, c->ynew, 4, +1, c->stream);
+    double* real = on_device ? fields : reinterpret_cast<double*>(fp64_scratch(c));
+    launch_x_pass<double>(g, c->ph, XM_C2R_REAL, c->ynew, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr, real,
+                          c->stream);
+    int rc = check_launch(c, "pf_get_state");
+    if (rc) return rc;
+    if (!on_device)
+        PF_CUDA(c, cudaMemcpyAsync(fields, real, 4 * (size_t)g.N * sizeof(double), cudaMemcpyDeviceToHost,
+                                   c->stream));
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PF_OK;
+}
+
+int pf_set_state_hat(pf_ctx* c, const void* y_hat, int on_device) {
+    if (!c || !y_hat) return fail(c, PF_EINVAL, "pf_set_state_hat: NULL argument");
+    cudaSetDevice(c->dev);
+    PF_CUDA(c, cudaMemcpyAsync(c->y, y_hat, 4 * (size_t)c->g.NK * sizeof(double2),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PF_OK;
+}
+
+int pf_get_state_hat(pf_ctx* c, void* y_hat, int on_device) {
+    if (!c || !y_hat) return fail(c, PF_EINVAL, "pf_get_state_hat: NULL argument");
+    cudaSetDevice(c->dev);
+    PF_CUDA(c, cudaMemcpyAsync(y_hat, c->y, 4 * (size_t)c->g.NK * sizeof(double2),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PF_OK;
+}
+
+
+int pf_rhs_explicit(pf_ctx* c, const void* y_hat, void* fE_hat) {
+    if (!c || !y_hat || !fE_hat) return fail(c, PF_EINVAL, "pf_rhs_explicit: NULL argument");
+    if (y_hat == fE_hat) return fail(c, PF_EINVAL, "pf_rhs_explicit: y_hat and fE_hat may not alias");
+    cudaSetDevice(c->dev);
+    const double2* yh = reinterpret_cast<const double2*>(y_hat);
+    double2* out = reinterpret_cast<double2*>(fE_hat);
+    int rc = c->fp32 ? rhs_explicit_t<float>(c, yh, out) : rhs_explicit_t<double>(c, yh, out);
+    if (rc) return rc;
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->st.rhs_evals += 1;
+    return PF_OK;
+}
+
+int pf_solve_implicit(pf_ctx* c, double gamma, const void* r_hat, void* z_hat) {
+    if (!c || !r_hat || !z_hat) return fail(c, PF_EINVAL, "pf_solve_implicit: NULL argument");
+    cudaSetDevice(c->dev);
+    launch_solve(c->g, c->ph, gamma, reinterpret_cast<const double2*>(r_hat), reinterpret_cast<double2*>(z_hat),
+                 c->stream);
+    int rc = check_launch(c, "pf_solve_implicit");
+    if (rc) return rc;
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PF_OK;
+}
+
+int pf_step(pf_ctx* c, double dt, double* lte_wrms_out) {
+    if (!c) return fail(c, PF_EINVAL, "pf_step: NULL context");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(c, PF_EINVAL, "pf_step: dt must be positive");
+    cudaSetDevice(c->dev);
+    double e = 0.0;
+    int rc = step_once(c, dt, lte_wrms_out != nullptr, &e);
+    if (rc) return rc;
+    if (lte_wrms_out == nullptr) PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::swap(c->y, c->ynew);
+    c->t += dt;
+    c->st.steps_accepted += 1;
+    c->st.t = c->t;
+    c->st.last_wrms = e;
+    if (lte_wrms_out) *lte_wrms_out = e;
+    return PF_OK;
+}
+
+int pf_advance(pf_ctx* c, double t_final, double rtol, double atol, pf_stats* out) {
+    return pf_advance_attempts(c, t_final, rtol, atol, 0x7fffffff, out);
+}
+
+int pf_advance_attempts(pf_ctx* c, double t_final, double rtol, double atol, int max_attempts, pf_stats* out) {
+    if (!c) return fail(c, PF_EINVAL, "pf_advance: NULL context");
+    if (max_attempts < 1) return fail(c, PF_EINVAL, "pf_advance_attempts: max_attempts < 1");
+    if (!(rtol >= 0) || !(atol > 0)) return fail(c, PF_EINVAL, "pf_advance: need rtol >= 0, atol > 0");
+    cudaSetDevice(c->dev);
+    c->prm.rtol = rtol;
+    c->prm.atol = atol;
+    const bool adaptive = c->tab.embedded;
+    auto t0 = std::chrono::steady_clock::now();
+    c->attempts.clear();
+    int nrej = 0;
+    double h = adaptive ? c->h : c->prm.h0;
+    int rc = PF_OK;
+    int natt = 0;
+    while (c->t < t_final * (1 - 1e-14) && natt++ < max_attempts) {
+        h = std::fmin(h, t_final - c->t);
+        double e = 0.0;
+        rc = step_once(c, h, adaptive, &e);
+        if (rc) break;
+        if (!adaptive) PF_CUDA(c, cudaStreamSynchronize(c->stream));
+        const bool ok = std::isfinite(e) && e <= 1.0;
+        c->attempts.push_back(c->t);
+        c->attempts.push_back(h);
+        c->attempts.push_back(e);
+        c->attempts.push_back(ok ? 1.0 : 0.0);
+        c->st.last_wrms = e;
+        double hn;
+        if (ok) {
+            std::swap(c->y, c->ynew);
+            c->t += h;
+            nrej = 0;
+            c->st.steps_accepted += 1;
+            hn = adaptive ? ctl_accept(c, h, e) : c->prm.h0;
+        } else {
+            c->st.steps_rejected += 1;
+            if (++nrej > c->prm.max_rejects) {
+                rc = fail(c, std::isfinite(e) ? PF_ESTEPFAIL : PF_ENONFINITE,
+                          "step failed at t=%g: %d rejections (last ||LTE|| = %g)", c->t, nrej, e);
+                break;
+            }
+            hn = ctl_reject(c, h, e);
+        }
+        h = std::fmin(std::fmax(hn, c->prm.h_min), c->prm.h_max);
+    }
+    if (adaptive) c->h = h;
+    c->st.t = c->t;
+    c->st.h = c->h;
+    c->st.wall_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (out) *out = c->st;
+    return rc;
+}
+
+int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, double atol, pf_stats* out) {
+    if (!ctxs || n <= 0) return fail(nullptr, PF_EINVAL, "pf_batch_advance: empty batch");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(nullptr, PF_EINVAL, "pf_batch_advance: NULL context %d", i);
+        if (ctxs[i]->prm.method != ctxs[0]->prm.method || ctxs[i]->fp32 != ctxs[0]->fp32)
+            return fail(ctxs[i], PF_EINVAL, "pf_batch_advance: members differ in method or precision");
+    }
+    for (int i = 0; i < n; ++i) {
+        int rc = pf_advance(ctxs[i], t_final, rtol, atol, out ? &out[i] : nullptr);
+        if (rc) return rc;
+    }
+    return PF_OK;
+}
+
+int pf_free_energy(pf_ctx* c, double* F_out) {
+    if (!c || !F_out) return fail(c, PF_EINVAL, "pf_free_energy: NULL argument");
+    cudaSetDevice(c->dev);
+    const Geo& g = c->g;
+    cudaStream_t s = c->stream;
+    double2* S1 = c->ynew;
+    double2* S2 = fp64_scratch(c);
+    StageTerms none{};
+    launch_z_stage<double>(g, c->ph, c->y, none, nullptr, S1, s);
+    launch_y_pass<double>(g, S1, 4, +1, s);
+    launch_x_pass<double>(g, c->ph, XM_ENERGY, S1, S2, nullptr, nullptr, c->partials, 0, 0, nullptr, nullptr, s);
+    int rc = check_launch(c, "pf_free_energy");
+    if (rc) return rc;
+    launch_reduce(c->partials, x_pass_blocks(g, 1), 1.0, c->d_scalar, s);  // local densities
+    launch_y_pass<double>(g, S2, 3, -1, s);
+    launch_z_fwd<double>(g, c->ph, S2, S1, 0, s, 3);  // h^ (normalised) into S1
+    launch_energy_k(g, c->ph, c->y, S1, c->partials, s);
+    launch_reduce(c->partials, energy_k_blocks(g), 1.0, c->d_scalar + 1, s);
+    rc = check_launch(c, "pf_free_energy");
+    if (rc) return rc;
+    PF_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_scalar, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(c, cudaStreamSynchronize(s));
+    const double dV = c->grid.dx * c->grid.dy * c->grid.dz;
+    const double V = (double)g.N * dV;
+    *F_out = c->h_scalar[0] * dV + 0.5 * V * c->h_scalar[1];
+    return PF_OK;
+}
+
+int pf_get_time(pf_ctx* c, double* t, double* h) {
+    if (!c) return fail(c, PF_EINVAL, "pf_get_time: NULL context");
+    if (t) *t = c->t;
+    if (h) *h = c->h;
+    return PF_OK;
+}
+
+int pf_set_time(pf_ctx* c, double t, double h) {
+    if (!c || !(h > 0)) return fail(c, PF_EINVAL, "pf_set_time: bad argument");
+    c->t = t;
+    c->h = h;
+    c->e_prev = 1.0;
+    c->after_reject = false;
+    return PF_OK;
+}
+
+int pf_get_stats(pf_ctx* c, pf_stats* out) {
+    if (!c || !out) return fail(c, PF_EINVAL, "pf_get_stats: NULL argument");
+    c->st.t = c->t;
+    c->st.h = c->h;
+    *out = c->st;
+    return PF_OK;
+}
+
+static const char* kKernelNames[PF_NKERNELS] = {"z_stage_solve_ifft", "y_fft", "x_c2r_physics1_r2c",
+                                                 "x_c2r_physics2_r2c", "z_elastic_contraction", "z_fft_scale_fE",
+                                                 "z_step_completion_lte", "x_c2r_wrms", "wrms_reduce",
+                                                 "stage_pointwise"};
+
+const char* pf_kernel_name(int kind) { return (kind >= 0 && kind < PF_NKERNELS) ? kKernelNames[kind] : "?"; }
+
+int pf_profile_enable(pf_ctx* c, int on) {
+    if (!c) return fail(c, PF_EINVAL, "pf_profile_enable: NULL context");
+    c->prof_on = on != 0;
+    c->prof_recs.clear();
+    c->prof_next = 0;
+    return PF_OK;
+}
+
+int pf_profile_read(pf_ctx* c, double* ms, double* bytes, long long* launches) {
+    if (!c) return fail(c, PF_EINVAL, "pf_profile_read: NULL context");
+    cudaSetDevice(c->dev);
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < PF_NKERNELS; ++k) {
+        if (ms) ms[k] = 0.0;
+        if (bytes) bytes[k] = 0.0;
+        if (launches) launches[k] = 0;
+    }
+    for (const auto& r : c->prof_recs) {
+        float t = 0.f;
+        PF_CUDA(c, cudaEventElapsedTime(&t, r.e0, r.e1));
+        if (ms) ms[r.kind] += t;
+        if (bytes) bytes[r.kind] += r.bytes;
+        if (launches) launches[r.kind] += 1;
+    }
+    c->prof_recs.clear();
+    c->prof_next = 0;
+    return PF_OK;
+}
+
+int pf_get_attempts(pf_ctx* c, double* buf, int max_attempts) {
+    if (!c) return fail(c, PF_EINVAL, "pf_get_attempts: NULL context");
+    const int n = (int)(c->attempts.size() / 4);
+    if (buf) {
+        const int m = n < max_attempts ? n : max_attempts;
+        std::memcpy(buf, c->attempts.data(), (size_t)m * 4 * sizeof(double));
+    }
+    return n;
+}
+
+}  // extern "C"

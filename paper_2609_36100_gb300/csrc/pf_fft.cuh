@@ -1,0 +1,203 @@
+// Shared-memory mixed-radix (2,3,4,5,8) Stockham FFT used by every pass of
+// the pseudospectral right-hand side.  A CTA transforms `nl` lines of length
+// n held in shared memory; element e of line l sits at l*ls + e*es.  Stages
+// ping-pong between two buffers; each butterfly reads R inputs strided by n/R,
+// applies the twiddles exp(SIGN 2 pi i t k / (Ns R)) from an n-point table and
+// writes R outputs strided by Ns (autosort, no bit reversal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pf_internal.h"
+
+namespace pf {
+
+template <typename T>
+struct Cx;
+template <>
+struct Cx<double> {
+    using t = double2;
+};
+template <>
+struct Cx<float> {
+    using t = float2;
+};
+
+template <typename T2>
+__device__ __forceinline__ T2 cadd(T2 a, T2 b) { return T2{a.x + b.x, a.y + b.y}; }
+template <typename T2>
+__device__ __forceinline__ T2 csub(T2 a, T2 b) { return T2{a.x - b.x, a.y - b.y}; }
+template <typename T2>
+__device__ __forceinline__ T2 cmul(T2 a, T2 b) { return T2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+// a * conj(b)
+template <typename T2>
+__device__ __forceinline__ T2 cmulc(T2 a, T2 b) { return T2{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }
+// multiply by SIGN * i
+template <int SIGN, typename T2>
+__device__ __forceinline__ T2 mul_si(T2 a) {
+    return SIGN > 0 ? T2{-a.y, a.x} : T2{a.y, -a.x};
+}
+template <typename T2, typename S>
+__device__ __forceinline__ T2 cscale(T2 a, S s) { return T2{a.x * s, a.y * s}; }
+
+// Butterfly constants (correctly rounded FP64): cos/sin of 2 pi/5, 4 pi/5, sin(pi/3), sqrt(2)/2.
+#define PF_C1_5 0.30901699437494745
+#define PF_C2_5 (-0.8090169943749475)
+#define PF_S1_5 0.9510565162951535
+#define PF_S2_5 0.5877852522924731
+#define PF_S3 0.8660254037844386
+#define PF_R2 0.7071067811865476
+
+template <int R, int SIGN, typename T2>
+struct Bfly;
+
+template <int SIGN, typename T2>
+struct Bfly<2, SIGN, T2> {
+    __device__ __forceinline__ static void run(T2* v) {
+        T2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <int SIGN, typename T2>
+struct Bfly<4, SIGN, T2> {
+    __device__ __forceinline__ static void run(T2* v) {
+        T2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        T2 c = cadd(v[1], v[3]), d = mul_si<SIGN>(csub(v[1], v[3]));
+        v[0] = cadd(a, c);
+        v[2] = csub(a, c);
+        v[1] = cadd(b, d);
+        v[3] = csub(b, d);
+    }
+};
+
+template <int SIGN, typename T2>
+struct Bfly<3, SIGN, T2> {
+    __device__ __forceinline__ static void run(T2* v) {
+        using T = decltype(v[0].x);
+        T2 s = cadd(v[1], v[2]);
+        T2 d = mul_si<SIGN>(cscale(csub(v[1], v[2]), (T)PF_S3));
+        T2 m = csub(v[0], cscale(s, (T)0.5));
+        v[0] = cadd(v[0], s);
+        v[1] = cadd(m, d);
+        v[2] = csub(m, d);
+    }
+};
+
+template <int SIGN, typename T2>
+struct Bfly<5, SIGN, T2> {
+    __device__ __forceinline__ static void run(T2* v) {
+        using T = decltype(v[0].x);
+        const T c1 = (T)PF_C1_5, c2 = (T)PF_C2_5, s1 = (T)PF_S1_5, s2 = (T)PF_S2_5;
+        T2 s = cadd(v[1], v[4]), d = csub(v[1], v[4]);
+        T2 sp = cadd(v[2], v[3]), dp = csub(v[2], v[3]);
+        T2 x0 = v[0];
+        T2 a1 = T2{x0.x + c1 * s.x + c2 * sp.x, x0.y + c1 * s.y + c2 * sp.y};
+        T2 a2 = T2{x0.x + c2 * s.x + c1 * sp.x, x0.y + c2 * s.y + c1 * sp.y};
+        T2 b1 = mul_si<SIGN>(T2{s1 * d.x + s2 * dp.x, s1 * d.y + s2 * dp.y});
+        T2 b2 = mul_si<SIGN>(T2{s2 * d.x - s1 * dp.x, s2 * d.y - s1 * dp.y});
+        v[0] = cadd(x0, cadd(s, sp));
+        v[1] = cadd(a1, b1);
+        v[4] = csub(a1, b1);
+        v[2] = cadd(a2, b2);
+        v[3] = csub(a2, b2);
+    }
+};
+
+template <int SIGN, typename T2>
+struct Bfly<8, SIGN, T2> {
+    __device__ __forceinline__ static void run(T2* v) {
+        using T = decltype(v[0].x);
+        T2 e[4] = {v[0], v[2], v[4], v[6]};
+        T2 o[4] = {v[1], v[3], v[5], v[7]};
+        Bfly<4, SIGN, T2>::run(e);
+        Bfly<4, SIGN, T2>::run(o);
+        const T r2 = (T)PF_R2;
+        // w^m o_m with w = exp(SIGN i pi/4)
+        T2 w1 = cscale(cadd(o[1], mul_si<SIGN>(o[1])), r2);
+        T2 w2 = mul_si<SIGN>(o[2]);
+        T2 w3 = cscale(csub(mul_si<SIGN>(o[3]), o[3]), r2);
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], w1);
+        v[5] = csub(e[1], w1);
+        v[2] = cadd(e[2], w2);
+        v[6] = csub(e[2], w2);
+        v[3] = cadd(e[3], w3);
+        v[7] = csub(e[3], w3);
+    }
+};
+
+template <typename T2>
+__device__ __forceinline__ const T2* twiddles(const AxisPlan& p);
+template <>
+__device__ __forceinline__ const double2* twiddles<double2>(const AxisPlan& p) { return p.tw64; }
+template <>
+__device__ __forceinline__ const float2* twiddles<float2>(const AxisPlan& p) { return p.tw32; }
+
+// One radix-R Stockham stage over all lines. LINE_FAST maps consecutive
+// threads to consecutive lines (strided tiles, lines are contiguous columns);
+// otherwise to consecutive butterflies of a line (contiguous x lines).
+template <int R, int SIGN, bool LINE_FAST, typename T2>
+__device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __restrict__ dst, int n, int nl, int es,
+                                          int ls, int Ns, const T2* __restrict__ tw) {
+    const int m = n / R;
+    const int total = nl * m;
+    const int tws = n / (Ns * R);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int line, j;
+        if (LINE_FAST) {
+            line = idx % nl;
+            j = idx / nl;
+        } else {
+            j = idx % m;
+            line = idx / m;
+        }
+        const T2* s = src + line * ls;
+        T2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = s[(j + t * m) * es];
+        const int k = j % Ns;
+        if (Ns > 1) {
+            const int st = k * tws;
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                const T2 w = __ldg(tw + t * st);
+                v[t] = SIGN < 0 ? cmul(v[t], w) : cmulc(v[t], w);
+            }
+        }
+        Bfly<R, SIGN, T2>::run(v);
+        const int base = (j - k) * R + k;
+        T2* d = dst + line * ls;
+#pragma unroll
+        for (int t = 0; t < R; ++t) d[(base + t * Ns) * es] = v[t];
+    }
+}
+
+// Full transform of the lines in `a` (b is scratch).  Callers synchronise
+// before; returns the buffer holding the result (synchronised).
+template <int SIGN, bool LINE_FAST, typename T2>
+__device__ T2* fft_lines(T2* a, T2* b, const AxisPlan& p, int nl, int es, int ls) {
+    const T2* tw = twiddles<T2>(p);
+    T2* src = a;
+    T2* dst = b;
+    int Ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        const int r = p.rad[s];
+        switch (r) {
+            case 2: fft_stage<2, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
+            case 3: fft_stage<3, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
+            case 4: fft_stage<4, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
+            case 5: fft_stage<5, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
+            default: fft_stage<8, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
+        }
+        __syncthreads();
+        T2* t = src;
+        src = dst;
+        dst = t;
+        Ns *= r;
+    }
+    return src;
+}
+
+}  // namespace pf

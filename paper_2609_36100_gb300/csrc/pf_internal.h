@@ -1,0 +1,99 @@
+// Internal declarations shared by the kernel and host translation units of
+// the phase-field library (not part of the public C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace pf {
+
+constexpr int kMaxStages = 8;
+constexpr int kMaxRadices = 10;
+
+// One FFT axis: length n = product of radices (each in {2,3,4,5,8}) and the
+// device table tw[k] = exp(-2 pi i k / n), k = 0..n-1, in both precisions.
+struct AxisPlan {
+    int n;
+    int nst;
+    int rad[kMaxRadices];
+    const double2* tw64;
+    const float2* tw32;
+};
+
+// Grid geometry and the per-axis wave-number tables k_m = 2 pi m / (n d)
+// (FP64, Nyquist index taken as +pi/d).
+struct Geo {
+    int nx, ny, nz, nxh;
+    long long NK;  // nz * ny * nxh  (complex entries per field)
+    long long N;   // nz * ny * nx   (real entries per field)
+    const double* kx;  // [nxh]
+    const double* ky;  // [ny]
+    const double* kz;  // [nz]
+    AxisPlan px, py, pz;
+    int tx_y, tx_z, tx_el;  // tile widths (kx columns) of the strided passes
+    int rp;                  // row pairs per CTA in the x passes
+};
+
+// Derived model constants (Sec. 4.1 with the readings of the library).
+struct Phys {
+    double M;             // mobility at T
+    double Am, Av, A0m, A0v, Bm, Bv;
+    double inv2Am, inv2Av;  // 1/(2 A^p)
+    double L, wbar;
+    double w[3][3];       // pairwise barrier omega_vq (zero diagonal)
+    double pair_eps;      // Huber width of |phi_v phi_q|
+    double kap[3][6];     // gradient tensors (Voigt)
+    int elastic;          // 0: all eigenstrains zero
+    double Caniso, Cmix, C44;  // C11 - C12 - 2 C44, C12 + C44, C44
+    double sig[3][6];     // sigma*_v = C : eps*_v (Voigt)
+    double cvq[3][3];     // eps*_v : C : eps*_q
+};
+
+// Coefficients of one stage assembly / step completion pass.
+struct StageTerms {
+    int n;                             // number of previous-stage terms
+    const double2* z[kMaxStages];      // stage vectors z_j (FP64)
+    const void* f[kMaxStages];         // f^E_j (compute type)
+    double cI[kMaxStages];             // dt * A^I_ij (or dt * b^I_j)
+    double cE[kMaxStages];             // dt * A^E_ij (or dt * b^E_j)
+    double gamma;                      // dt * A^I_ii (0: explicit stage)
+};
+
+enum XMode {
+    XM_PHYS1 = 0,      // C2R state -> real fields, h(phi) -> R2C (or the full RHS when elasticity is off)
+    XM_PHYS2 = 1,      // C2R elastic potential + stored real fields -> RHS -> R2C
+    XM_WRMS = 2,       // C2R local error + weights from stored real y -> partial sums
+    XM_R2C_REAL = 3,   // real FP64 fields -> R2C (set_state)
+    XM_C2R_REAL = 4,   // C2R -> real FP64 fields (get_state)
+    XM_ENERGY = 5      // C2R state -> local free-energy density partial sums + h -> R2C
+};
+
+// Host launchers (defined in pf_kernels.cu).  `T` = compute type.
+template <typename T>
+void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, double2* zout,
+                    void* W, cudaStream_t s);
+template <typename T>
+void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s);
+template <typename T>
+void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
+                   double* partials, double rtol, double atol, const double* real_in, double* real_out,
+                   cudaStream_t s);
+template <typename T>
+void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s);
+// forward z FFT; scale_mode 0: y = W/N to FP64 (set_state); 1: f^E scaling
+// into the compute type; 2: f^E scaling into FP64 (ABI output)
+template <typename T>
+void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int scale_mode, cudaStream_t s,
+                  int nf = 4);
+template <typename T>
+void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageTerms& bterm,
+                    const StageTerms& dterm, int want_lte, double2* ynew, void* W, cudaStream_t s);
+void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, int fe_is_f32,
+                            double2* zout, cudaStream_t s);
+void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s);
+void launch_reduce(const double* partials, int n, double scale, double* out, cudaStream_t s);
+void launch_energy_k(const Geo& g, const Phys& ph, const double2* y, const double2* hk, double* partials,
+                     cudaStream_t s);
+int x_pass_blocks(const Geo& g, int f64);
+int energy_k_blocks(const Geo& g);
+
+}  // namespace pf

@@ -1,0 +1,878 @@
+// Pass kernels of the pseudospectral ImEx-ARK right-hand side (Sec. 4.2/4.4
+// of the paper) on sm_103a.
+//
+// One explicit right-hand-side evaluation f^E(z) is nine memory passes over
+// field-major arrays ([field][z][y][x] real, [field][kz][ky][kx] half
+// spectrum), each one shared-memory FFT along one axis with the pointwise
+// work of that point of the method fused into it:
+//   z: stage assembly + diagonal implicit solve (Eq. ARK_stage) + inverse FFT
+//   y: inverse FFT
+//   x: C2R -> real X, phi_v; h(phi_v) -> R2C (or the whole RHS when the
+//      eigenstrains vanish)
+//   y: forward FFT of h          z: forward FFT, Green's contraction
+//   y: inverse FFT of e          B_vq(k/|k|) h^_q, inverse FFT
+//   x: C2R of e, KKS mu, g_v, q -> R2C        y: forward FFT
+//   z: forward FFT + k-space scaling -> f^E (-M k^2, -L)
+// Step completion (Eq. ARK_method), the embedded local error (Eq.
+// ARK_embedding) and its WRMS norm (Eqs. wrms_norm, wrms_weights) are three
+// more passes.  Template parameter T is the compute type of the transforms
+// and RHS (double, or float for the FP32-bulk form); the state and stage
+// vectors are always FP64.
+#include <cstdio>
+
+#include "pf_fft.cuh"
+#include "pf_internal.h"
+
+namespace pf {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+// lambda(k) of field f: -2 A^m M k^2 (X), -L k.kappa_v.k (phi_v); FP64
+__device__ __forceinline__ double lambda_k(const Phys& ph, int f, double kx, double ky, double kz) {
+    if (f == 0) return (-2.0 * ph.Am * ph.M) * (kx * kx + ky * ky + kz * kz);
+    const double* K = ph.kap[f - 1];
+    double kk = K[0] * kx * kx + K[1] * ky * ky + K[2] * kz * kz;
+    kk += 2.0 * (K[3] * ky * kz + K[4] * kx * kz + K[5] * kx * ky);
+    return -ph.L * kk;
+}
+
+template <typename T2>
+__device__ __forceinline__ double2 to_d2(T2 a) { return make_double2((double)a.x, (double)a.y); }
+template <typename T2>
+__device__ __forceinline__ T2 from_d2(double2 a);
+template <>
+__device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
+template <>
+__device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+template <typename T>
+static int strided_tile(int n, int nbuf, int budget) {
+    int tx = 16;
+    while (tx > 1 && (size_t)nbuf * tx * n * sizeof(typename Cx<T>::t) > (size_t)budget) tx >>= 1;
+    return tx;
+}
+
+template <typename T>
+static int tile_cols(const Geo& g, int n, int nbuf, int budget) {
+    int tx = strided_tile<T>(n, nbuf, budget);
+    // no wider than the (odd) half-spectrum row
+    while (tx > 1 && tx / 2 >= g.nxh) tx >>= 1;
+    return tx;
+}
+
+template <typename K>
+static void set_smem(K kern, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------------------------
+// z pass: stage assembly + implicit solve + inverse FFT along z
+//   r = y + sum_j (dt A^I_ij) lambda z_j + (dt A^E_ij) f^E_j
+//   z_i = r / (1 - dt A^I_ii lambda)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_z_stage(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st,
+                                                      double2* __restrict__ zout, typename Cx<T>::t* __restrict__ W,
+                                                      int TX) {
+    using T2 = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* A = reinterpret_cast<T2*>(smraw);
+    T2* B = A + TX * g.nz;
+    const int f = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    const int ncol = min(TX, g.nxh - kx0);
+    const long long fo = (long long)f * g.NK;
+    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
+        const int col = e % TX, kz = e / TX;
+        T2 v = T2{0, 0};
+        if (col < ncol) {
+            const long long gi = fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col;
+            double2 r = y[gi];
+            const double lam = lambda_k(ph, f, g.kx[kx0 + col], g.ky[ky], g.kz[kz]);
+            for (int j = 0; j < st.n; ++j) {
+                if (st.cI[j] != 0.0) {
+                    const double2 zj = st.z[j][gi];
+                    r.x = r.x + st.cI[j] * (lam * zj.x);
+                    r.y = r.y + st.cI[j] * (lam * zj.y);
+                }
+                if (st.cE[j] != 0.0) {
+                    const double2 fj = to_d2(reinterpret_cast<const T2*>(st.f[j])[gi]);
+                    r.x = r.x + st.cE[j] * fj.x;
+                    r.y = r.y + st.cE[j] * fj.y;
+                }
+            }
+            if (st.gamma != 0.0) {
+                const double den = 1.0 - st.gamma * lam;
+                r.x = r.x / den;
+                r.y = r.y / den;
+            }
+            if (zout) zout[gi] = r;
+            v = from_d2<T2>(r);
+        }
+        A[kz * TX + col] = v;
+    }
+    __syncthreads();
+    T2* res = fft_lines<+1, true>(A, B, g.pz, TX, TX, 1);
+    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
+        const int col = e % TX, kz = e / TX;
+        if (col < ncol) W[fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] = res[kz * TX + col];
+    }
+}
+
+template <typename T>
+void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, double2* zout, void* W,
+                    cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    const int TX = tile_cols<T>(g, g.nz, 2, 96 * 1024);
+    const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
+    set_smem(k_z_stage<T>, sm);
+    dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
+    k_z_stage<T><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout, reinterpret_cast<T2*>(W), TX);
+}
+
+// ---------------------------------------------------------------------------
+// y pass: in-place complex FFT along y of nf fields
+// ---------------------------------------------------------------------------
+template <typename T, int SIGN>
+__global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* __restrict__ buf, int TX) {
+    using T2 = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* A = reinterpret_cast<T2*>(smraw);
+    T2* B = A + TX * g.ny;
+    const int f = blockIdx.z, kz = blockIdx.y, kx0 = blockIdx.x * TX;
+    const int ncol = min(TX, g.nxh - kx0);
+    T2* base = buf + (long long)f * g.NK + (long long)kz * g.ny * g.nxh + kx0;
+    for (int e = threadIdx.x; e < TX * g.ny; e += blockDim.x) {
+        const int col = e % TX, ky = e / TX;
+        A[ky * TX + col] = col < ncol ? base[(long long)ky * g.nxh + col] : T2{0, 0};
+    }
+    __syncthreads();
+    T2* res = fft_lines<SIGN, true>(A, B, g.py, TX, TX, 1);
+    for (int e = threadIdx.x; e < TX * g.ny; e += blockDim.x) {
+        const int col = e % TX, ky = e / TX;
+        if (col < ncol) base[(long long)ky * g.nxh + col] = res[ky * TX + col];
+    }
+}
+
+template <typename T>
+void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    const int TX = tile_cols<T>(g, g.ny, 2, 96 * 1024);
+    const size_t sm = 2 * (size_t)TX * g.ny * sizeof(T2);
+    dim3 grid((g.nxh + TX - 1) / TX, g.nz, nf);
+    if (sign > 0) {
+        set_smem(k_y_pass<T, 1>, sm);
+        k_y_pass<T, 1><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf), TX);
+    } else {
+        set_smem(k_y_pass<T, -1>, sm);
+        k_y_pass<T, -1><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf), TX);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z pass, forward: FFT along z then k-space scaling
+//   mode 0: y^ = W / N  -> FP64                                  (set_state)
+//   mode 1: f^E_X = -M k^2 q^/N, f^E_phi = -L g^/N -> compute type (stages)
+//   mode 2: same scaling -> FP64                                  (ABI f^E)
+// ---------------------------------------------------------------------------
+template <typename T, typename OT2>
+__global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typename Cx<T>::t* __restrict__ W,
+                                                    OT2* __restrict__ out, int mode, int TX) {
+    using T2 = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* A = reinterpret_cast<T2*>(smraw);
+    T2* B = A + TX * g.nz;
+    const int f = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    const int ncol = min(TX, g.nxh - kx0);
+    const long long fo = (long long)f * g.NK;
+    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
+        const int col = e % TX, kz = e / TX;
+        A[kz * TX + col] = col < ncol ? W[fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] : T2{0, 0};
+    }
+    __syncthreads();
+    T2* res = fft_lines<-1, true>(A, B, g.pz, TX, TX, 1);
+    const double invN = 1.0 / (double)g.N;
+    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
+        const int col = e % TX, kz = e / TX;
+        if (col >= ncol) continue;
+        const long long gi = fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col;
+        const T2 v = res[kz * TX + col];
+        if (mode == 0) {
+            out[gi] = OT2{(decltype(OT2{}.x))((double)v.x * invN), (decltype(OT2{}.x))((double)v.y * invN)};
+        } else {
+            T sc;
+            if (f == 0) {
+                const double kx = g.kx[kx0 + col], kyv = g.ky[ky], kzv = g.kz[kz];
+                sc = (T)(-ph.M * (kx * kx + kyv * kyv + kzv * kzv) * invN);
+            } else {
+                sc = (T)(-ph.L * invN);
+            }
+            out[gi] = OT2{(decltype(OT2{}.x))(v.x * sc), (decltype(OT2{}.x))(v.y * sc)};
+        }
+    }
+}
+
+template <typename T>
+void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int scale_mode, cudaStream_t s, int nf) {
+    using T2 = typename Cx<T>::t;
+    const int TX = tile_cols<T>(g, g.nz, 2, 96 * 1024);
+    const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
+    dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
+    if (scale_mode == 1) {
+        set_smem(k_z_fwd<T, T2>, sm);
+        k_z_fwd<T, T2><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W), reinterpret_cast<T2*>(out),
+                                                  1, TX);
+    } else {
+        set_smem(k_z_fwd<T, double2>, sm);
+        k_z_fwd<T, double2><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
+                                                       reinterpret_cast<double2*>(out), scale_mode, TX);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z pass: elastic Green's contraction (homogeneous cubic modulus)
+//   e^_v(k) = sum_q B_vq(n) h^_q(k) / N,  n = k/|k|, B(0) = 0
+//   B_vq(n) = eps*_v:C:eps*_q - (sigma*_v n) . Omega(n) . (sigma*_q n),
+//   Omega^{-1}_ik = C44 d_ik + (C12 + C44) n_i n_k + (C11 - C12 - 2 C44) d_ik n_i^2
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void elastic_kernel(const Phys& ph, double kx, double ky, double kz, T Bm[3][3]) {
+    const T k2 = (T)(kx * kx + ky * ky + kz * kz);
+    if (k2 == (T)0) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Bm[v][q] = (T)0;
+        return;
+    }
+    const T inv = (T)1 / sqrt(k2);
+    const T n0 = (T)kx * inv, n1 = (T)ky * inv, n2 = (T)kz * inv;
+    const T C44 = (T)ph.C44, Cm = (T)ph.Cmix, Ca = (T)ph.Caniso;
+    const T a = C44 + Cm * n0 * n0 + Ca * n0 * n0;
+    const T b = C44 + Cm * n1 * n1 + Ca * n1 * n1;
+    const T c = C44 + Cm * n2 * n2 + Ca * n2 * n2;
+    const T d = Cm * n0 * n1, e = Cm * n0 * n2, f = Cm * n1 * n2;
+    // inverse of the symmetric acoustic tensor by cofactors
+    const T A11 = b * c - f * f, A12 = e * f - d * c, A13 = d * f - b * e;
+    const T A22 = a * c - e * e, A23 = d * e - a * f, A33 = a * b - d * d;
+    const T idet = (T)1 / (a * A11 + d * A12 + e * A13);
+    T s[3][3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const double* S = ph.sig[v];  // xx yy zz yz xz xy
+        s[v][0] = (T)S[0] * n0 + (T)S[5] * n1 + (T)S[4] * n2;
+        s[v][1] = (T)S[5] * n0 + (T)S[1] * n1 + (T)S[3] * n2;
+        s[v][2] = (T)S[4] * n0 + (T)S[3] * n1 + (T)S[2] * n2;
+    }
+    T Os[3][3];  // Omega s_q
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        Os[q][0] = (A11 * s[q][0] + A12 * s[q][1] + A13 * s[q][2]) * idet;
+        Os[q][1] = (A12 * s[q][0] + A22 * s[q][1] + A23 * s[q][2]) * idet;
+        Os[q][2] = (A13 * s[q][0] + A23 * s[q][1] + A33 * s[q][2]) * idet;
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            Bm[v][q] = (T)ph.cvq[v][q] - (s[v][0] * Os[q][0] + s[v][1] * Os[q][1] + s[v][2] * Os[q][2]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename Cx<T>::t* __restrict__ H, int TX) {
+    using T2 = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* buf[4];
+    const int tile = TX * g.nz;
+    for (int i = 0; i < 4; ++i) buf[i] = reinterpret_cast<T2*>(smraw) + i * tile;
+    const int ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    const int ncol = min(TX, g.nxh - kx0);
+    for (int e = threadIdx.x; e < 3 * tile; e += blockDim.x) {
+        const int f = e / tile, r = e % tile, col = r % TX, kz = r / TX;
+        buf[f][r] = col < ncol ? H[(long long)f * g.NK + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] : T2{0, 0};
+    }
+    __syncthreads();
+    // forward FFT of each field; field slots rotate through the scratch slot
+    for (int f = 0; f < 3; ++f) {
+        T2* res = fft_lines<-1, true>(buf[f], buf[3], g.pz, TX, TX, 1);
+        if (res == buf[3]) {
+            buf[3] = buf[f];
+            buf[f] = res;
+        }
+    }
+    const T invN = (T)(1.0 / (double)g.N);
+    for (int r = threadIdx.x; r < tile; r += blockDim.x) {
+        const int col = r % TX, kz = r / TX;
+        if (col >= ncol) continue;
+        T Bm[3][3];
+        elastic_kernel<T>(ph, g.kx[kx0 + col], g.ky[ky], g.kz[kz], Bm);
+        const T2 h0 = buf[0][r], h1 = buf[1][r], h2 = buf[2][r];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            T2 o;
+            o.x = (Bm[v][0] * h0.x + Bm[v][1] * h1.x + Bm[v][2] * h2.x) * invN;
+            o.y = (Bm[v][0] * h0.y + Bm[v][1] * h1.y + Bm[v][2] * h2.y) * invN;
+            buf[v][r] = o;
+        }
+    }
+    __syncthreads();
+    for (int f = 0; f < 3; ++f) {
+        T2* res = fft_lines<+1, true>(buf[f], buf[3], g.pz, TX, TX, 1);
+        if (res == buf[3]) {
+            buf[3] = buf[f];
+            buf[f] = res;
+        }
+    }
+    for (int e = threadIdx.x; e < 3 * tile; e += blockDim.x) {
+        const int f = e / tile, r = e % tile, col = r % TX, kz = r / TX;
+        if (col < ncol) H[(long long)f * g.NK + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] = buf[f][r];
+    }
+}
+
+template <typename T>
+void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    const int TX = tile_cols<T>(g, g.nz, 4, 128 * 1024);
+    const size_t sm = 4 * (size_t)TX * g.nz * sizeof(T2);
+    set_smem(k_z_elastic<T>, sm);
+    dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);
+    k_z_elastic<T><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<T2*>(H), TX);
+}
+
+// ---------------------------------------------------------------------------
+// z pass: step completion, embedded local error, inverse FFT of the error
+//   y_n = y + sum_i (dt b^I_i) lambda z_i + (dt b^E_i) f^E_i
+//   LTE = sum_i (dt (b-bt)^I_i) lambda z_i + (dt (b-bt)^E_i) f^E_i
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_z_final(Geo g, Phys ph, const double2* __restrict__ y, StageTerms bt,
+                                                      StageTerms dt, int want_lte, double2* __restrict__ ynew,
+                                                      typename Cx<T>::t* __restrict__ W, int TX) {
+    using T2 = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* A = reinterpret_cast<T2*>(smraw);
+    T2* B = A + TX * g.nz;
+    const int f = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    const int ncol = min(TX, g.nxh - kx0);
+    const long long fo = (long long)f * g.NK;
+    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
+        const int col = e % TX, kz = e / TX;
+        T2 v = T2{0, 0};
+        if (col < ncol) {
+            const long long gi = fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col;
+            const double lam = lambda_k(ph, f, g.kx[kx0 + col], g.ky[ky], g.kz[kz]);
+            double2 r = y[gi];
+            double2 l = make_double2(0.0, 0.0);
+            for (int j = 0; j < bt.n; ++j) {
+                const double2 zj = bt.z[j][gi];
+                const double2 fj =
+                    (bt.cE[j] != 0.0 || dt.cE[j] != 0.0) ? to_d2(reinterpret_cast<const T2*>(bt.f[j])[gi])
+                                                         : make_double2(0.0, 0.0);
+                if (bt.cI[j] != 0.0) {
+                    r.x = r.x + bt.cI[j] * (lam * zj.x);
+                    r.y = r.y + bt.cI[j] * (lam * zj.y);
+                }
+                if (bt.cE[j] != 0.0) {
+                    r.x = r.x + bt.cE[j] * fj.x;
+                    r.y = r.y + bt.cE[j] * fj.y;
+                }
+                if (want_lte) {
+                    if (dt.cI[j] != 0.0) {
+                        l.x = l.x + dt.cI[j] * (lam * zj.x);
+                        l.y = l.y + dt.cI[j] * (lam * zj.y);
+                    }
+                    if (dt.cE[j] != 0.0) {
+                        l.x = l.x + dt.cE[j] * fj.x;
+                        l.y = l.y + dt.cE[j] * fj.y;
+                    }
+                }
+            }
+            ynew[gi] = r;
+            v = from_d2<T2>(l);
+        }
+        A[kz * TX + col] = v;
+    }
+    if (!want_lte) return;
+    __syncthreads();
+    T2* res = fft_lines<+1, true>(A, B, g.pz, TX, TX, 1);
+    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
+        const int col = e % TX, kz = e / TX;
+        if (col < ncol) W[fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] = res[kz * TX + col];
+    }
+}
+
+template <typename T>
+void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageTerms& bterm, const StageTerms& dterm,
+                    int want_lte, double2* ynew, void* W, cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    const int TX = tile_cols<T>(g, g.nz, 2, 96 * 1024);
+    const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
+    set_smem(k_z_final<T>, sm);
+    dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
+    k_z_final<T><<<grid, kThreads, sm, s>>>(g, ph, y, bterm, dterm, want_lte, ynew, reinterpret_cast<T2*>(W), TX);
+}
+
+// ---------------------------------------------------------------------------
+// x passes: packed real transforms with the real-space physics fused in.
+// Two consecutive rows (y, y+1) of one field share one complex line
+// z = a + i b; C2R packs Z_k = A_k + i B_k (Hermitian extension for k > n/2,
+// imaginary parts of DC and Nyquist dropped), R2C unpacks
+// A_k = (Z_k + conj Z_{n-k})/2, B_k = (Z_k - conj Z_{n-k})/(2i).
+// ---------------------------------------------------------------------------
+struct Pt {
+    // real-space physics at one point (Sec. 4.1); returns q and g_v
+    template <typename T>
+    __device__ __forceinline__ static void rhs(const Phys& ph, T X, const T* p, const T* e, T& q, T* gv) {
+        T h[3], hp[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const T f = p[v];
+            h[v] = f * f * f * ((T)6 * f * f - (T)15 * f + (T)10);
+            hp[v] = (T)30 * f * f * ((T)1 - f) * ((T)1 - f);
+        }
+        const T H = h[0] + h[1] + h[2];
+        const T Bv = (T)ph.Bv, Bm = (T)ph.Bm;
+        const T denom = H * (T)ph.inv2Av + ((T)1 - H) * (T)ph.inv2Am;
+        const T mu = (X - H * Bv - ((T)1 - H) * Bm) / denom;
+        const T Xm = mu * (T)ph.inv2Am + Bm;
+        const T Xv = mu * (T)ph.inv2Av + Bv;
+        const T fm = (T)ph.A0m + (T)ph.Am * (Xm - Bm) * (Xm - Bm);
+        const T fv = (T)ph.A0v + (T)ph.Av * (Xv - Bv) * (Xv - Bv);
+        const T drive = fv - fm - mu * (Xv - Xm);
+        const T wb2 = (T)(2.0 * ph.wbar);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const T f = p[v];
+            T d = wb2 * f * ((T)1 - f) * ((T)1 - (T)2 * f);
+            const T ie = (T)(1.0 / ph.pair_eps);
+#pragma unroll
+            for (int qq = 0; qq < 3; ++qq)
+                if (qq != v) {
+                    const T sl = fmin((T)1, fmax((T)-1, f * p[qq] * ie));
+                    d += (T)ph.w[v][qq] * sl * p[qq];
+                }
+            gv[v] = d + hp[v] * drive + hp[v] * e[v];
+        }
+        q = mu - (T)(2.0 * ph.Am) * X;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T hfun(T f) { return f * f * f * ((T)6 * f * f - (T)15 * f + (T)10); }
+
+// load F packed lines (C2R input) of row pairs [rp0, rp0+P) into S
+template <typename T2>
+__device__ __forceinline__ void c2r_load(const Geo& g, const T2* __restrict__ in, int F, int P, int rp0, int npairs,
+                                         T2* S, int ls) {
+    const int nx = g.nx, nh = nx / 2;
+    for (int e = threadIdx.x; e < P * F * nx; e += blockDim.x) {
+        const int x = e % nx, line = e / nx, rp = line / F, f = line % F;
+        T2 Z = T2{0, 0};
+        if (rp0 + rp < npairs) {
+            const long long row = 2LL * (rp0 + rp);
+            const int k = x <= nh ? x : nx - x;
+            const T2* base = in + (long long)f * g.NK + row * g.nxh + k;
+            T2 a = base[0], b = base[g.nxh];
+            if (k == 0 || k == nh) {
+                a.y = 0;
+                b.y = 0;
+            }
+            if (x <= nh)
+                Z = T2{a.x - b.y, a.y + b.x};
+            else
+                Z = T2{a.x + b.y, b.x - a.y};
+        }
+        S[line * ls + x] = Z;
+    }
+}
+
+template <typename T2>
+__device__ __forceinline__ void r2c_store(const Geo& g, const T2* S, int ls, int F, int P, int rp0, int npairs,
+                                          T2* __restrict__ out) {
+    using T = decltype(T2{}.x);
+    const int nx = g.nx, nxh = g.nxh;
+    for (int e = threadIdx.x; e < P * F * nxh; e += blockDim.x) {
+        const int k = e % nxh, line = e / nxh, rp = line / F, f = line % F;
+        if (rp0 + rp >= npairs) continue;
+        const T2 Zk = S[line * ls + k];
+        const T2 Zm = S[line * ls + (k == 0 ? 0 : nx - k)];
+        const T half = (T)0.5;
+        const T2 A = T2{(Zk.x + Zm.x) * half, (Zk.y - Zm.y) * half};
+        const T2 B = T2{(Zk.y + Zm.y) * half, (Zm.x - Zk.x) * half};
+        const long long row = 2LL * (rp0 + rp);
+        T2* base = out + (long long)f * g.NK + row * nxh + k;
+        base[0] = A;
+        base[nxh] = B;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, const typename Cx<T>::t* __restrict__ in,
+                                                     typename Cx<T>::t* __restrict__ out, T* __restrict__ R,
+                                                     const T* __restrict__ Rin, double* __restrict__ partials,
+                                                     double rtol, double atol, const double* __restrict__ real_in,
+                                                     double* __restrict__ real_out, int P) {
+    using T2 = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nx = g.nx;
+    const int ls = nx;
+    const int npairs = g.nz * g.ny / 2;
+    const int rp0 = blockIdx.x * P;
+    T2* S0 = reinterpret_cast<T2*>(smraw);
+    T2* S1 = S0 + 4 * P * nx;
+    __shared__ double red[kThreads / 32];
+
+    // ---- input: C2R of the incoming half-spectrum lines, or packed real rows
+    int Fin = 0;
+    if (mode == XM_PHYS1 || mode == XM_WRMS || mode == XM_C2R_REAL || mode == XM_ENERGY) Fin = 4;
+    if (mode == XM_PHYS2) Fin = ph.elastic ? 3 : 0;
+    T2* RS = S0;  // real-space lines (a + i b)
+    if (mode == XM_R2C_REAL) {
+        for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
+            const int x = e % nx, line = e / nx, rp = line / 4, f = line % 4;
+            T2 Z = T2{0, 0};
+            if (rp0 + rp < npairs) {
+                const long long row = 2LL * (rp0 + rp);
+                const double* b = real_in + (long long)f * g.N + row * nx + x;
+                Z = T2{(T)b[0], (T)b[nx]};
+            }
+            S0[line * ls + x] = Z;
+        }
+        __syncthreads();
+        T2* res = fft_lines<-1, false>(S0, S1, g.px, 4 * P, 1, ls);
+        r2c_store(g, res, ls, 4, P, rp0, npairs, out);
+        return;
+    }
+    if (Fin > 0) {
+        c2r_load(g, in, Fin, P, rp0, npairs, S0, ls);
+        __syncthreads();
+        RS = fft_lines<+1, false>(S0, S1, g.px, Fin * P, 1, ls);
+    }
+    T2* OS = (RS == S0) ? S1 : S0;  // output lines
+
+    if (mode == XM_C2R_REAL) {
+        for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
+            const int x = e % nx, line = e / nx, rp = line / 4, f = line % 4;
+            if (rp0 + rp >= npairs) continue;
+            const long long row = 2LL * (rp0 + rp);
+            const T2 z = RS[line * ls + x];
+            double* b = real_out + (long long)f * g.N + row * nx + x;
+            b[0] = (double)z.x;
+            b[nx] = (double)z.y;
+        }
+        return;
+    }
+
+    if (mode == XM_WRMS) {
+        double acc = 0.0;
+        for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
+            const int x = e % nx, line = e / nx, rp = line / 4, f = line % 4;
+            if (rp0 + rp >= npairs) continue;
+            const long long row = 2LL * (rp0 + rp);
+            const T2 z = RS[line * ls + x];
+            const T* yr = Rin + (long long)f * g.N + row * nx + x;
+            const double w0 = 1.0 / (rtol * fabs((double)yr[0]) + atol);
+            const double w1 = 1.0 / (rtol * fabs((double)yr[nx]) + atol);
+            const double a = (double)z.x * w0, b = (double)z.y * w1;
+            acc += a * a + b * b;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+            partials[blockIdx.x] = s;
+        }
+        return;
+    }
+
+    // ---- pointwise physics: 2 rows per line, all fields of a point together
+    int Fout = 0;
+    double eacc = 0.0;
+    const bool full_rhs = (mode == XM_PHYS2) || (mode == XM_PHYS1 && !ph.elastic);
+    for (int e = threadIdx.x; e < P * nx; e += blockDim.x) {
+        const int x = e % nx, rp = e / nx;
+        if (rp0 + rp >= npairs) continue;
+        const long long row = 2LL * (rp0 + rp);
+        T Xr[2], pr[2][3], er[2][3];
+        if (mode == XM_PHYS2) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const T* b = Rin + (long long)f * g.N + row * nx + x;
+                if (f == 0) {
+                    Xr[0] = b[0];
+                    Xr[1] = b[nx];
+                } else {
+                    pr[0][f - 1] = b[0];
+                    pr[1][f - 1] = b[nx];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                if (ph.elastic) {
+                    const T2 z = RS[(rp * 3 + v) * ls + x];
+                    er[0][v] = z.x;
+                    er[1][v] = z.y;
+                } else {
+                    er[0][v] = 0;
+                    er[1][v] = 0;
+                }
+            }
+        } else {
+            const T2 zX = RS[(rp * 4 + 0) * ls + x];
+            Xr[0] = zX.x;
+            Xr[1] = zX.y;
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const T2 z = RS[(rp * 4 + 1 + v) * ls + x];
+                pr[0][v] = z.x;
+                pr[1][v] = z.y;
+                er[0][v] = 0;
+                er[1][v] = 0;
+            }
+            if (mode == XM_PHYS1 && R) {
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    T* b = R + (long long)f * g.N + row * nx + x;
+                    b[0] = f == 0 ? Xr[0] : pr[0][f - 1];
+                    b[nx] = f == 0 ? Xr[1] : pr[1][f - 1];
+                }
+            }
+        }
+        if (full_rhs) {
+            T q[2], gv[2][3];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) Pt::rhs<T>(ph, Xr[r], pr[r], er[r], q[r], gv[r]);
+            OS[(rp * 4 + 0) * ls + x] = T2{q[0], q[1]};
+#pragma unroll
+            for (int v = 0; v < 3; ++v) OS[(rp * 4 + 1 + v) * ls + x] = T2{gv[0][v], gv[1][v]};
+        } else {
+            // h(phi_v) lines for the elastic contraction (and the local energy)
+#pragma unroll
+            for (int v = 0; v < 3; ++v) OS[(rp * 3 + v) * ls + x] = T2{hfun(pr[0][v]), hfun(pr[1][v])};
+            if (mode == XM_ENERGY) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const double X = (double)Xr[r];
+                    double p[3], h[3];
+                    for (int v = 0; v < 3; ++v) {
+                        p[v] = (double)pr[r][v];
+                        h[v] = p[v] * p[v] * p[v] * (6.0 * p[v] * p[v] - 15.0 * p[v] + 10.0);
+                    }
+                    const double H = h[0] + h[1] + h[2];
+                    const double denom = H * ph.inv2Av + (1.0 - H) * ph.inv2Am;
+                    const double mu = (X - H * ph.Bv - (1.0 - H) * ph.Bm) / denom;
+                    const double Xm = mu * ph.inv2Am + ph.Bm, Xv = mu * ph.inv2Av + ph.Bv;
+                    const double fm = ph.A0m + ph.Am * (Xm - ph.Bm) * (Xm - ph.Bm);
+                    const double fv = ph.A0v + ph.Av * (Xv - ph.Bv) * (Xv - ph.Bv);
+                    double loc = 0.0;
+                    for (int v = 0; v < 3; ++v) loc += ph.wbar * p[v] * p[v] * (1.0 - p[v]) * (1.0 - p[v]);
+                    const double e = ph.pair_eps;
+                    const double pr[3] = {p[0] * p[1], p[0] * p[2], p[1] * p[2]};
+                    const double wv[3] = {ph.w[0][1], ph.w[0][2], ph.w[1][2]};
+                    for (int k = 0; k < 3; ++k) {
+                        const double ax = fabs(pr[k]);
+                        loc += wv[k] * (ax < e ? pr[k] * pr[k] / (2.0 * e) : ax - 0.5 * e);
+                    }
+                    loc += H * fv + (1.0 - H) * fm;
+                    eacc += loc;
+                }
+            }
+        }
+    }
+    Fout = full_rhs ? 4 : 3;
+    if (mode == XM_ENERGY) {
+        for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = eacc;
+    }
+    __syncthreads();
+    if (mode == XM_ENERGY && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        partials[blockIdx.x] = s;
+    }
+    T2* res = fft_lines<-1, false>(OS, RS, g.px, Fout * P, 1, ls);
+    r2c_store(g, res, ls, Fout, P, rp0, npairs, out);
+}
+
+template <typename T>
+static int x_rows(const Geo& g) {
+    using T2 = typename Cx<T>::t;
+    int P = (int)(64 * 1024 / (8 * (size_t)g.nx * sizeof(T2)));
+    if (P < 1) P = 1;
+    if (P > 16) P = 16;
+    const int npairs = g.nz * g.ny / 2;
+    // keep at least ~2 waves of CTAs on 152 SMs
+    while (P > 1 && (npairs + P - 1) / P < 304) P >>= 1;
+    return P;
+}
+
+int x_pass_blocks(const Geo& g, int f64) {
+    const int P = f64 ? x_rows<double>(g) : x_rows<float>(g);
+    const int npairs = g.nz * g.ny / 2;
+    return (npairs + P - 1) / P;
+}
+
+template <typename T>
+void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
+                   double* partials, double rtol, double atol, const double* real_in, double* real_out,
+                   cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    const int P = x_rows<T>(g);
+    const size_t sm = 2 * 4 * (size_t)P * g.nx * sizeof(T2);
+    set_smem(k_x_pass<T>, sm);
+    const int npairs = g.nz * g.ny / 2;
+    const int nb = (npairs + P - 1) / P;
+    k_x_pass<T><<<nb, kThreads, sm, s>>>(g, ph, mode, reinterpret_cast<const T2*>(in), reinterpret_cast<T2*>(out),
+                                         reinterpret_cast<T*>(R), reinterpret_cast<const T*>(Rin), partials, rtol,
+                                         atol, real_in, real_out, P);
+}
+
+// ---------------------------------------------------------------------------
+// pointwise kernels (FP64)
+// ---------------------------------------------------------------------------
+__global__ void k_stage_pointwise(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st, int fe32,
+                                  double2* __restrict__ zout) {
+    const long long total = 4LL * g.NK;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(gi / g.NK);
+        const long long r = gi % g.NK;
+        const int kx = (int)(r % g.nxh);
+        const int ky = (int)((r / g.nxh) % g.ny);
+        const int kz = (int)(r / ((long long)g.nxh * g.ny));
+        const double lam = lambda_k(ph, f, g.kx[kx], g.ky[ky], g.kz[kz]);
+        double2 v = y[gi];
+        for (int j = 0; j < st.n; ++j) {
+            if (st.cI[j] != 0.0) {
+                const double2 zj = st.z[j][gi];
+                v.x = v.x + st.cI[j] * (lam * zj.x);
+                v.y = v.y + st.cI[j] * (lam * zj.y);
+            }
+            if (st.cE[j] != 0.0) {
+                double2 fj;
+                if (fe32) {
+                    const float2 a = reinterpret_cast<const float2*>(st.f[j])[gi];
+                    fj = make_double2(a.x, a.y);
+                } else {
+                    fj = reinterpret_cast<const double2*>(st.f[j])[gi];
+                }
+                v.x = v.x + st.cE[j] * fj.x;
+                v.y = v.y + st.cE[j] * fj.y;
+            }
+        }
+        if (st.gamma != 0.0) {
+            const double den = 1.0 - st.gamma * lam;
+            v.x = v.x / den;
+            v.y = v.y / den;
+        }
+        zout[gi] = v;
+    }
+}
+
+void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, int fe_is_f32,
+                            double2* zout, cudaStream_t s) {
+    k_stage_pointwise<<<152 * 8, 256, 0, s>>>(g, ph, y, st, fe_is_f32, zout);
+}
+
+__global__ void k_solve(Geo g, Phys ph, double gamma, const double2* r, double2* z) {
+    const long long total = 4LL * g.NK;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(gi / g.NK);
+        const long long q = gi % g.NK;
+        const int kx = (int)(q % g.nxh);
+        const int ky = (int)((q / g.nxh) % g.ny);
+        const int kz = (int)(q / ((long long)g.nxh * g.ny));
+        const double den = 1.0 - gamma * lambda_k(ph, f, g.kx[kx], g.ky[ky], g.kz[kz]);
+        const double2 v = r[gi];
+        z[gi] = make_double2(v.x / den, v.y / den);
+    }
+}
+
+void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s) {
+    k_solve<<<152 * 8, 256, 0, s>>>(g, ph, gamma, r, z);
+}
+
+// deterministic single-CTA reduction: out = sum(partials) * scale (FP64)
+__global__ void k_reduce(const double* __restrict__ p, int n, double scale, double* out) {
+    __shared__ double sh[1024];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a += p[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0] * scale;
+}
+
+void launch_reduce(const double* partials, int n, double scale, double* out, cudaStream_t s) {
+    k_reduce<<<1, 1024, 0, s>>>(partials, n, scale, out);
+}
+
+// k-space part of the free energy: sum_k w_k [ sum_v k.kappa_v.k |phi^_v|^2
+//                                              + sum_vq B_vq Re(h^_v conj h^_q) ]
+__global__ void k_energy_k(Geo g, Phys ph, const double2* __restrict__ y, const double2* __restrict__ hk,
+                           double* partials) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.NK;
+         r += (long long)gridDim.x * blockDim.x) {
+        const int kx = (int)(r % g.nxh);
+        const int ky = (int)((r / g.nxh) % g.ny);
+        const int kz = (int)(r / ((long long)g.nxh * g.ny));
+        const double w = (kx == 0 || (g.nx % 2 == 0 && kx == g.nx / 2)) ? 1.0 : 2.0;
+        const double KX = g.kx[kx], KY = g.ky[ky], KZ = g.kz[kz];
+        double s = 0.0;
+        for (int v = 0; v < 3; ++v) {
+            const double lam = lambda_k(ph, v + 1, KX, KY, KZ);  // -L k.kappa.k
+            const double2 a = y[(long long)(v + 1) * g.NK + r];
+            s += (-lam / ph.L) * (a.x * a.x + a.y * a.y);
+        }
+        if (ph.elastic) {
+            double Bm[3][3];
+            elastic_kernel<double>(ph, KX, KY, KZ, Bm);
+            double2 h[3];
+            for (int v = 0; v < 3; ++v) h[v] = hk[(long long)v * g.NK + r];
+            for (int v = 0; v < 3; ++v)
+                for (int q = 0; q < 3; ++q) s += Bm[v][q] * (h[v].x * h[q].x + h[v].y * h[q].y);
+        }
+        acc += w * s;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        partials[blockIdx.x] = t;
+    }
+}
+
+int energy_k_blocks(const Geo& g) { return 152 * 4; }
+
+void launch_energy_k(const Geo& g, const Phys& ph, const double2* y, const double2* hk, double* partials,
+                     cudaStream_t s) {
+    k_energy_k<<<energy_k_blocks(g), 256, 0, s>>>(g, ph, y, hk, partials);
+}
+
+// explicit instantiations
+#define PF_INST(T)                                                                                                 \
+    template void launch_z_stage<T>(const Geo&, const Phys&, const double2*, const StageTerms&, double2*, void*,   \
+                                    cudaStream_t);                                                                 \
+    template void launch_y_pass<T>(const Geo&, void*, int, int, cudaStream_t);                                    \
+    template void launch_x_pass<T>(const Geo&, const Phys&, int, const void*, void*, void*, const void*, double*,  \
+                                   double, double, const double*, double*, cudaStream_t);                          \
+    template void launch_z_elastic<T>(const Geo&, const Phys&, void*, cudaStream_t);                               \
+    template void launch_z_fwd<T>(const Geo&, const Phys&, const void*, void*, int, cudaStream_t, int);                 \
+    template void launch_z_final<T>(const Geo&, const Phys&, const double2*, const StageTerms&, const StageTerms&, \
+                                    int, double2*, void*, cudaStream_t);
+PF_INST(double)
+PF_INST(float)
+
+}  // namespace pf

@@ -197,8 +197,19 @@ def test_free_energy_uniform_states(params):
     A = p["A_m"]
     mu = (0.07 - H * p["B_v"] - (1 - H) * p["B_m0"]) * 2 * A  # equal curvatures
     fch = H * A * (mu / (2 * A)) ** 2 + (1 - H) * A * (mu / (2 * A)) ** 2
-    fb = p["omega_bar"] * (a * a * (1 - a) ** 2 + b * b * (1 - b) ** 2) + p["omega_pair"][0] * a * b
+    eps = p["pair_eps"]
+    assert a * b > eps  # Huber branch |x| - eps/2
+    fb = p["omega_bar"] * (a * a * (1 - a) ** 2 + b * b * (1 - b) ** 2) + p["omega_pair"][0] * (a * b - eps / 2)
     # uniform h has only a DC mode, where B = 0
+    assert m.free_energy(m.to_k(y)) == pytest.approx(V * (fch + fb), rel=1e-12)
+    # quadratic branch of the regularised pairwise barrier: |x| -> x^2/(2 eps)
+    a, b = 0.1, 0.15
+    y[1], y[2] = a, b
+    H = h(a) + h(b)
+    mu = (0.07 - H * p["B_v"] - (1 - H) * p["B_m0"]) * 2 * A
+    fch = A * (mu / (2 * A)) ** 2
+    fb = p["omega_bar"] * (a * a * (1 - a) ** 2 + b * b * (1 - b) ** 2) + p["omega_pair"][0] * (a * b) ** 2 / (2 * eps)
+    assert a * b < eps
     assert m.free_energy(m.to_k(y)) == pytest.approx(V * (fch + fb), rel=1e-12)
 
 
@@ -252,18 +263,22 @@ def test_rhs_is_variational_derivative_of_free_energy(params):
     yh = m.to_k(y)
     tot = m.to_r(m.rhs_explicit(yh) + m.rhs_implicit(yh))
     dV = p["dx"] ** 3
-    eps = 1e-6
+    eps = 2e-5
+
+    def F_at(field, idx, d):
+        yp = y.copy()
+        yp[(field,) + idx] += d
+        return m.free_energy(m.to_k(yp))
 
     def dF(field, idx):
-        yp = y.copy()
-        yp[(field,) + idx] += eps
-        ym = y.copy()
-        ym[(field,) + idx] -= eps
-        return (m.free_energy(m.to_k(yp)) - m.free_energy(m.to_k(ym))) / (2 * eps * dV)
+        # fourth-order central difference of F w.r.t. one grid value
+        d1 = F_at(field, idx, eps) - F_at(field, idx, -eps)
+        d2 = F_at(field, idx, 2 * eps) - F_at(field, idx, -2 * eps)
+        return (8 * d1 - d2) / (12 * eps * dV)
 
     for idx in [(0, 0, 0), (3, 5, 2), (7, 1, 6)]:
         for v in range(3):
-            assert tot[1 + v][idx] == pytest.approx(-p["L"] * dF(1 + v, idx), rel=2e-6, abs=1e-9)
+            assert tot[1 + v][idx] == pytest.approx(-p["L"] * dF(1 + v, idx), rel=1e-6, abs=1e-10)
     # composition: dX/dt = -M k^2 mu^ ; recover mu differences from the RHS
     k2 = m.k2.copy()
     k2[0, 0, 0] = 1.0
@@ -271,7 +286,7 @@ def test_rhs_is_variational_derivative_of_free_energy(params):
     muh[0, 0, 0] = 0.0
     mu = m.to_r(muh[None])[0]
     a, b = (1, 2, 3), (6, 0, 4)
-    assert mu[a] - mu[b] == pytest.approx(dF(0, a) - dF(0, b), rel=2e-6)
+    assert mu[a] - mu[b] == pytest.approx(dF(0, a) - dF(0, b), rel=1e-6)
 
 
 # --------------------------------------------------------------------------
