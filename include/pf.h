@@ -191,6 +191,27 @@ const char* pf_kernel_name(int kind);
  * or PF_EUNSUPPORTED. Buffers must hold s*s (A) and s (b) doubles; s <= 8. */
 int pf_method_tableau(int method, double* AE, double* AI, double* bE, double* bI, double* btE, double* btI);
 
+/* Allocation-free inverse transform (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory -- e.g. applications
+ * that reserve their whole device budget at start-up or whose host framework
+ * forbids device allocation where it calls this library -- and therefore
+ * cannot create a context).  Computes what pf_set_state_hat + pf_get_state
+ * compute: the real-space fields [4][nz][ny][nx] (FP64, device pointer
+ * `fields`) of the k-space state `y_hat` (device complex128
+ * [4][nz][ny][nx/2+1], normalised as above), on `cuda_stream`, and waits for
+ * it.  All intermediates live in file-scope __device__ arrays of the library:
+ * 8.25 MiB of scratch plus 96 KiB of tables, held on every GPU that loads the
+ * library until the process exits.  Limits: each size even, 2,3,5-smooth,
+ * 4..1024, and nz*ny*(nx/2+1) <= 135168 (a 64^3 grid); larger grids return
+ * PF_EINVAL.  The first call on a device resolves the arrays' device
+ * addresses (once per device), so make that first call before any stream
+ * capture.  Every call reuses the same arrays: calls that overlap on the GPU
+ * (other threads or streams) race and must be serialised by the caller; no
+ * part of the scratch needs clearing, each call overwrites what it reads.
+ * No cudaMalloc/cudaFree or other allocating routine is called.  Errors:
+ * PF_EINVAL, PF_EUNSUPPORTED, PF_ECUDA; pf_last_error(NULL) describes them. */
+int pf_state_to_real_noalloc(const pf_grid* grid, const void* y_hat, double* fields, void* cuda_stream);
+
 /* Description of the last error of `ctx` (or of the last failed pf_create
  * when ctx is NULL). Never NULL. */
 const char* pf_last_error(const pf_ctx* ctx);

@@ -80,6 +80,7 @@ SIGNATURES = {
     "pf_profile_enable": (C.c_int, [_P, C.c_int]),
     "pf_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "pf_kernel_name": (C.c_char_p, [C.c_int]),
+    "pf_state_to_real_noalloc": (C.c_int, [C.POINTER(PFGrid), _P, _P, _P]),
 }
 NKERNELS = 10
 _DPTR_ARGS = {"pf_method_tableau"}

@@ -516,6 +516,8 @@ int rhs_explicit_t(pf_ctx* c, const double2* yh, double2* out) {
 }
 }  // namespace
 
+char* pf::create_error_buffer() { return g_create_err; }
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

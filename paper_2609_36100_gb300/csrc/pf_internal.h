@@ -94,6 +94,8 @@ void launch_reduce(const double* partials, int n, double scale, double* out, cud
 void launch_energy_k(const Geo& g, const Phys& ph, const double2* y, const double2* hk, double* partials,
                      cudaStream_t s);
 int x_pass_blocks(const Geo& g, int f64);
+// the thread's error buffer behind pf_last_error(NULL) (256 bytes)
+char* create_error_buffer();
 int energy_k_blocks(const Geo& g);
 
 }  // namespace pf
