@@ -100,33 +100,6 @@ bool make_tableau(int method, Tableau& t) {
 // ---------------------------------------------------------------------------
 // FFT plans
 // ---------------------------------------------------------------------------
-bool factor_radices(int n, AxisPlan& p) {
-    int m = n, a = 0, b = 0, c = 0;
-    while (m % 2 == 0) { m /= 2; ++a; }
-    while (m % 3 == 0) { m /= 3; ++b; }
-    while (m % 5 == 0) { m /= 5; ++c; }
-    if (m != 1) return false;
-    p.n = n;
-    p.nst = 0;
-    std::vector<int> r;
-    int n8 = a / 3, rem = a % 3;
-    if (rem == 1 && n8 > 0) {  // 2^(3k+1): prefer 4*4 over 8*2
-        --n8;
-        r.push_back(4);
-        r.push_back(4);
-    } else if (rem == 2) {
-        r.push_back(4);
-    } else if (rem == 1) {
-        r.push_back(2);
-    }
-    for (int i = 0; i < n8; ++i) r.insert(r.begin(), 8);
-    for (int i = 0; i < b; ++i) r.push_back(3);
-    for (int i = 0; i < c; ++i) r.push_back(5);
-    if ((int)r.size() > kMaxRadices) return false;
-    for (size_t i = 0; i < r.size(); ++i) p.rad[p.nst++] = r[i];
-    return true;
-}
-
 // exp(-2 pi i k / n) evaluated in extended precision with the angle reduced
 // to the first octant, then rounded to double.
 void twiddle_table(int n, std::vector<double2>& tw) {
@@ -183,6 +156,9 @@ struct pf_ctx {
     void* H = nullptr;
     void* R = nullptr;
     void* R1 = nullptr;
+    double* lam = nullptr;   // [4][NK] lambda(k), FP64
+    double* qtab = nullptr;  // [4][NK] 1/(1 - dt gamma lambda) of the current step (ESDIRK diagonal)
+    double gdiag = 0.0;      // common nonzero implicit diagonal entry, or 0
     double* partials = nullptr;
     int npartials = 0;
     double* d_scalar = nullptr;
@@ -256,6 +232,13 @@ void derive_phys(const pf_params& p, Phys& ph) {
     ph.w[0][2] = ph.w[2][0] = p.omega_pair[1];
     ph.w[1][2] = ph.w[2][1] = p.omega_pair[2];
     std::memcpy(ph.kap, p.kappa, sizeof(ph.kap));
+    ph.kap_iso = 1;
+    for (int v = 0; v < 3; ++v) {
+        const double* K = p.kappa[v];
+        if (!(K[1] == K[0] && K[2] == K[0] && K[3] == 0.0 && K[4] == 0.0 && K[5] == 0.0)) ph.kap_iso = 0;
+    }
+    ph.lamc[0] = -2.0 * p.A_m * ph.M;
+    for (int v = 0; v < 3; ++v) ph.lamc[1 + v] = -p.L * p.kappa[v][0];
     ph.C44 = p.C44;
     ph.Cmix = p.C12 + p.C44;
     ph.Caniso = p.C11 - p.C12 - 2.0 * p.C44;
@@ -296,6 +279,8 @@ void free_all(pf_ctx* c) {
     cudaFree(c->H);
     cudaFree(c->R);
     cudaFree(c->R1);
+    cudaFree(c->lam);
+    cudaFree(c->qtab);
     cudaFree(c->partials);
     cudaFree(c->d_scalar);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
@@ -314,6 +299,13 @@ int dalloc(pf_ctx* c, P** p, size_t bytes) {
 }
 
 double2* fp64_scratch(pf_ctx* c) { return c->zhat[c->tab.s - 1]; }
+
+// c = hi + lo with hi = fl32(c): the double-single form of an FP64 stage
+// coefficient that multiplies FP32 terms
+void split_ds(double c, float& hi, float& lo) {
+    hi = (float)c;
+    lo = (float)(c - (double)hi);
+}
 
 // Enqueue one attempted ImEx-ARK step of size dt from c->y into c->ynew; the
 // WRMS sum of the local error lands in c->d_scalar when want_lte.
@@ -360,6 +352,15 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte) {
             terms += (st.cI[j] != 0.0 && !c->alias_y[j] ? 16.0 : 0.0) + (st.cE[j] != 0.0 ? (c->fp32 ? 8.0 : 16.0) : 0.0);
         }
         st.gamma = dt * tb.AI[i][i];
+        for (int j = 0; j < i; ++j) split_ds(st.cE[j], st.cEh[j], st.cEl[j]);
+        if (c->gdiag != 0.0) {
+            if (i == 0) {
+                st.qout = c->qtab;
+                st.qgamma = dt * c->gdiag;
+            } else if (st.gamma != 0.0) {
+                st.qin = c->qtab;
+            }
+        }
         double2* zout = c->alias_y[i] ? nullptr : zp[i];
         if (!c->need_fe[i]) {
             if (zout) {
@@ -425,6 +426,8 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte) {
             dtm.cI[j] = dt * (tb.bI[j] - tb.btI[j]);
             dtm.cE[j] = dt * (tb.bE[j] - tb.btE[j]);
         }
+        split_ds(bt.cE[j], bt.cEh[j], bt.cEl[j]);
+        split_ds(dtm.cE[j], dtm.cEh[j], dtm.cEl[j]);
         const bool zI = bt.cI[j] != 0.0 || (lte && dtm.cI[j] != 0.0);
         const bool fEn = bt.cE[j] != 0.0 || (lte && dtm.cE[j] != 0.0);
         fterms += (zI && !(c->alias_y[j]) ? 16.0 : 0.0) + (fEn ? (c->fp32 ? 8.0 : 16.0) : 0.0);
@@ -575,6 +578,16 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
         for (int j = 0; j < i; ++j) ex = ex && tb.AI[i][j] == 0.0 && tb.AE[i][j] == 0.0;
         c->alias_y[i] = ex;
     }
+    // one shared implicit diagonal (SDIRK/ESDIRK): 1/(1 - dt gamma lambda) is
+    // formed once per step by the first stage and reused by every implicit stage
+    c->gdiag = 0.0;
+    for (int i = 0; i < tb.s; ++i) {
+        const double d = tb.AI[i][i];
+        if (d == 0.0) continue;
+        if (c->gdiag == 0.0) c->gdiag = d;
+        else if (c->gdiag != d) c->gdiag = -1.0;
+    }
+    if (c->gdiag < 0.0 || !c->need_fe[0]) c->gdiag = 0.0;
     Geo& g = c->g;
     g.nx = grid->nx;
     g.ny = grid->ny;
@@ -582,6 +595,8 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     g.nxh = g.nx / 2 + 1;
     g.NK = (long long)g.nz * g.ny * g.nxh;
     g.N = (long long)g.nz * g.ny * g.nx;
+    g.mul_nx = magic_u32((unsigned)g.nx);
+    g.mul_nxh = magic_u32((unsigned)g.nxh);
     int rc = PF_OK;
     // wave numbers k_m = 2 pi m / (n d), Nyquist +pi/d
     auto ktab = [](int n, double d, bool half) {
@@ -598,7 +613,7 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     AxisPlan* plans[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
-        if (!factor_radices(ns[a], *plans[a])) {
+        if (!make_axis_plan(ns[a], *plans[a])) {
             delete c;
             return fail(nullptr, PF_EUNSUPPORTED, "cannot factor %d", ns[a]);
         }
@@ -622,6 +637,8 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     rc = rc ? rc : dalloc(c, &c->H, 3 * (size_t)g.NK * 2 * tsz);
     rc = rc ? rc : dalloc(c, &c->R, 4 * (size_t)g.N * tsz);
     rc = rc ? rc : dalloc(c, &c->R1, 4 * (size_t)g.N * tsz);
+    rc = rc ? rc : dalloc(c, &c->lam, nk4 * sizeof(double));
+    rc = rc ? rc : dalloc(c, &c->qtab, nk4 * sizeof(double));
     c->npartials = x_pass_blocks(g, 0) > x_pass_blocks(g, 1) ? x_pass_blocks(g, 0) : x_pass_blocks(g, 1);
     if (energy_k_blocks(g) > c->npartials) c->npartials = energy_k_blocks(g);
     rc = rc ? rc : dalloc(c, &c->partials, (size_t)c->npartials * sizeof(double));
@@ -651,6 +668,14 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
         plans[a]->tw32 = c->d_tw32[a];
     }
     e = e ? e : cudaMemsetAsync(c->y, 0, nk4 * sizeof(double2), c->stream);
+    if (!e) {
+        g.kx = c->d_kx;
+        g.ky = c->d_ky;
+        g.kz = c->d_kz;
+        launch_lambda_table(g, c->ph, c->lam, c->stream);
+        e = cudaGetLastError();
+        g.lam = c->lam;
+    }
     e = e ? e : cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         std::snprintf(g_create_err, sizeof g_create_err, "device setup: %s", cudaGetErrorString(e));

@@ -135,29 +135,45 @@ __device__ __forceinline__ const double2* twiddles<double2>(const AxisPlan& p) {
 template <>
 __device__ __forceinline__ const float2* twiddles<float2>(const AxisPlan& p) { return p.tw32; }
 
+// Exact unsigned division by a constant d >= 1 for numerators n with
+// n * d < 2^32 (here n < 2^15, d <= 1024): q = (n * mul) >> 32 with
+// mul = ceil(2^32 / d), computed on the host (see magic_u32).
+struct FastDiv {
+    unsigned d, mul;
+    __device__ __forceinline__ FastDiv(unsigned dd, unsigned mm) : d(dd), mul(mm) {}
+    __device__ __forceinline__ unsigned div(unsigned n) const { return d == 1 ? n : __umulhi(n, mul); }
+};
+
 // One radix-R Stockham stage over all lines. LINE_FAST maps consecutive
 // threads to consecutive lines (strided tiles, lines are contiguous columns);
 // otherwise to consecutive butterflies of a line (contiguous x lines).
-template <int R, int SIGN, bool LINE_FAST, typename T2>
+template <int R, int SIGN, bool LINE_FAST, int NL, typename T2>
 __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __restrict__ dst, int n, int nl, int es,
-                                          int ls, int Ns, const T2* __restrict__ tw) {
+                                          int ls, int Ns, const T2* __restrict__ tw, FastDiv divm, FastDiv divN,
+                                          FastDiv divl) {
     const int m = n / R;
     const int total = nl * m;
     const int tws = n / (Ns * R);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int line, j;
-        if (LINE_FAST) {
-            line = idx % nl;
-            j = idx / nl;
+        if constexpr (LINE_FAST) {
+            if constexpr (NL > 0) {
+                line = idx & (NL - 1);
+                j = idx / NL;
+            } else {
+                j = (int)divl.div((unsigned)idx);
+                line = idx - j * nl;
+            }
         } else {
-            j = idx % m;
-            line = idx / m;
+            line = (int)divm.div((unsigned)idx);
+            j = idx - line * m;
         }
         const T2* s = src + line * ls;
         T2 v[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) v[t] = s[(j + t * m) * es];
-        const int k = j % Ns;
+        const int jq = (int)divN.div((unsigned)j);
+        const int k = j - jq * Ns;
         if (Ns > 1) {
             const int st = k * tws;
 #pragma unroll
@@ -167,7 +183,7 @@ __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __rest
             }
         }
         Bfly<R, SIGN, T2>::run(v);
-        const int base = (j - k) * R + k;
+        const int base = jq * Ns * R + k;
         T2* d = dst + line * ls;
 #pragma unroll
         for (int t = 0; t < R; ++t) d[(base + t * Ns) * es] = v[t];
@@ -175,21 +191,23 @@ __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __rest
 }
 
 // Full transform of the lines in `a` (b is scratch).  Callers synchronise
-// before; returns the buffer holding the result (synchronised).
-template <int SIGN, bool LINE_FAST, typename T2>
-__device__ T2* fft_lines(T2* a, T2* b, const AxisPlan& p, int nl, int es, int ls) {
+// before; returns the buffer holding the result (synchronised).  NL > 0 fixes
+// the line count at compile time (strided tiles of NL columns).
+template <int SIGN, bool LINE_FAST, int NL = 0, typename T2>
+__device__ T2* fft_lines(T2* a, T2* b, const AxisPlan& p, int nl, int es, int ls, FastDiv divl = FastDiv(1, 0)) {
     const T2* tw = twiddles<T2>(p);
     T2* src = a;
     T2* dst = b;
     int Ns = 1;
     for (int s = 0; s < p.nst; ++s) {
         const int r = p.rad[s];
+        const FastDiv dm((unsigned)(p.n / r), p.mulm[s]), dN((unsigned)Ns, p.mulN[s]);
         switch (r) {
-            case 2: fft_stage<2, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
-            case 3: fft_stage<3, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
-            case 4: fft_stage<4, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
-            case 5: fft_stage<5, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
-            default: fft_stage<8, SIGN, LINE_FAST>(src, dst, p.n, nl, es, ls, Ns, tw); break;
+            case 2: fft_stage<2, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            case 3: fft_stage<3, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            case 4: fft_stage<4, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            case 5: fft_stage<5, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            default: fft_stage<8, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
         }
         __syncthreads();
         T2* t = src;
@@ -198,6 +216,95 @@ __device__ T2* fft_lines(T2* a, T2* b, const AxisPlan& p, int nl, int es, int ls
         Ns *= r;
     }
     return src;
+}
+
+// ---------------------------------------------------------------------------
+// Column-tile transform: TX lines ("columns", contiguous in global memory)
+// of length n.  Stage 0 reads element (pos, col) through src(pos, col) --
+// straight from global memory, with the pass's pointwise prologue fused --
+// and the last stage hands each result to dst(pos, col, v); only the middle
+// stages go through shared memory (layout [pos][TX]), ping-ponging between
+// P and Q (P first).  Callers pick P/Q so that no stage reads and writes the
+// same buffer.  With one stage and IN_PLACE (dst writes what src reads),
+// results go through P first.
+// ---------------------------------------------------------------------------
+template <int R, int SIGN, int TX, typename T2, class Src, class Dst>
+__device__ __forceinline__ void col_stage(int n, int Ns, FastDiv dN, const T2* __restrict__ in, T2* __restrict__ out,
+                                          bool first, bool last, const T2* __restrict__ tw, Src& src, Dst& dst) {
+    const int m = n / R;
+    const int total = TX * m;
+    const int tws = n / (Ns * R);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int col = idx & (TX - 1);
+        const int j = idx / TX;
+        T2 v[R];
+        if (first) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = src(j + t * m, col);
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = in[(j + t * m) * TX + col];
+        }
+        const int jq = (int)dN.div((unsigned)j);
+        const int k = j - jq * Ns;
+        if (Ns > 1) {
+            const int st = k * tws;
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                const T2 w = __ldg(tw + t * st);
+                v[t] = SIGN < 0 ? cmul(v[t], w) : cmulc(v[t], w);
+            }
+        }
+        Bfly<R, SIGN, T2>::run(v);
+        const int base = jq * Ns * R + k;
+        if (last) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) dst(base + t * Ns, col, v[t]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) out[(base + t * Ns) * TX + col] = v[t];
+        }
+    }
+}
+
+template <int SIGN, int TX, bool IN_PLACE = false, typename T2, class Src, class Dst>
+__device__ void fft_cols(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
+    const T2* tw = twiddles<T2>(p);
+    const int n = p.n;
+    if (p.nst == 1 && IN_PLACE) {
+        // single stage reading and writing the same global columns: stage
+        // into P, then store
+        auto toP = [&](int pos, int col, T2 v) { P[pos * TX + col] = v; };
+        const FastDiv dN(1u, 0u);
+        switch (p.rad[0]) {
+            case 2: col_stage<2, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
+            case 3: col_stage<3, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
+            case 4: col_stage<4, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
+            case 5: col_stage<5, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
+            default: col_stage<8, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < TX * n; e += blockDim.x) dst(e / TX, e & (TX - 1), P[e]);
+        return;
+    }
+    const T2* in = nullptr;
+    T2* out = P;
+    int Ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        const bool first = (s == 0), last = (s == p.nst - 1);
+        const FastDiv dN((unsigned)Ns, p.mulN[s]);
+        switch (p.rad[s]) {
+            case 2: col_stage<2, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
+            case 3: col_stage<3, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
+            case 4: col_stage<4, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
+            case 5: col_stage<5, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
+            default: col_stage<8, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
+        }
+        if (!last) __syncthreads();
+        in = out;
+        out = (out == P) ? Q : P;
+        Ns *= p.rad[s];
+    }
 }
 
 }  // namespace pf

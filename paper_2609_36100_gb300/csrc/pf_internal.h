@@ -15,9 +15,16 @@ struct AxisPlan {
     int n;
     int nst;
     int rad[kMaxRadices];
+    unsigned mulm[kMaxRadices];  // division magic for n / rad[s]
+    unsigned mulN[kMaxRadices];  // division magic for the stage's Ns
     const double2* tw64;
     const float2* tw32;
 };
+
+// ceil(2^32 / d) for d >= 2 (0 for d = 1, which FastDiv special-cases)
+inline unsigned magic_u32(unsigned d) { return d <= 1 ? 0u : (unsigned)((0xffffffffull + d) / d); }
+// radix schedule (8s first, then 4/2, 3s, 5s) and division magic of one axis
+bool make_axis_plan(int n, AxisPlan& p);
 
 // Grid geometry and the per-axis wave-number tables k_m = 2 pi m / (n d)
 // (FP64, Nyquist index taken as +pi/d).
@@ -28,7 +35,9 @@ struct Geo {
     const double* kx;  // [nxh]
     const double* ky;  // [ny]
     const double* kz;  // [nz]
+    const double* lam;  // [4][NK] lambda(k) per field (FP64), or null (computed on the fly)
     AxisPlan px, py, pz;
+    unsigned mul_nx, mul_nxh;  // division magic for nx and nx/2+1
     int tx_y, tx_z, tx_el;  // tile widths (kx columns) of the strided passes
     int rp;                  // row pairs per CTA in the x passes
 };
@@ -42,6 +51,8 @@ struct Phys {
     double w[3][3];       // pairwise barrier omega_vq (zero diagonal)
     double pair_eps;      // Huber width of |phi_v phi_q|
     double kap[3][6];     // gradient tensors (Voigt)
+    int kap_iso;          // every kappa_v is a multiple of the identity
+    double lamc[4];       // lambda = lamc[f] k^2 when kap_iso (lamc[0] always)
     int elastic;          // 0: all eigenstrains zero
     double Caniso, Cmix, C44;  // C11 - C12 - 2 C44, C12 + C44, C44
     double sig[3][6];     // sigma*_v = C : eps*_v (Voigt)
@@ -55,7 +66,11 @@ struct StageTerms {
     const void* f[kMaxStages];         // f^E_j (compute type)
     double cI[kMaxStages];             // dt * A^I_ij (or dt * b^I_j)
     double cE[kMaxStages];             // dt * A^E_ij (or dt * b^E_j)
+    float cEh[kMaxStages], cEl[kMaxStages];  // cE = cEh + cEl (double-single split, FP32-bulk terms)
     double gamma;                      // dt * A^I_ii (0: explicit stage)
+    const double* qin;                 // table of 1/(1 - gamma lambda) for this gamma, or null
+    double* qout;                      // if set: write 1/(1 - qgamma lambda) (once per step)
+    double qgamma;
 };
 
 enum XMode {
@@ -90,6 +105,7 @@ void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageT
 void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, int fe_is_f32,
                             double2* zout, cudaStream_t s);
 void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s);
+void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, cudaStream_t s);
 void launch_reduce(const double* partials, int n, double scale, double* out, cudaStream_t s);
 void launch_energy_k(const Geo& g, const Phys& ph, const double2* y, const double2* hk, double* partials,
                      cudaStream_t s);

@@ -30,9 +30,11 @@ constexpr int kThreads = 256;
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-// lambda(k) of field f: -2 A^m M k^2 (X), -L k.kappa_v.k (phi_v); FP64
+// lambda(k) of field f: -2 A^m M k^2 (X), -L k.kappa_v.k (phi_v); FP64.
+// Isotropic gradient tensors reduce to lamc[f] * k^2.
 __device__ __forceinline__ double lambda_k(const Phys& ph, int f, double kx, double ky, double kz) {
-    if (f == 0) return (-2.0 * ph.Am * ph.M) * (kx * kx + ky * ky + kz * kz);
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    if (f == 0 || ph.kap_iso) return ph.lamc[f] * k2;
     const double* K = ph.kap[f - 1];
     double kk = K[0] * kx * kx + K[1] * ky * ky + K[2] * kz * kz;
     kk += 2.0 * (K[3] * ky * kz + K[4] * kx * kz + K[5] * kx * ky);
@@ -47,6 +49,50 @@ template <>
 __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
 template <>
 __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+template <typename T2>
+__device__ __forceinline__ double2 load_f(const void* p, long long i) {
+    return to_d2(reinterpret_cast<const T2*>(p)[i]);
+}
+
+// r += c * v (complex v, real c), FP64
+__device__ __forceinline__ void axpy(double2& r, double c, double2 v) {
+    r.x = fma(c, v.x, r.x);
+    r.y = fma(c, v.y, r.y);
+}
+
+// Double-single accumulation (hi, lo) += (ch + cl) * f for an FP32 value f:
+// the product ch*f is split exactly with an FMA, cl*f is added to its error,
+// and the sum uses the two-sum error-free transformation (no contraction:
+// explicitly rounded intrinsics).  Carries ~48 bits, so FP32 stage terms enter
+// the FP64 combination without passing through the narrow FP64 pipe.
+__device__ __forceinline__ void ds_add_prod(float& sh, float& sl, float ch, float cl, float f) {
+    const float p = __fmul_rn(ch, f);
+    float e = __fmaf_rn(ch, f, -p);
+    e = __fmaf_rn(cl, f, e);
+    const float s = __fadd_rn(sh, p);
+    const float bb = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+struct DS2 {
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
+    __device__ __forceinline__ void add(float ch, float cl, float2 f) {
+        ds_add_prod(xh, xl, ch, cl, f.x);
+        ds_add_prod(yh, yl, ch, cl, f.y);
+    }
+    __device__ __forceinline__ void flush(double2& r) const {
+        r.x += (double)xh + (double)xl;
+        r.y += (double)yh + (double)yl;
+    }
+};
+
+__device__ __forceinline__ double lam_at(const Geo& g, const Phys& ph, int f, long long gi, double kx, double ky,
+                                         double kz) {
+    return g.lam ? g.lam[gi] : lambda_k(ph, f, kx, ky, kz);
+}
 
 template <typename T>
 static int strided_tile(int n, int nbuf, int budget) {
@@ -68,57 +114,82 @@ static void set_smem(K kern, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// compile-time tile width dispatch
+#define PF_TX_SWITCH(tx, ...)                 \
+    switch (tx) {                             \
+        case 16: {                            \
+            constexpr int TXC = 16;           \
+            __VA_ARGS__;                      \
+        } break;                              \
+        case 8: {                             \
+            constexpr int TXC = 8;            \
+            __VA_ARGS__;                      \
+        } break;                              \
+        case 4: {                             \
+            constexpr int TXC = 4;            \
+            __VA_ARGS__;                      \
+        } break;                              \
+        case 2: {                             \
+            constexpr int TXC = 2;            \
+            __VA_ARGS__;                      \
+        } break;                              \
+        default: {                            \
+            constexpr int TXC = 1;            \
+            __VA_ARGS__;                      \
+        } break;                              \
+    }
+
 // ---------------------------------------------------------------------------
 // z pass: stage assembly + implicit solve + inverse FFT along z
 //   r = y + sum_j (dt A^I_ij) lambda z_j + (dt A^E_ij) f^E_j
 //   z_i = r / (1 - dt A^I_ii lambda)
+// The assembly is the first FFT stage's load: each element is formed once.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int TX>
 __global__ void __launch_bounds__(kThreads) k_z_stage(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st,
-                                                      double2* __restrict__ zout, typename Cx<T>::t* __restrict__ W,
-                                                      int TX) {
+                                                      double2* __restrict__ zout,
+                                                      typename Cx<T>::t* __restrict__ W) {
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
     T2* B = A + TX * g.nz;
     const int f = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * TX;
     const int ncol = min(TX, g.nxh - kx0);
-    const long long fo = (long long)f * g.NK;
-    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
-        const int col = e % TX, kz = e / TX;
-        T2 v = T2{0, 0};
-        if (col < ncol) {
-            const long long gi = fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col;
-            double2 r = y[gi];
-            const double lam = lambda_k(ph, f, g.kx[kx0 + col], g.ky[ky], g.kz[kz]);
-            for (int j = 0; j < st.n; ++j) {
-                if (st.cI[j] != 0.0) {
-                    const double2 zj = st.z[j][gi];
-                    r.x = r.x + st.cI[j] * (lam * zj.x);
-                    r.y = r.y + st.cI[j] * (lam * zj.y);
-                }
+    const long long base = (long long)f * g.NK + (long long)ky * g.nxh + kx0;
+    const long long zs = (long long)g.ny * g.nxh;
+    const double kyv = g.ky[ky];
+    auto src = [&](int kz, int col) -> T2 {
+        if (col >= ncol) return T2{0, 0};
+        const long long gi = base + kz * zs + col;
+        double2 r = y[gi];
+        const double lam = lam_at(g, ph, f, gi, g.kx[kx0 + col], kyv, g.kz[kz]);
+        DS2 fs;
+#pragma unroll
+        for (int j = 0; j < kMaxStages; ++j) {
+            if (j < st.n) {
+                if (st.cI[j] != 0.0) axpy(r, st.cI[j] * lam, st.z[j][gi]);
                 if (st.cE[j] != 0.0) {
-                    const double2 fj = to_d2(reinterpret_cast<const T2*>(st.f[j])[gi]);
-                    r.x = r.x + st.cE[j] * fj.x;
-                    r.y = r.y + st.cE[j] * fj.y;
+                    if (sizeof(T) == 4)
+                        fs.add(st.cEh[j], st.cEl[j], reinterpret_cast<const float2*>(st.f[j])[gi]);
+                    else
+                        axpy(r, st.cE[j], load_f<T2>(st.f[j], gi));
                 }
             }
-            if (st.gamma != 0.0) {
-                const double den = 1.0 - st.gamma * lam;
-                r.x = r.x / den;
-                r.y = r.y / den;
-            }
-            if (zout) zout[gi] = r;
-            v = from_d2<T2>(r);
         }
-        A[kz * TX + col] = v;
-    }
-    __syncthreads();
-    T2* res = fft_lines<+1, true>(A, B, g.pz, TX, TX, 1);
-    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
-        const int col = e % TX, kz = e / TX;
-        if (col < ncol) W[fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] = res[kz * TX + col];
-    }
+        if (sizeof(T) == 4) fs.flush(r);
+        if (st.qout) st.qout[gi] = 1.0 / (1.0 - st.qgamma * lam);
+        if (st.gamma != 0.0) {
+            const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - st.gamma * lam);
+            r.x *= q;
+            r.y *= q;
+        }
+        if (zout) zout[gi] = r;
+        return from_d2<T2>(r);
+    };
+    auto dst = [&](int kz, int col, T2 v) {
+        if (col < ncol) W[base + kz * zs + col] = v;
+    };
+    fft_cols<+1, TX>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
@@ -127,16 +198,16 @@ void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageT
     using T2 = typename Cx<T>::t;
     const int TX = tile_cols<T>(g, g.nz, 2, 96 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
-    set_smem(k_z_stage<T>, sm);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
-    k_z_stage<T><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout, reinterpret_cast<T2*>(W), TX);
+    PF_TX_SWITCH(TX, set_smem(k_z_stage<T, TXC>, sm);
+                 k_z_stage<T, TXC><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout, reinterpret_cast<T2*>(W)))
 }
 
 // ---------------------------------------------------------------------------
 // y pass: in-place complex FFT along y of nf fields
 // ---------------------------------------------------------------------------
-template <typename T, int SIGN>
-__global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* __restrict__ buf, int TX) {
+template <typename T, int SIGN, int TX>
+__global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* __restrict__ buf) {
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
@@ -144,16 +215,12 @@ __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* _
     const int f = blockIdx.z, kz = blockIdx.y, kx0 = blockIdx.x * TX;
     const int ncol = min(TX, g.nxh - kx0);
     T2* base = buf + (long long)f * g.NK + (long long)kz * g.ny * g.nxh + kx0;
-    for (int e = threadIdx.x; e < TX * g.ny; e += blockDim.x) {
-        const int col = e % TX, ky = e / TX;
-        A[ky * TX + col] = col < ncol ? base[(long long)ky * g.nxh + col] : T2{0, 0};
-    }
-    __syncthreads();
-    T2* res = fft_lines<SIGN, true>(A, B, g.py, TX, TX, 1);
-    for (int e = threadIdx.x; e < TX * g.ny; e += blockDim.x) {
-        const int col = e % TX, ky = e / TX;
-        if (col < ncol) base[(long long)ky * g.nxh + col] = res[ky * TX + col];
-    }
+    const int ys = g.nxh;
+    auto src = [&](int ky, int col) -> T2 { return col < ncol ? base[ky * ys + col] : T2{0, 0}; };
+    auto dst = [&](int ky, int col, T2 v) {
+        if (col < ncol) base[ky * ys + col] = v;
+    };
+    fft_cols<SIGN, TX, true>(g.py, A, B, src, dst);
 }
 
 template <typename T>
@@ -163,55 +230,52 @@ void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
     const size_t sm = 2 * (size_t)TX * g.ny * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.nz, nf);
     if (sign > 0) {
-        set_smem(k_y_pass<T, 1>, sm);
-        k_y_pass<T, 1><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf), TX);
+        PF_TX_SWITCH(TX, set_smem(k_y_pass<T, 1, TXC>, sm);
+                     k_y_pass<T, 1, TXC><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf)))
     } else {
-        set_smem(k_y_pass<T, -1>, sm);
-        k_y_pass<T, -1><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf), TX);
+        PF_TX_SWITCH(TX, set_smem(k_y_pass<T, -1, TXC>, sm);
+                     k_y_pass<T, -1, TXC><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf)))
     }
 }
 
 // ---------------------------------------------------------------------------
-// z pass, forward: FFT along z then k-space scaling
+// z pass, forward: FFT along z then k-space scaling (the last stage's store)
 //   mode 0: y^ = W / N  -> FP64                                  (set_state)
 //   mode 1: f^E_X = -M k^2 q^/N, f^E_phi = -L g^/N -> compute type (stages)
 //   mode 2: same scaling -> FP64                                  (ABI f^E)
 // ---------------------------------------------------------------------------
-template <typename T, typename OT2>
+template <typename T, typename OT2, int TX>
 __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typename Cx<T>::t* __restrict__ W,
-                                                    OT2* __restrict__ out, int mode, int TX) {
+                                                    OT2* __restrict__ out, int mode) {
     using T2 = typename Cx<T>::t;
+    using OT = decltype(OT2{}.x);
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
     T2* B = A + TX * g.nz;
     const int f = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * TX;
     const int ncol = min(TX, g.nxh - kx0);
-    const long long fo = (long long)f * g.NK;
-    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
-        const int col = e % TX, kz = e / TX;
-        A[kz * TX + col] = col < ncol ? W[fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] : T2{0, 0};
-    }
-    __syncthreads();
-    T2* res = fft_lines<-1, true>(A, B, g.pz, TX, TX, 1);
+    const long long base = (long long)f * g.NK + (long long)ky * g.nxh + kx0;
+    const long long zs = (long long)g.ny * g.nxh;
     const double invN = 1.0 / (double)g.N;
-    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
-        const int col = e % TX, kz = e / TX;
-        if (col >= ncol) continue;
-        const long long gi = fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col;
-        const T2 v = res[kz * TX + col];
+    const double kyv = g.ky[ky];
+    auto src = [&](int kz, int col) -> T2 { return col < ncol ? W[base + kz * zs + col] : T2{0, 0}; };
+    auto dst = [&](int kz, int col, T2 v) {
+        if (col >= ncol) return;
+        const long long gi = base + kz * zs + col;
         if (mode == 0) {
-            out[gi] = OT2{(decltype(OT2{}.x))((double)v.x * invN), (decltype(OT2{}.x))((double)v.y * invN)};
+            out[gi] = OT2{(OT)((double)v.x * invN), (OT)((double)v.y * invN)};
         } else {
             T sc;
             if (f == 0) {
-                const double kx = g.kx[kx0 + col], kyv = g.ky[ky], kzv = g.kz[kz];
+                const double kx = g.kx[kx0 + col], kzv = g.kz[kz];
                 sc = (T)(-ph.M * (kx * kx + kyv * kyv + kzv * kzv) * invN);
             } else {
                 sc = (T)(-ph.L * invN);
             }
-            out[gi] = OT2{(decltype(OT2{}.x))(v.x * sc), (decltype(OT2{}.x))(v.y * sc)};
+            out[gi] = OT2{(OT)(v.x * sc), (OT)(v.y * sc)};
         }
-    }
+    };
+    fft_cols<-1, TX>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
@@ -221,13 +285,14 @@ void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int sc
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
     if (scale_mode == 1) {
-        set_smem(k_z_fwd<T, T2>, sm);
-        k_z_fwd<T, T2><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W), reinterpret_cast<T2*>(out),
-                                                  1, TX);
+        PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, T2, TXC>, sm);
+                     k_z_fwd<T, T2, TXC><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
+                                                                    reinterpret_cast<T2*>(out), 1))
     } else {
-        set_smem(k_z_fwd<T, double2>, sm);
-        k_z_fwd<T, double2><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
-                                                       reinterpret_cast<double2*>(out), scale_mode, TX);
+        PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, double2, TXC>, sm);
+                     k_z_fwd<T, double2, TXC><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
+                                                                         reinterpret_cast<double2*>(out),
+                                                                         scale_mode))
     }
 }
 
@@ -280,54 +345,63 @@ __device__ __forceinline__ void elastic_kernel(const Phys& ph, double kx, double
             Bm[v][q] = (T)ph.cvq[v][q] - (s[v][0] * Os[q][0] + s[v][1] * Os[q][1] + s[v][2] * Os[q][2]);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename Cx<T>::t* __restrict__ H, int TX) {
+template <typename T, int TX>
+__global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename Cx<T>::t* __restrict__ H) {
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T2* buf[4];
     const int tile = TX * g.nz;
-    for (int i = 0; i < 4; ++i) buf[i] = reinterpret_cast<T2*>(smraw) + i * tile;
+    T2* slot[3];
+    slot[0] = reinterpret_cast<T2*>(smraw);
+    slot[1] = slot[0] + tile;
+    slot[2] = slot[1] + tile;
+    T2* E = slot[2] + tile;
     const int ky = blockIdx.y, kx0 = blockIdx.x * TX;
     const int ncol = min(TX, g.nxh - kx0);
-    for (int e = threadIdx.x; e < 3 * tile; e += blockDim.x) {
-        const int f = e / tile, r = e % tile, col = r % TX, kz = r / TX;
-        buf[f][r] = col < ncol ? H[(long long)f * g.NK + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] : T2{0, 0};
-    }
-    __syncthreads();
-    // forward FFT of each field; field slots rotate through the scratch slot
+    const long long rowoff = (long long)ky * g.nxh + kx0;
+    const long long zs = (long long)g.ny * g.nxh;
+    const bool nst_even = (g.pz.nst % 2) == 0;
+    // forward transforms: global -> field slot (middle stages ping-pong with E
+    // so that the last stage reads E and writes the slot)
+#pragma unroll
     for (int f = 0; f < 3; ++f) {
-        T2* res = fft_lines<-1, true>(buf[f], buf[3], g.pz, TX, TX, 1);
-        if (res == buf[3]) {
-            buf[3] = buf[f];
-            buf[f] = res;
-        }
+        T2* S = slot[f];
+        const long long fb = (long long)f * g.NK + rowoff;
+        auto src = [&](int kz, int col) -> T2 { return col < ncol ? H[fb + kz * zs + col] : T2{0, 0}; };
+        auto dst = [&](int kz, int col, T2 v) { S[kz * TX + col] = v; };
+        if (nst_even)
+            fft_cols<-1, TX>(g.pz, E, S, src, dst);
+        else
+            fft_cols<-1, TX>(g.pz, S, E, src, dst);
+        __syncthreads();
     }
     const T invN = (T)(1.0 / (double)g.N);
+    const double kyv = g.ky[ky];
     for (int r = threadIdx.x; r < tile; r += blockDim.x) {
-        const int col = r % TX, kz = r / TX;
+        const int col = r & (TX - 1), kz = r / TX;
         if (col >= ncol) continue;
         T Bm[3][3];
-        elastic_kernel<T>(ph, g.kx[kx0 + col], g.ky[ky], g.kz[kz], Bm);
-        const T2 h0 = buf[0][r], h1 = buf[1][r], h2 = buf[2][r];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            T2 o;
-            o.x = (Bm[v][0] * h0.x + Bm[v][1] * h1.x + Bm[v][2] * h2.x) * invN;
-            o.y = (Bm[v][0] * h0.y + Bm[v][1] * h1.y + Bm[v][2] * h2.y) * invN;
-            buf[v][r] = o;
-        }
+        elastic_kernel<T>(ph, g.kx[kx0 + col], kyv, g.kz[kz], Bm);
+        const T2 h0 = slot[0][r], h1 = slot[1][r], h2 = slot[2][r];
+        slot[0][r] = T2{(Bm[0][0] * h0.x + Bm[0][1] * h1.x + Bm[0][2] * h2.x) * invN,
+                        (Bm[0][0] * h0.y + Bm[0][1] * h1.y + Bm[0][2] * h2.y) * invN};
+        slot[1][r] = T2{(Bm[1][0] * h0.x + Bm[1][1] * h1.x + Bm[1][2] * h2.x) * invN,
+                        (Bm[1][0] * h0.y + Bm[1][1] * h1.y + Bm[1][2] * h2.y) * invN};
+        slot[2][r] = T2{(Bm[2][0] * h0.x + Bm[2][1] * h1.x + Bm[2][2] * h2.x) * invN,
+                        (Bm[2][0] * h0.y + Bm[2][1] * h1.y + Bm[2][2] * h2.y) * invN};
     }
     __syncthreads();
+    // inverse transforms: field slot -> global (stage 0 reads the slot and
+    // writes E)
+#pragma unroll
     for (int f = 0; f < 3; ++f) {
-        T2* res = fft_lines<+1, true>(buf[f], buf[3], g.pz, TX, TX, 1);
-        if (res == buf[3]) {
-            buf[3] = buf[f];
-            buf[f] = res;
-        }
-    }
-    for (int e = threadIdx.x; e < 3 * tile; e += blockDim.x) {
-        const int f = e / tile, r = e % tile, col = r % TX, kz = r / TX;
-        if (col < ncol) H[(long long)f * g.NK + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] = buf[f][r];
+        T2* S = slot[f];
+        const long long fb = (long long)f * g.NK + rowoff;
+        auto src = [&](int kz, int col) -> T2 { return S[kz * TX + col]; };
+        auto dst = [&](int kz, int col, T2 v) {
+            if (col < ncol) H[fb + kz * zs + col] = v;
+        };
+        fft_cols<+1, TX>(g.pz, E, S, src, dst);
+        __syncthreads();
     }
 }
 
@@ -336,9 +410,9 @@ void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
     const int TX = tile_cols<T>(g, g.nz, 4, 128 * 1024);
     const size_t sm = 4 * (size_t)TX * g.nz * sizeof(T2);
-    set_smem(k_z_elastic<T>, sm);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);
-    k_z_elastic<T><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<T2*>(H), TX);
+    PF_TX_SWITCH(TX, set_smem(k_z_elastic<T, TXC>, sm);
+                 k_z_elastic<T, TXC><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<T2*>(H)))
 }
 
 // ---------------------------------------------------------------------------
@@ -346,61 +420,65 @@ void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
 //   y_n = y + sum_i (dt b^I_i) lambda z_i + (dt b^E_i) f^E_i
 //   LTE = sum_i (dt (b-bt)^I_i) lambda z_i + (dt (b-bt)^E_i) f^E_i
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int TX>
 __global__ void __launch_bounds__(kThreads) k_z_final(Geo g, Phys ph, const double2* __restrict__ y, StageTerms bt,
                                                       StageTerms dt, int want_lte, double2* __restrict__ ynew,
-                                                      typename Cx<T>::t* __restrict__ W, int TX) {
+                                                      typename Cx<T>::t* __restrict__ W) {
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
     T2* B = A + TX * g.nz;
     const int f = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * TX;
     const int ncol = min(TX, g.nxh - kx0);
-    const long long fo = (long long)f * g.NK;
-    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
-        const int col = e % TX, kz = e / TX;
-        T2 v = T2{0, 0};
-        if (col < ncol) {
-            const long long gi = fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col;
-            const double lam = lambda_k(ph, f, g.kx[kx0 + col], g.ky[ky], g.kz[kz]);
-            double2 r = y[gi];
-            double2 l = make_double2(0.0, 0.0);
-            for (int j = 0; j < bt.n; ++j) {
-                const double2 zj = bt.z[j][gi];
-                const double2 fj =
-                    (bt.cE[j] != 0.0 || dt.cE[j] != 0.0) ? to_d2(reinterpret_cast<const T2*>(bt.f[j])[gi])
-                                                         : make_double2(0.0, 0.0);
-                if (bt.cI[j] != 0.0) {
-                    r.x = r.x + bt.cI[j] * (lam * zj.x);
-                    r.y = r.y + bt.cI[j] * (lam * zj.y);
+    const long long base = (long long)f * g.NK + (long long)ky * g.nxh + kx0;
+    const long long zs = (long long)g.ny * g.nxh;
+    const double kyv = g.ky[ky];
+    auto combine = [&](int kz, int col) -> T2 {
+        if (col >= ncol) return T2{0, 0};
+        const long long gi = base + kz * zs + col;
+        const double lam = lam_at(g, ph, f, gi, g.kx[kx0 + col], kyv, g.kz[kz]);
+        double2 r = y[gi];
+        double2 l = make_double2(0.0, 0.0);
+        DS2 rs, ls;
+#pragma unroll
+        for (int j = 0; j < kMaxStages; ++j) {
+            if (j < bt.n) {
+                const bool useI = bt.cI[j] != 0.0 || (want_lte && dt.cI[j] != 0.0);
+                const bool useE = bt.cE[j] != 0.0 || (want_lte && dt.cE[j] != 0.0);
+                if (useI) {
+                    const double2 zj = bt.z[j][gi];
+                    const double2 lz = make_double2(lam * zj.x, lam * zj.y);
+                    if (bt.cI[j] != 0.0) axpy(r, bt.cI[j], lz);
+                    if (want_lte && dt.cI[j] != 0.0) axpy(l, dt.cI[j], lz);
                 }
-                if (bt.cE[j] != 0.0) {
-                    r.x = r.x + bt.cE[j] * fj.x;
-                    r.y = r.y + bt.cE[j] * fj.y;
-                }
-                if (want_lte) {
-                    if (dt.cI[j] != 0.0) {
-                        l.x = l.x + dt.cI[j] * (lam * zj.x);
-                        l.y = l.y + dt.cI[j] * (lam * zj.y);
-                    }
-                    if (dt.cE[j] != 0.0) {
-                        l.x = l.x + dt.cE[j] * fj.x;
-                        l.y = l.y + dt.cE[j] * fj.y;
+                if (useE) {
+                    if (sizeof(T) == 4) {
+                        const float2 fj = reinterpret_cast<const float2*>(bt.f[j])[gi];
+                        if (bt.cE[j] != 0.0) rs.add(bt.cEh[j], bt.cEl[j], fj);
+                        if (want_lte && dt.cE[j] != 0.0) ls.add(dt.cEh[j], dt.cEl[j], fj);
+                    } else {
+                        const double2 fj = load_f<T2>(bt.f[j], gi);
+                        if (bt.cE[j] != 0.0) axpy(r, bt.cE[j], fj);
+                        if (want_lte && dt.cE[j] != 0.0) axpy(l, dt.cE[j], fj);
                     }
                 }
             }
-            ynew[gi] = r;
-            v = from_d2<T2>(l);
         }
-        A[kz * TX + col] = v;
+        if (sizeof(T) == 4) {
+            rs.flush(r);
+            ls.flush(l);
+        }
+        ynew[gi] = r;
+        return from_d2<T2>(l);
+    };
+    if (!want_lte) {
+        for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) combine(e / TX, e & (TX - 1));
+        return;
     }
-    if (!want_lte) return;
-    __syncthreads();
-    T2* res = fft_lines<+1, true>(A, B, g.pz, TX, TX, 1);
-    for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) {
-        const int col = e % TX, kz = e / TX;
-        if (col < ncol) W[fo + ((long long)kz * g.ny + ky) * g.nxh + kx0 + col] = res[kz * TX + col];
-    }
+    auto dst = [&](int kz, int col, T2 v) {
+        if (col < ncol) W[base + kz * zs + col] = v;
+    };
+    fft_cols<+1, TX>(g.pz, A, B, combine, dst);
 }
 
 template <typename T>
@@ -409,9 +487,10 @@ void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageT
     using T2 = typename Cx<T>::t;
     const int TX = tile_cols<T>(g, g.nz, 2, 96 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
-    set_smem(k_z_final<T>, sm);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
-    k_z_final<T><<<grid, kThreads, sm, s>>>(g, ph, y, bterm, dterm, want_lte, ynew, reinterpret_cast<T2*>(W), TX);
+    PF_TX_SWITCH(TX, set_smem(k_z_final<T, TXC>, sm);
+                 k_z_final<T, TXC><<<grid, kThreads, sm, s>>>(g, ph, y, bterm, dterm, want_lte, ynew,
+                                                              reinterpret_cast<T2*>(W)))
 }
 
 // ---------------------------------------------------------------------------
@@ -467,8 +546,9 @@ template <typename T2>
 __device__ __forceinline__ void c2r_load(const Geo& g, const T2* __restrict__ in, int F, int P, int rp0, int npairs,
                                          T2* S, int ls) {
     const int nx = g.nx, nh = nx / 2;
+    const FastDiv dnx((unsigned)nx, g.mul_nx);
     for (int e = threadIdx.x; e < P * F * nx; e += blockDim.x) {
-        const int x = e % nx, line = e / nx, rp = line / F, f = line % F;
+        const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = line / F, f = line - rp * F;
         T2 Z = T2{0, 0};
         if (rp0 + rp < npairs) {
             const long long row = 2LL * (rp0 + rp);
@@ -493,8 +573,9 @@ __device__ __forceinline__ void r2c_store(const Geo& g, const T2* S, int ls, int
                                           T2* __restrict__ out) {
     using T = decltype(T2{}.x);
     const int nx = g.nx, nxh = g.nxh;
+    const FastDiv dnh((unsigned)nxh, g.mul_nxh);
     for (int e = threadIdx.x; e < P * F * nxh; e += blockDim.x) {
-        const int k = e % nxh, line = e / nxh, rp = line / F, f = line % F;
+        const int line = (int)dnh.div((unsigned)e), k = e - line * nxh, rp = line / F, f = line - rp * F;
         if (rp0 + rp >= npairs) continue;
         const T2 Zk = S[line * ls + k];
         const T2 Zm = S[line * ls + (k == 0 ? 0 : nx - k)];
@@ -518,6 +599,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx;
     const int ls = nx;
+    const FastDiv dnx((unsigned)nx, g.mul_nx);
     const int npairs = g.nz * g.ny / 2;
     const int rp0 = blockIdx.x * P;
     T2* S0 = reinterpret_cast<T2*>(smraw);
@@ -531,7 +613,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
     T2* RS = S0;  // real-space lines (a + i b)
     if (mode == XM_R2C_REAL) {
         for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
-            const int x = e % nx, line = e / nx, rp = line / 4, f = line % 4;
+            const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = line >> 2, f = line & 3;
             T2 Z = T2{0, 0};
             if (rp0 + rp < npairs) {
                 const long long row = 2LL * (rp0 + rp);
@@ -554,7 +636,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
 
     if (mode == XM_C2R_REAL) {
         for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
-            const int x = e % nx, line = e / nx, rp = line / 4, f = line % 4;
+            const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = line >> 2, f = line & 3;
             if (rp0 + rp >= npairs) continue;
             const long long row = 2LL * (rp0 + rp);
             const T2 z = RS[line * ls + x];
@@ -568,7 +650,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
     if (mode == XM_WRMS) {
         double acc = 0.0;
         for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
-            const int x = e % nx, line = e / nx, rp = line / 4, f = line % 4;
+            const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = line >> 2, f = line & 3;
             if (rp0 + rp >= npairs) continue;
             const long long row = 2LL * (rp0 + rp);
             const T2 z = RS[line * ls + x];
@@ -594,7 +676,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
     double eacc = 0.0;
     const bool full_rhs = (mode == XM_PHYS2) || (mode == XM_PHYS1 && !ph.elastic);
     for (int e = threadIdx.x; e < P * nx; e += blockDim.x) {
-        const int x = e % nx, rp = e / nx;
+        const int rp = (int)dnx.div((unsigned)e), x = e - rp * nx;
         if (rp0 + rp >= npairs) continue;
         const long long row = 2LL * (rp0 + rp);
         T Xr[2], pr[2][3], er[2][3];
@@ -710,6 +792,45 @@ static int x_rows(const Geo& g) {
     return P;
 }
 
+bool make_axis_plan(int n, AxisPlan& p) {
+    int m = n, a = 0, b = 0, c = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    while (m % 3 == 0) { m /= 3; ++b; }
+    while (m % 5 == 0) { m /= 5; ++c; }
+    if (m != 1) return false;
+    int r[kMaxRadices + 8];
+    int nr = 0;
+    int n8 = a / 3;
+    const int rem = a % 3;
+    int head = 0;
+    if (rem == 1 && n8 > 0) {  // 2^(3k+1): prefer 4*4 over 8*2
+        --n8;
+        head = 2;
+    }
+    for (int i = 0; i < n8; ++i) r[nr++] = 8;
+    if (head == 2) {
+        r[nr++] = 4;
+        r[nr++] = 4;
+    } else if (rem == 2) {
+        r[nr++] = 4;
+    } else if (rem == 1) {
+        r[nr++] = 2;
+    }
+    for (int i = 0; i < b; ++i) r[nr++] = 3;
+    for (int i = 0; i < c; ++i) r[nr++] = 5;
+    if (nr > kMaxRadices) return false;
+    p.n = n;
+    p.nst = nr;
+    unsigned Ns = 1;
+    for (int s = 0; s < nr; ++s) {
+        p.rad[s] = r[s];
+        p.mulm[s] = magic_u32((unsigned)(n / r[s]));
+        p.mulN[s] = magic_u32(Ns);
+        Ns *= (unsigned)r[s];
+    }
+    return true;
+}
+
 int x_pass_blocks(const Geo& g, int f64) {
     const int P = f64 ? x_rows<double>(g) : x_rows<float>(g);
     const int npairs = g.nz * g.ny / 2;
@@ -744,30 +865,20 @@ __global__ void k_stage_pointwise(Geo g, Phys ph, const double2* __restrict__ y,
         const int kx = (int)(r % g.nxh);
         const int ky = (int)((r / g.nxh) % g.ny);
         const int kz = (int)(r / ((long long)g.nxh * g.ny));
-        const double lam = lambda_k(ph, f, g.kx[kx], g.ky[ky], g.kz[kz]);
+        const double lam = lam_at(g, ph, f, gi, g.kx[kx], g.ky[ky], g.kz[kz]);
         double2 v = y[gi];
-        for (int j = 0; j < st.n; ++j) {
-            if (st.cI[j] != 0.0) {
-                const double2 zj = st.z[j][gi];
-                v.x = v.x + st.cI[j] * (lam * zj.x);
-                v.y = v.y + st.cI[j] * (lam * zj.y);
-            }
-            if (st.cE[j] != 0.0) {
-                double2 fj;
-                if (fe32) {
-                    const float2 a = reinterpret_cast<const float2*>(st.f[j])[gi];
-                    fj = make_double2(a.x, a.y);
-                } else {
-                    fj = reinterpret_cast<const double2*>(st.f[j])[gi];
-                }
-                v.x = v.x + st.cE[j] * fj.x;
-                v.y = v.y + st.cE[j] * fj.y;
+#pragma unroll
+        for (int j = 0; j < kMaxStages; ++j) {
+            if (j < st.n) {
+                if (st.cI[j] != 0.0) axpy(v, st.cI[j] * lam, st.z[j][gi]);
+                if (st.cE[j] != 0.0)
+                    axpy(v, st.cE[j], fe32 ? load_f<float2>(st.f[j], gi) : load_f<double2>(st.f[j], gi));
             }
         }
         if (st.gamma != 0.0) {
-            const double den = 1.0 - st.gamma * lam;
-            v.x = v.x / den;
-            v.y = v.y / den;
+            const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - st.gamma * lam);
+            v.x *= q;
+            v.y *= q;
         }
         zout[gi] = v;
     }
@@ -795,6 +906,23 @@ __global__ void k_solve(Geo g, Phys ph, double gamma, const double2* r, double2*
 
 void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s) {
     k_solve<<<152 * 8, 256, 0, s>>>(g, ph, gamma, r, z);
+}
+
+__global__ void k_lambda_table(Geo g, Phys ph, double* __restrict__ lam) {
+    const long long total = 4LL * g.NK;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(gi / g.NK);
+        const long long q = gi % g.NK;
+        const int kx = (int)(q % g.nxh);
+        const int ky = (int)((q / g.nxh) % g.ny);
+        const int kz = (int)(q / ((long long)g.nxh * g.ny));
+        lam[gi] = lambda_k(ph, f, g.kx[kx], g.ky[ky], g.kz[kz]);
+    }
+}
+
+void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, cudaStream_t s) {
+    k_lambda_table<<<152 * 8, 256, 0, s>>>(g, ph, lam);
 }
 
 // deterministic single-CTA reduction: out = sum(partials) * scale (FP64)

@@ -83,34 +83,7 @@ bool smooth_even_axis(int n) {
     return m == 1;
 }
 
-// Same radix schedule and twiddle construction as the context path.
-bool plan_axis(int n, AxisPlan& p) {
-    int m = n, a = 0, b = 0, c = 0;
-    while (m % 2 == 0) { m /= 2; ++a; }
-    while (m % 3 == 0) { m /= 3; ++b; }
-    while (m % 5 == 0) { m /= 5; ++c; }
-    if (m != 1) return false;
-    std::vector<int> r;
-    int n8 = a / 3, rem = a % 3;
-    if (rem == 1 && n8 > 0) {
-        --n8;
-        r.push_back(4);
-        r.push_back(4);
-    } else if (rem == 2) {
-        r.push_back(4);
-    } else if (rem == 1) {
-        r.push_back(2);
-    }
-    for (int i = 0; i < n8; ++i) r.insert(r.begin(), 8);
-    for (int i = 0; i < b; ++i) r.push_back(3);
-    for (int i = 0; i < c; ++i) r.push_back(5);
-    if ((int)r.size() > kMaxRadices) return false;
-    p.n = n;
-    p.nst = (int)r.size();
-    for (int i = 0; i < p.nst; ++i) p.rad[i] = r[i];
-    return true;
-}
-
+// Twiddles exactly as the context path builds them.
 void twiddles(int n, double2* tw, float2* tw32) {
     for (int k = 0; k < n; ++k) {
         const long double th = 2.0L * 3.141592653589793238462643383279502884L * ((long double)k / (long double)n);
@@ -153,6 +126,8 @@ int pf_state_to_real_noalloc(const pf_grid* grid, const void* y_hat, double* fie
     g.nxh = g.nx / 2 + 1;
     g.NK = NK;
     g.N = (long long)g.nz * g.ny * g.nx;
+    g.mul_nx = magic_u32((unsigned)g.nx);
+    g.mul_nxh = magic_u32((unsigned)g.nxh);
     AxisPlan* plans[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     const double ds[3] = {grid->dx, grid->dy, grid->dz};
@@ -161,7 +136,8 @@ int pf_state_to_real_noalloc(const pf_grid* grid, const void* y_hat, double* fie
     static thread_local float2 htw32[3][kNoallocMaxAxis];
     static thread_local double hk[3][kNoallocMaxAxis];
     for (int a = 0; a < 3; ++a) {
-        if (!plan_axis(ns[a], *plans[a])) return err(PF_EUNSUPPORTED, "pf_state_to_real_noalloc: cannot factor size");
+        if (!make_axis_plan(ns[a], *plans[a]))
+            return err(PF_EUNSUPPORTED, "pf_state_to_real_noalloc: cannot factor size");
         twiddles(ns[a], htw[a], htw32[a]);
         const bool half = (a == 0);
         const int len = half ? ns[a] / 2 + 1 : ns[a];
