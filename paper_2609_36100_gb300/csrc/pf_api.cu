@@ -146,6 +146,7 @@ struct pf_ctx {
     bool alias_y[kMaxStages] = {};  // z_i == y_{n-1} exactly (explicit first stage)
     // device memory
     double *d_kx = nullptr, *d_ky = nullptr, *d_kz = nullptr;
+    float* d_k32 = nullptr;  // kx | ky | kz in FP32
     double2* d_tw64[3] = {};
     float2* d_tw32[3] = {};
     double2* y = nullptr;
@@ -265,6 +266,7 @@ void free_all(pf_ctx* c) {
     cudaFree(c->d_kx);
     cudaFree(c->d_ky);
     cudaFree(c->d_kz);
+    cudaFree(c->d_k32);
     for (int i = 0; i < 3; ++i) {
         cudaFree(c->d_tw64[i]);
         cudaFree(c->d_tw32[i]);
@@ -299,6 +301,16 @@ int dalloc(pf_ctx* c, P** p, size_t bytes) {
 }
 
 double2* fp64_scratch(pf_ctx* c) { return c->zhat[c->tab.s - 1]; }
+
+// integer flags of the nonzero coefficients (tested per element on device)
+void set_masks(StageTerms& st) {
+    st.mI = st.mE = 0u;
+    for (int j = 0; j < st.n; ++j) {
+        if (st.cI[j] != 0.0) st.mI |= 1u << j;
+        if (st.cE[j] != 0.0) st.mE |= 1u << j;
+    }
+    st.has_gamma = st.gamma != 0.0 ? 1 : 0;
+}
 
 // c = hi + lo with hi = fl32(c): the double-single form of an FP64 stage
 // coefficient that multiplies FP32 terms
@@ -353,6 +365,7 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte) {
         }
         st.gamma = dt * tb.AI[i][i];
         for (int j = 0; j < i; ++j) split_ds(st.cE[j], st.cEh[j], st.cEl[j]);
+        set_masks(st);
         if (c->gdiag != 0.0) {
             if (i == 0) {
                 st.qout = c->qtab;
@@ -428,6 +441,8 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte) {
         }
         split_ds(bt.cE[j], bt.cEh[j], bt.cEl[j]);
         split_ds(dtm.cE[j], dtm.cEh[j], dtm.cEl[j]);
+        set_masks(bt);
+        set_masks(dtm);
         const bool zI = bt.cI[j] != 0.0 || (lte && dtm.cI[j] != 0.0);
         const bool fEn = bt.cE[j] != 0.0 || (lte && dtm.cE[j] != 0.0);
         fterms += (zI && !(c->alias_y[j]) ? 16.0 : 0.0) + (fEn ? (c->fp32 ? 8.0 : 16.0) : 0.0);
@@ -623,6 +638,7 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     rc = rc ? rc : dalloc(c, &c->d_kx, kx.size() * sizeof(double));
     rc = rc ? rc : dalloc(c, &c->d_ky, ky.size() * sizeof(double));
     rc = rc ? rc : dalloc(c, &c->d_kz, kz.size() * sizeof(double));
+    rc = rc ? rc : dalloc(c, &c->d_k32, (kx.size() + ky.size() + kz.size()) * sizeof(float));
     for (int a = 0; a < 3 && !rc; ++a) {
         rc = rc ? rc : dalloc(c, &c->d_tw64[a], ns[a] * sizeof(double2));
         rc = rc ? rc : dalloc(c, &c->d_tw32[a], ns[a] * sizeof(float2));
@@ -657,6 +673,13 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     e = e ? e : cudaMemcpy(c->d_kx, kx.data(), kx.size() * sizeof(double), cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(c->d_ky, ky.data(), ky.size() * sizeof(double), cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(c->d_kz, kz.data(), kz.size() * sizeof(double), cudaMemcpyHostToDevice);
+    {
+        std::vector<float> k32;
+        for (double v : kx) k32.push_back((float)v);
+        for (double v : ky) k32.push_back((float)v);
+        for (double v : kz) k32.push_back((float)v);
+        e = e ? e : cudaMemcpy(c->d_k32, k32.data(), k32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     for (int a = 0; a < 3 && !e; ++a) {
         std::vector<double2> tw;
         twiddle_table(ns[a], tw);
@@ -686,6 +709,9 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     g.kx = c->d_kx;
     g.ky = c->d_ky;
     g.kz = c->d_kz;
+    g.kx32 = c->d_k32;
+    g.ky32 = c->d_k32 + kx.size();
+    g.kz32 = c->d_k32 + kx.size() + ky.size();
     c->t = 0.0;
     c->h = params->h0;
     c->st.h = c->h;

@@ -36,6 +36,9 @@ struct Geo {
     const double* ky;  // [ny]
     const double* kz;  // [nz]
     const double* lam;  // [4][NK] lambda(k) per field (FP64), or null (computed on the fly)
+    const float* kx32;  // FP32 copies of the wave-number tables (FP32-bulk kernels)
+    const float* ky32;
+    const float* kz32;
     AxisPlan px, py, pz;
     unsigned mul_nx, mul_nxh;  // division magic for nx and nx/2+1
     int tx_y, tx_z, tx_el;  // tile widths (kx columns) of the strided passes
@@ -62,6 +65,9 @@ struct Phys {
 // Coefficients of one stage assembly / step completion pass.
 struct StageTerms {
     int n;                             // number of previous-stage terms
+    unsigned mI, mE;                   // bit j set: cI[j] / cE[j] nonzero (integer tests keep
+                                       // the per-element branches off the FP64 pipe)
+    int has_gamma;                     // gamma != 0
     const double2* z[kMaxStages];      // stage vectors z_j (FP64)
     const void* f[kMaxStages];         // f^E_j (compute type)
     double cI[kMaxStages];             // dt * A^I_ij (or dt * b^I_j)

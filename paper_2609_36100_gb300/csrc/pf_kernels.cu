@@ -61,6 +61,42 @@ __device__ __forceinline__ void axpy(double2& r, double c, double2 v) {
     r.y = fma(c, v.y, r.y);
 }
 
+// Exact float -> double by bit manipulation (FP32 subnormals flush to zero),
+// keeping the conversion off the FP64 pipe.
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned ex = (u >> 23) & 0xffu, sign = u & 0x80000000u, man = u & 0x7fffffu;
+    if (ex == 0u) return __hiloint2double((int)sign, 0);
+    unsigned hi;
+    if (ex == 0xffu)
+        hi = sign | 0x7ff00000u | (man >> 3) | (man ? 0x80000u : 0u);
+    else
+        hi = sign | ((ex + 896u) << 20) | (man >> 3);
+    return __hiloint2double((int)hi, (int)(man << 29));
+}
+
+// double -> float, round to nearest even, by bit manipulation (results below
+// the FP32 normal range flush to zero).
+__device__ __forceinline__ float d2f_bits(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
+    int fe = e - 896;
+    if (fe <= 0) return __uint_as_float(sign);
+    unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu, half = 0x10000000u;
+    if (rem > half || (rem == half && (m & 1u))) {
+        m += 1u;
+        if (m == 0x800000u) {
+            m = 0u;
+            ++fe;
+        }
+    }
+    if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)fe << 23) | m);
+}
+
 // Double-single accumulation (hi, lo) += (ch + cl) * f for an FP32 value f:
 // the product ch*f is split exactly with an FMA, cl*f is added to its error,
 // and the sum uses the two-sum error-free transformation (no contraction:
@@ -84,8 +120,8 @@ struct DS2 {
         ds_add_prod(yh, yl, ch, cl, f.y);
     }
     __device__ __forceinline__ void flush(double2& r) const {
-        r.x += (double)xh + (double)xl;
-        r.y += (double)yh + (double)yl;
+        r.x += f2d_bits(xh) + f2d_bits(xl);
+        r.y += f2d_bits(yh) + f2d_bits(yl);
     }
 };
 
@@ -93,6 +129,62 @@ __device__ __forceinline__ double lam_at(const Geo& g, const Phys& ph, int f, lo
                                          double kz) {
     return g.lam ? g.lam[gi] : lambda_k(ph, f, kx, ky, kz);
 }
+
+// Model constants in the compute type, converted once per thread (a
+// per-element double->float conversion would run on the narrow FP64 pipe).
+template <typename T>
+struct PhysT {
+    T Bv, Bm, inv2Av, inv2Am, A0m, A0v, Am, Av, wb2, ie, twoAm;
+    T w[3][3];
+    T C44, Cm, Ca;
+    T sig[3][6];
+    T cvq[3][3];
+    __device__ __forceinline__ explicit PhysT(const Phys& ph) {
+        Bv = (T)ph.Bv;
+        Bm = (T)ph.Bm;
+        inv2Av = (T)ph.inv2Av;
+        inv2Am = (T)ph.inv2Am;
+        A0m = (T)ph.A0m;
+        A0v = (T)ph.A0v;
+        Am = (T)ph.Am;
+        Av = (T)ph.Av;
+        wb2 = (T)(2.0 * ph.wbar);
+        ie = (T)(1.0 / ph.pair_eps);
+        twoAm = (T)(2.0 * ph.Am);
+        C44 = (T)ph.C44;
+        Cm = (T)ph.Cmix;
+        Ca = (T)ph.Caniso;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                w[a][b] = (T)ph.w[a][b];
+                cvq[a][b] = (T)ph.cvq[a][b];
+            }
+#pragma unroll
+            for (int b = 0; b < 6; ++b) sig[a][b] = (T)ph.sig[a][b];
+        }
+    }
+};
+
+// wave number of axis a (0 = x half spectrum, 1 = y, 2 = z) in the compute type
+template <typename T>
+__device__ __forceinline__ T kval(const Geo& g, int a, int i);
+template <>
+__device__ __forceinline__ double kval<double>(const Geo& g, int a, int i) {
+    return a == 0 ? g.kx[i] : (a == 1 ? g.ky[i] : g.kz[i]);
+}
+template <>
+__device__ __forceinline__ float kval<float>(const Geo& g, int a, int i) {
+    return a == 0 ? g.kx32[i] : (a == 1 ? g.ky32[i] : g.kz32[i]);
+}
+
+template <typename T2>
+__device__ __forceinline__ T2 narrow(double2 a);
+template <>
+__device__ __forceinline__ double2 narrow<double2>(double2 a) { return a; }
+template <>
+__device__ __forceinline__ float2 narrow<float2>(double2 a) { return make_float2(d2f_bits(a.x), d2f_bits(a.y)); }
 
 template <typename T>
 static int strided_tile(int n, int nbuf, int budget) {
@@ -164,11 +256,12 @@ __global__ void __launch_bounds__(kThreads) k_z_stage(Geo g, Phys ph, const doub
         double2 r = y[gi];
         const double lam = lam_at(g, ph, f, gi, g.kx[kx0 + col], kyv, g.kz[kz]);
         DS2 fs;
+        double2 zi = make_double2(0.0, 0.0);  // sum_j (dt A^I_ij) z_j, times lambda below
 #pragma unroll
         for (int j = 0; j < kMaxStages; ++j) {
             if (j < st.n) {
-                if (st.cI[j] != 0.0) axpy(r, st.cI[j] * lam, st.z[j][gi]);
-                if (st.cE[j] != 0.0) {
+                if ((st.mI >> j) & 1u) axpy(zi, st.cI[j], st.z[j][gi]);
+                if ((st.mE >> j) & 1u) {
                     if (sizeof(T) == 4)
                         fs.add(st.cEh[j], st.cEl[j], reinterpret_cast<const float2*>(st.f[j])[gi]);
                     else
@@ -176,15 +269,16 @@ __global__ void __launch_bounds__(kThreads) k_z_stage(Geo g, Phys ph, const doub
                 }
             }
         }
+        axpy(r, lam, zi);
         if (sizeof(T) == 4) fs.flush(r);
         if (st.qout) st.qout[gi] = 1.0 / (1.0 - st.qgamma * lam);
-        if (st.gamma != 0.0) {
+        if (st.has_gamma) {
             const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - st.gamma * lam);
             r.x *= q;
             r.y *= q;
         }
         if (zout) zout[gi] = r;
-        return from_d2<T2>(r);
+        return narrow<T2>(r);
     };
     auto dst = [&](int kz, int col, T2 v) {
         if (col < ncol) W[base + kz * zs + col] = v;
@@ -257,7 +351,8 @@ __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typena
     const long long base = (long long)f * g.NK + (long long)ky * g.nxh + kx0;
     const long long zs = (long long)g.ny * g.nxh;
     const double invN = 1.0 / (double)g.N;
-    const double kyv = g.ky[ky];
+    const T mN = (T)(-ph.M * invN), lN = (T)(-ph.L * invN);
+    const T kyv = kval<T>(g, 1, ky);
     auto src = [&](int kz, int col) -> T2 { return col < ncol ? W[base + kz * zs + col] : T2{0, 0}; };
     auto dst = [&](int kz, int col, T2 v) {
         if (col >= ncol) return;
@@ -267,10 +362,10 @@ __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typena
         } else {
             T sc;
             if (f == 0) {
-                const double kx = g.kx[kx0 + col], kzv = g.kz[kz];
-                sc = (T)(-ph.M * (kx * kx + kyv * kyv + kzv * kzv) * invN);
+                const T kx = kval<T>(g, 0, kx0 + col), kzv = kval<T>(g, 2, kz);
+                sc = mN * (kx * kx + kyv * kyv + kzv * kzv);
             } else {
-                sc = (T)(-ph.L * invN);
+                sc = lN;
             }
             out[gi] = OT2{(OT)(v.x * sc), (OT)(v.y * sc)};
         }
@@ -303,8 +398,8 @@ void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int sc
 //   Omega^{-1}_ik = C44 d_ik + (C12 + C44) n_i n_k + (C11 - C12 - 2 C44) d_ik n_i^2
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void elastic_kernel(const Phys& ph, double kx, double ky, double kz, T Bm[3][3]) {
-    const T k2 = (T)(kx * kx + ky * ky + kz * kz);
+__device__ __forceinline__ void elastic_kernel(const PhysT<T>& pt, T kx, T ky, T kz, T Bm[3][3]) {
+    const T k2 = kx * kx + ky * ky + kz * kz;
     if (k2 == (T)0) {
 #pragma unroll
         for (int v = 0; v < 3; ++v)
@@ -313,8 +408,8 @@ __device__ __forceinline__ void elastic_kernel(const Phys& ph, double kx, double
         return;
     }
     const T inv = (T)1 / sqrt(k2);
-    const T n0 = (T)kx * inv, n1 = (T)ky * inv, n2 = (T)kz * inv;
-    const T C44 = (T)ph.C44, Cm = (T)ph.Cmix, Ca = (T)ph.Caniso;
+    const T n0 = kx * inv, n1 = ky * inv, n2 = kz * inv;
+    const T C44 = pt.C44, Cm = pt.Cm, Ca = pt.Ca;
     const T a = C44 + Cm * n0 * n0 + Ca * n0 * n0;
     const T b = C44 + Cm * n1 * n1 + Ca * n1 * n1;
     const T c = C44 + Cm * n2 * n2 + Ca * n2 * n2;
@@ -326,10 +421,10 @@ __device__ __forceinline__ void elastic_kernel(const Phys& ph, double kx, double
     T s[3][3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-        const double* S = ph.sig[v];  // xx yy zz yz xz xy
-        s[v][0] = (T)S[0] * n0 + (T)S[5] * n1 + (T)S[4] * n2;
-        s[v][1] = (T)S[5] * n0 + (T)S[1] * n1 + (T)S[3] * n2;
-        s[v][2] = (T)S[4] * n0 + (T)S[3] * n1 + (T)S[2] * n2;
+        const T* S = pt.sig[v];  // xx yy zz yz xz xy
+        s[v][0] = S[0] * n0 + S[5] * n1 + S[4] * n2;
+        s[v][1] = S[5] * n0 + S[1] * n1 + S[3] * n2;
+        s[v][2] = S[4] * n0 + S[3] * n1 + S[2] * n2;
     }
     T Os[3][3];  // Omega s_q
 #pragma unroll
@@ -342,7 +437,7 @@ __device__ __forceinline__ void elastic_kernel(const Phys& ph, double kx, double
     for (int v = 0; v < 3; ++v)
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            Bm[v][q] = (T)ph.cvq[v][q] - (s[v][0] * Os[q][0] + s[v][1] * Os[q][1] + s[v][2] * Os[q][2]);
+            Bm[v][q] = pt.cvq[v][q] - (s[v][0] * Os[q][0] + s[v][1] * Os[q][1] + s[v][2] * Os[q][2]);
 }
 
 template <typename T, int TX>
@@ -375,12 +470,13 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
         __syncthreads();
     }
     const T invN = (T)(1.0 / (double)g.N);
-    const double kyv = g.ky[ky];
+    const PhysT<T> pt(ph);
+    const T kyv = kval<T>(g, 1, ky);
     for (int r = threadIdx.x; r < tile; r += blockDim.x) {
         const int col = r & (TX - 1), kz = r / TX;
         if (col >= ncol) continue;
         T Bm[3][3];
-        elastic_kernel<T>(ph, g.kx[kx0 + col], kyv, g.kz[kz], Bm);
+        elastic_kernel<T>(pt, kval<T>(g, 0, kx0 + col), kyv, kval<T>(g, 2, kz), Bm);
         const T2 h0 = slot[0][r], h1 = slot[1][r], h2 = slot[2][r];
         slot[0][r] = T2{(Bm[0][0] * h0.x + Bm[0][1] * h1.x + Bm[0][2] * h2.x) * invN,
                         (Bm[0][0] * h0.y + Bm[0][1] * h1.y + Bm[0][2] * h2.y) * invN};
@@ -408,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
 template <typename T>
 void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
-    const int TX = tile_cols<T>(g, g.nz, 4, 128 * 1024);
+    const int TX = tile_cols<T>(g, g.nz, 4, 64 * 1024);
     const size_t sm = 4 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);
     PF_TX_SWITCH(TX, set_smem(k_z_elastic<T, TXC>, sm);
@@ -439,37 +535,39 @@ __global__ void __launch_bounds__(kThreads) k_z_final(Geo g, Phys ph, const doub
         const double lam = lam_at(g, ph, f, gi, g.kx[kx0 + col], kyv, g.kz[kz]);
         double2 r = y[gi];
         double2 l = make_double2(0.0, 0.0);
+        double2 zr = make_double2(0.0, 0.0), zl = make_double2(0.0, 0.0);  // times lambda below
         DS2 rs, ls;
 #pragma unroll
         for (int j = 0; j < kMaxStages; ++j) {
             if (j < bt.n) {
-                const bool useI = bt.cI[j] != 0.0 || (want_lte && dt.cI[j] != 0.0);
-                const bool useE = bt.cE[j] != 0.0 || (want_lte && dt.cE[j] != 0.0);
-                if (useI) {
+                const bool bI = (bt.mI >> j) & 1u, bE = (bt.mE >> j) & 1u;
+                const bool lI = want_lte && ((dt.mI >> j) & 1u), lE = want_lte && ((dt.mE >> j) & 1u);
+                if (bI || lI) {
                     const double2 zj = bt.z[j][gi];
-                    const double2 lz = make_double2(lam * zj.x, lam * zj.y);
-                    if (bt.cI[j] != 0.0) axpy(r, bt.cI[j], lz);
-                    if (want_lte && dt.cI[j] != 0.0) axpy(l, dt.cI[j], lz);
+                    if (bI) axpy(zr, bt.cI[j], zj);
+                    if (lI) axpy(zl, dt.cI[j], zj);
                 }
-                if (useE) {
+                if (bE || lE) {
                     if (sizeof(T) == 4) {
                         const float2 fj = reinterpret_cast<const float2*>(bt.f[j])[gi];
-                        if (bt.cE[j] != 0.0) rs.add(bt.cEh[j], bt.cEl[j], fj);
-                        if (want_lte && dt.cE[j] != 0.0) ls.add(dt.cEh[j], dt.cEl[j], fj);
+                        if (bE) rs.add(bt.cEh[j], bt.cEl[j], fj);
+                        if (lE) ls.add(dt.cEh[j], dt.cEl[j], fj);
                     } else {
                         const double2 fj = load_f<T2>(bt.f[j], gi);
-                        if (bt.cE[j] != 0.0) axpy(r, bt.cE[j], fj);
-                        if (want_lte && dt.cE[j] != 0.0) axpy(l, dt.cE[j], fj);
+                        if (bE) axpy(r, bt.cE[j], fj);
+                        if (lE) axpy(l, dt.cE[j], fj);
                     }
                 }
             }
         }
+        axpy(r, lam, zr);
+        axpy(l, lam, zl);
         if (sizeof(T) == 4) {
             rs.flush(r);
             ls.flush(l);
         }
         ynew[gi] = r;
-        return from_d2<T2>(l);
+        return narrow<T2>(l);
     };
     if (!want_lte) {
         for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) combine(e / TX, e & (TX - 1));
@@ -503,7 +601,7 @@ void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageT
 struct Pt {
     // real-space physics at one point (Sec. 4.1); returns q and g_v
     template <typename T>
-    __device__ __forceinline__ static void rhs(const Phys& ph, T X, const T* p, const T* e, T& q, T* gv) {
+    __device__ __forceinline__ static void rhs(const PhysT<T>& pt, T X, const T* p, const T* e, T& q, T* gv) {
         T h[3], hp[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
@@ -512,29 +610,27 @@ struct Pt {
             hp[v] = (T)30 * f * f * ((T)1 - f) * ((T)1 - f);
         }
         const T H = h[0] + h[1] + h[2];
-        const T Bv = (T)ph.Bv, Bm = (T)ph.Bm;
-        const T denom = H * (T)ph.inv2Av + ((T)1 - H) * (T)ph.inv2Am;
+        const T Bv = pt.Bv, Bm = pt.Bm;
+        const T denom = H * pt.inv2Av + ((T)1 - H) * pt.inv2Am;
         const T mu = (X - H * Bv - ((T)1 - H) * Bm) / denom;
-        const T Xm = mu * (T)ph.inv2Am + Bm;
-        const T Xv = mu * (T)ph.inv2Av + Bv;
-        const T fm = (T)ph.A0m + (T)ph.Am * (Xm - Bm) * (Xm - Bm);
-        const T fv = (T)ph.A0v + (T)ph.Av * (Xv - Bv) * (Xv - Bv);
+        const T Xm = mu * pt.inv2Am + Bm;
+        const T Xv = mu * pt.inv2Av + Bv;
+        const T fm = pt.A0m + pt.Am * (Xm - Bm) * (Xm - Bm);
+        const T fv = pt.A0v + pt.Av * (Xv - Bv) * (Xv - Bv);
         const T drive = fv - fm - mu * (Xv - Xm);
-        const T wb2 = (T)(2.0 * ph.wbar);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
             const T f = p[v];
-            T d = wb2 * f * ((T)1 - f) * ((T)1 - (T)2 * f);
-            const T ie = (T)(1.0 / ph.pair_eps);
+            T d = pt.wb2 * f * ((T)1 - f) * ((T)1 - (T)2 * f);
 #pragma unroll
             for (int qq = 0; qq < 3; ++qq)
                 if (qq != v) {
-                    const T sl = fmin((T)1, fmax((T)-1, f * p[qq] * ie));
-                    d += (T)ph.w[v][qq] * sl * p[qq];
+                    const T sl = fmin((T)1, fmax((T)-1, f * p[qq] * pt.ie));
+                    d += pt.w[v][qq] * sl * p[qq];
                 }
             gv[v] = d + hp[v] * drive + hp[v] * e[v];
         }
-        q = mu - (T)(2.0 * ph.Am) * X;
+        q = mu - pt.twoAm * X;
     }
 };
 
@@ -600,6 +696,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
     const int nx = g.nx;
     const int ls = nx;
     const FastDiv dnx((unsigned)nx, g.mul_nx);
+    const PhysT<T> pt(ph);
     const int npairs = g.nz * g.ny / 2;
     const int rp0 = blockIdx.x * P;
     T2* S0 = reinterpret_cast<T2*>(smraw);
@@ -655,10 +752,18 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
             const long long row = 2LL * (rp0 + rp);
             const T2 z = RS[line * ls + x];
             const T* yr = Rin + (long long)f * g.N + row * nx + x;
-            const double w0 = 1.0 / (rtol * fabs((double)yr[0]) + atol);
-            const double w1 = 1.0 / (rtol * fabs((double)yr[nx]) + atol);
-            const double a = (double)z.x * w0, b = (double)z.y * w1;
-            acc += a * a + b * b;
+            // weighted error w_i * LTE_i formed in the compute type (the
+            // error and y_{n-1} are already compute-type fields); squares
+            // accumulated in FP64
+            const T rt = (T)rtol, at = (T)atol;
+            const T a = z.x / (rt * fabs(yr[0]) + at), b = z.y / (rt * fabs(yr[nx]) + at);
+            if (sizeof(T) == 4) {
+                const double da = f2d_bits((float)a), db = f2d_bits((float)b);
+                acc = fma(da, da, acc);
+                acc = fma(db, db, acc);
+            } else {
+                acc += (double)a * (double)a + (double)b * (double)b;
+            }
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -727,7 +832,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
         if (full_rhs) {
             T q[2], gv[2][3];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) Pt::rhs<T>(ph, Xr[r], pr[r], er[r], q[r], gv[r]);
+            for (int r = 0; r < 2; ++r) Pt::rhs<T>(pt, Xr[r], pr[r], er[r], q[r], gv[r]);
             OS[(rp * 4 + 0) * ls + x] = T2{q[0], q[1]};
 #pragma unroll
             for (int v = 0; v < 3; ++v) OS[(rp * 4 + 1 + v) * ls + x] = T2{gv[0][v], gv[1][v]};
@@ -870,12 +975,12 @@ __global__ void k_stage_pointwise(Geo g, Phys ph, const double2* __restrict__ y,
 #pragma unroll
         for (int j = 0; j < kMaxStages; ++j) {
             if (j < st.n) {
-                if (st.cI[j] != 0.0) axpy(v, st.cI[j] * lam, st.z[j][gi]);
-                if (st.cE[j] != 0.0)
+                if ((st.mI >> j) & 1u) axpy(v, st.cI[j] * lam, st.z[j][gi]);
+                if ((st.mE >> j) & 1u)
                     axpy(v, st.cE[j], fe32 ? load_f<float2>(st.f[j], gi) : load_f<double2>(st.f[j], gi));
             }
         }
-        if (st.gamma != 0.0) {
+        if (st.has_gamma) {
             const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - st.gamma * lam);
             v.x *= q;
             v.y *= q;
@@ -964,7 +1069,8 @@ __global__ void k_energy_k(Geo g, Phys ph, const double2* __restrict__ y, const 
         }
         if (ph.elastic) {
             double Bm[3][3];
-            elastic_kernel<double>(ph, KX, KY, KZ, Bm);
+            const PhysT<double> pt(ph);
+            elastic_kernel<double>(pt, KX, KY, KZ, Bm);
             double2 h[3];
             for (int v = 0; v < 3; ++v) h[v] = hk[(long long)v * g.NK + r];
             for (int v = 0; v < 3; ++v)
