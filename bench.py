@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 path")
+    ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble measurement (0: skip)")
+    ap.add_argument("--ensemble-t", type=float, default=3.0, help="simulated seconds of the ensemble measurement")
     return ap.parse_args()
 
 
@@ -242,6 +244,51 @@ def run_ours(args, rank, world, dist):
     return line
 
 
+def run_ensemble(K, t_final):
+    """Uneven-grid ensemble (members 0..K-1 of the seeded recipe: sides from
+    {64,96,120,128,160}, 4-24 nuclei, T0 +/- 20 K), FP32-bulk ARK4 adaptive at
+    rtol 1e-4: all members one after another with pf_advance, then the same
+    states advanced together with pf_batch_advance."""
+    import torch
+
+    import paper_2609_36100_gb300 as pfg
+    import synth
+
+    mem = [synth.ensemble_member(i) for i in range(K)]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        sims = []
+        for y0, p in mem:
+            s = pfg.Simulation(y0.shape[1:], p, "ark4", "fp32bulk")
+            s.set_state(y0)
+            s.set_time(0.0, 1.0)
+            sims.append(s)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(sims)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = [s.stats() for s in sims]
+        for s in sims:
+            s.close()
+        return e0.elapsed_time(e1), st
+
+    ms_seq, st_seq = timed(lambda sims: [s.advance(t_final, 1e-4, 1e-8) for s in sims])
+    ms_bat, st_bat = timed(lambda sims: pfg.batch_advance(sims, t_final, 1e-4, 1e-8))
+    ps_seq = sum(x["point_stages"] for x in st_seq)
+    ps_bat = sum(x["point_stages"] for x in st_bat)
+    sides = sorted({int(y0.shape[1]) for y0, _ in mem})
+    return {"members": K, "sides": sides, "points": int(sum(y0[0].size for y0, _ in mem)), "t_final": t_final,
+            "sequential": {"ms": ms_seq, "gpt_stage_s": ps_seq / (ms_seq / 1e3) / 1e9,
+                           "sim_s_per_wall_s": K * t_final / (ms_seq / 1e3)},
+            "batched": {"ms": ms_bat, "gpt_stage_s": ps_bat / (ms_bat / 1e3) / 1e9,
+                        "sim_s_per_wall_s": K * t_final / (ms_bat / 1e3)},
+            "gain_batched_vs_sequential": ms_seq / ms_bat}
+
+
 def cpu_baseline(n, budget_s=15.0):
     """The FP64 oracle as it stands, timed on this host's cores on a bounded
     sample: explicit RHS evaluations of the same 256^3 workload."""
@@ -313,6 +360,8 @@ def main():
         td.init_process_group("nccl")
         dist = td
     line = run_ours(args, rank, world, dist)
+    if args.ensemble > 0:
+        line["ensemble"] = run_ensemble(args.ensemble, args.ensemble_t)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.n)

@@ -191,6 +191,46 @@ const char* pf_kernel_name(int kind);
  * or PF_EUNSUPPORTED. Buffers must hold s*s (A) and s (b) doubles; s <= 8. */
 int pf_method_tableau(int method, double* AE, double* AI, double* bE, double* bI, double* btE, double* btI);
 
+/* ---------------------------------------------------------------------------
+ * Fourier-neural-operator surrogate (not in the paper).  The network maps the
+ * normalised 4-field real-space state to the normalised state change over a
+ * horizon tau; all layers, gradients and the Adam update run in the library's
+ * kernels.  Architecture:
+ *   a_0 = P x + p;  per layer l < L: A = F_K(a_l) (truncated DFT: kx < m,
+ *   ky, kz in {0..m-1, n-m..n-1}), O = W_l A (per-mode complex C x C),
+ *   s = (1/N) Re sum_K w_kx O e^{ik.r} (w = 1 at kx = 0, else 2),
+ *   z = V_l a_l + v_l + s, a_{l+1} = GELU(z) except after the last layer;
+ *   h = GELU(Q1 a_L + q1), out = Q2 h + q2.   GELU(z) = z/2 (1 + erf(z/sqrt 2)).
+ * Parameters: one FP32 vector, in order P[C][4], p[C], then per layer
+ * W_l[K][C][C] complex (re, im interleaved; K = 4 m^3), V_l[C][C], v_l[C], then
+ * Q1[H][C], q1[H], Q2[4][H], q2[4].  With bf16 != 0 the spectral weights are
+ * used in BF16 (FP32 master copy, FP32 accumulation).  Loss: mean squared
+ * error.  Device arrays are FP32 [4][nz][ny][nx].
+ * ------------------------------------------------------------------------- */
+typedef struct pf_fno pf_fno;
+int pf_fno_create(int nx, int ny, int nz, int C, int modes, int H, int L, int bf16, void* cuda_stream, pf_fno** out);
+void pf_fno_destroy(pf_fno* f);
+long long pf_fno_num_params(const pf_fno* f);
+int pf_fno_set_params(pf_fno* f, const float* theta, long long n); /* host; resets the Adam state */
+int pf_fno_get_params(pf_fno* f, float* theta, long long n);       /* host */
+int pf_fno_get_grads(pf_fno* f, float* g, long long n);            /* host; gradient of the last backward */
+/* per-channel input mean/std and output std used by pf_surrogate_step */
+int pf_fno_set_norm(pf_fno* f, const float* in_mean, const float* in_std, const float* out_std);
+int pf_fno_forward(pf_fno* f, const float* x_dev, float* out_dev); /* out_dev may be NULL */
+/* gradient of the MSE against target_dev for the last forward; loss to *loss_out */
+int pf_fno_backward(pf_fno* f, const float* target_dev, double* loss_out);
+int pf_fno_adam(pf_fno* f, float lr, float b1, float b2, float eps);
+int pf_fno_train_step(pf_fno* f, const float* x_dev, const float* target_dev, float lr, double* loss_out);
+const char* pf_fno_last_error(const pf_fno* f);
+/* One surrogate proposal with the integrator as judge: the network proposes
+ * y(t + tau) from y(t); the composition mean is reset to y(t)'s exactly; one
+ * ARK step of size h is taken from the proposal, and the proposal is accepted
+ * (state and clock advance to t + tau + h) if that step's ||LTE||_WRMS <= 1,
+ * else y(t) and the clock are restored.  *accepted and *lte report the
+ * decision.  Same grid for the network and the simulation. */
+int pf_surrogate_step(pf_ctx* ctx, pf_fno* f, double tau, double h, double rtol, double atol, int* accepted,
+                      double* lte);
+
 /* Allocation-free inverse transform (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory -- e.g. applications
  * that reserve their whole device budget at start-up or whose host framework

@@ -81,6 +81,20 @@ SIGNATURES = {
     "pf_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "pf_kernel_name": (C.c_char_p, [C.c_int]),
     "pf_state_to_real_noalloc": (C.c_int, [C.POINTER(PFGrid), _P, _P, _P]),
+    "pf_fno_create": (C.c_int, [C.c_int] * 8 + [_P, C.POINTER(_P)]),
+    "pf_fno_destroy": (None, [_P]),
+    "pf_fno_num_params": (C.c_longlong, [_P]),
+    "pf_fno_set_params": (C.c_int, [_P, _P, C.c_longlong]),
+    "pf_fno_get_params": (C.c_int, [_P, _P, C.c_longlong]),
+    "pf_fno_get_grads": (C.c_int, [_P, _P, C.c_longlong]),
+    "pf_fno_set_norm": (C.c_int, [_P, _P, _P, _P]),
+    "pf_fno_forward": (C.c_int, [_P, _P, _P]),
+    "pf_fno_backward": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+    "pf_fno_adam": (C.c_int, [_P, C.c_float, C.c_float, C.c_float, C.c_float]),
+    "pf_fno_train_step": (C.c_int, [_P, _P, _P, C.c_float, C.POINTER(C.c_double)]),
+    "pf_fno_last_error": (C.c_char_p, [_P]),
+    "pf_surrogate_step": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double)]),
 }
 NKERNELS = 10
 _DPTR_ARGS = {"pf_method_tableau"}
@@ -318,3 +332,87 @@ def batch_advance(sims, t_final, rtol=1e-4, atol=1e-8):
     rc = lib().pf_batch_advance(arr, n, float(t_final), float(rtol), float(atol), st)
     _check(rc, sims[0].ctx if rc != PF_OK else None)
     return [s.as_dict() for s in st]
+
+
+class FNO:
+    """Fourier-neural-operator surrogate on the current CUDA device (forward,
+    backward and Adam in the library's kernels).  Arrays are CUDA float32
+    tensors [4][nz][ny][nx]."""
+
+    def __init__(self, shape, C=32, modes=12, H=128, L=4, bf16=True, stream=None):
+        torch = _torch()
+        self.shape = tuple(int(s) for s in shape)
+        nz, ny, nx = self.shape
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ptr = _ctypes_void_p()
+        rc = lib().pf_fno_create(nx, ny, nz, C_int(C), C_int(modes), C_int(H), C_int(L), 1 if bf16 else 0,
+                                 _ctypes_void_p(self.stream.cuda_stream), _byref(ptr))
+        if rc != PF_OK:
+            raise PFError(rc, lib().pf_fno_last_error(None).decode())
+        self.f = ptr
+        self.n = int(lib().pf_fno_num_params(self.f))
+
+    def _chk(self, rc):
+        if rc != PF_OK:
+            raise PFError(rc, lib().pf_fno_last_error(self.f).decode())
+
+    def close(self):
+        if getattr(self, "f", None):
+            lib().pf_fno_destroy(self.f)
+            self.f = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        assert a.size == self.n
+        self._chk(lib().pf_fno_set_params(self.f, a.ctypes.data_as(_ctypes_void_p), self.n))
+
+    def params(self):
+        a = np.empty(self.n, dtype=np.float32)
+        self._chk(lib().pf_fno_get_params(self.f, a.ctypes.data_as(_ctypes_void_p), self.n))
+        return a
+
+    def grads(self):
+        a = np.empty(self.n, dtype=np.float32)
+        self._chk(lib().pf_fno_get_grads(self.f, a.ctypes.data_as(_ctypes_void_p), self.n))
+        return a
+
+    def set_norm(self, in_mean, in_std, out_std):
+        arrs = [np.ascontiguousarray(v, dtype=np.float32) for v in (in_mean, in_std, out_std)]
+        self._chk(lib().pf_fno_set_norm(self.f, *[a.ctypes.data_as(_ctypes_void_p) for a in arrs]))
+        self._norm = arrs
+
+    def forward(self, x):
+        torch = _torch()
+        out = torch.empty_like(x)
+        self._chk(lib().pf_fno_forward(self.f, _ctypes_void_p(x.data_ptr()), _ctypes_void_p(out.data_ptr())))
+        return out
+
+    def backward(self, target):
+        l = C_double()
+        self._chk(lib().pf_fno_backward(self.f, _ctypes_void_p(target.data_ptr()), _byref(l)))
+        return l.value
+
+    def train_step(self, x, target, lr):
+        l = C_double()
+        self._chk(lib().pf_fno_train_step(self.f, _ctypes_void_p(x.data_ptr()), _ctypes_void_p(target.data_ptr()),
+                                          float(lr), _byref(l)))
+        return l.value
+
+    def surrogate_step(self, sim, tau, h, rtol=1e-4, atol=1e-8):
+        acc = C_int()
+        lte = C_double()
+        self._chk(lib().pf_surrogate_step(sim.ctx, self.f, float(tau), float(h), float(rtol), float(atol),
+                                          _byref(acc), _byref(lte)))
+        return bool(acc.value), lte.value
+
+
+_ctypes_void_p = C.c_void_p
+_byref = C.byref
+C_int = C.c_int
+C_double = C.c_double

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpf.so")
-SOURCES = ["pf_kernels.cu", "pf_api.cu", "pf_noalloc.cu"]
+SOURCES = ["pf_kernels.cu", "pf_api.cu", "pf_noalloc.cu", "pf_fno.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

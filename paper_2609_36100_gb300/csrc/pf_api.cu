@@ -343,7 +343,7 @@ struct ProfScope {
 };
 
 template <typename T>
-int enqueue_step(pf_ctx* c, double dt, bool want_lte) {
+int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef = nullptr) {
     using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
     const Geo& g = c->g;
     const Phys& ph = c->ph;
@@ -366,6 +366,7 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte) {
         st.gamma = dt * tb.AI[i][i];
         for (int j = 0; j < i; ++j) split_ds(st.cE[j], st.cEh[j], st.cEl[j]);
         set_masks(st);
+        st.dc = dcoef ? dcoef + i : nullptr;
         if (c->gdiag != 0.0) {
             if (i == 0) {
                 st.qout = c->qtab;
@@ -443,6 +444,8 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte) {
         split_ds(dtm.cE[j], dtm.cEh[j], dtm.cEl[j]);
         set_masks(bt);
         set_masks(dtm);
+        bt.dc = dcoef ? dcoef + tb.s : nullptr;
+        dtm.dc = dcoef ? dcoef + tb.s + 1 : nullptr;
         const bool zI = bt.cI[j] != 0.0 || (lte && dtm.cI[j] != 0.0);
         const bool fEn = bt.cE[j] != 0.0 || (lte && dtm.cE[j] != 0.0);
         fterms += (zI && !(c->alias_y[j]) ? 16.0 : 0.0) + (fEn ? (c->fp32 ? 8.0 : 16.0) : 0.0);
@@ -535,6 +538,22 @@ int rhs_explicit_t(pf_ctx* c, const double2* yh, double2* out) {
 }  // namespace
 
 char* pf::create_error_buffer() { return g_create_err; }
+
+// grid of a context (used by the surrogate)
+int pf_ctx_grid(pf_ctx* c, pf_grid* g) {
+    if (!c || !g) return PF_EINVAL;
+    *g = c->grid;
+    return PF_OK;
+}
+
+// overwrite the composition-mean entry X^(k = 0) of the state with src's
+int pf_copy_dc(pf_ctx* c, const void* src) {
+    if (!c || !src) return PF_EINVAL;
+    cudaSetDevice(c->dev);
+    PF_CUDA(c, cudaMemcpyAsync(c->y, src, sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PF_OK;
+}
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -885,16 +904,171 @@ int pf_advance_attempts(pf_ctx* c, double t_final, double rtol, double atol, int
 
 int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, double atol, pf_stats* out) {
     if (!ctxs || n <= 0) return fail(nullptr, PF_EINVAL, "pf_batch_advance: empty batch");
+    if (!(rtol >= 0) || !(atol > 0)) return fail(nullptr, PF_EINVAL, "pf_batch_advance: need rtol >= 0, atol > 0");
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return fail(nullptr, PF_EINVAL, "pf_batch_advance: NULL context %d", i);
         if (ctxs[i]->prm.method != ctxs[0]->prm.method || ctxs[i]->fp32 != ctxs[0]->fp32)
             return fail(ctxs[i], PF_EINVAL, "pf_batch_advance: members differ in method or precision");
+        if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->dev != ctxs[0]->dev)
+            return fail(ctxs[i], PF_EINVAL, "pf_batch_advance: members must share the device and stream");
     }
-    for (int i = 0; i < n; ++i) {
-        int rc = pf_advance(ctxs[i], t_final, rtol, atol, out ? &out[i] : nullptr);
-        if (rc) return rc;
+    pf_ctx* c0 = ctxs[0];
+    cudaSetDevice(c0->dev);
+    cudaStream_t s = c0->stream;
+    const Tableau& tb = c0->tab;
+    auto t0 = std::chrono::steady_clock::now();
+    // shared constants of the round kernels
+    BatchConst bc{};
+    bc.s = tb.s;
+    bc.embedded = tb.embedded ? 1 : 0;
+    bc.nrhs = 0;
+    for (int i = 0; i < tb.s; ++i) bc.nrhs += c0->need_fe[i] ? 1 : 0;
+    std::memcpy(bc.AE, tb.AE, sizeof bc.AE);
+    std::memcpy(bc.AI, tb.AI, sizeof bc.AI);
+    std::memcpy(bc.bE, tb.bE, sizeof bc.bE);
+    std::memcpy(bc.bI, tb.bI, sizeof bc.bI);
+    std::memcpy(bc.btE, tb.btE, sizeof bc.btE);
+    std::memcpy(bc.btI, tb.btI, sizeof bc.btI);
+    bc.gdiag = c0->gdiag;
+    bc.t_final = t_final;
+    const pf_params& p0 = c0->prm;
+    bc.h_min = p0.h_min;
+    bc.h_max = p0.h_max;
+    bc.h0 = p0.h0;
+    bc.safety = p0.safety;
+    bc.k1 = p0.k1;
+    bc.k2 = p0.k2;
+    bc.eta_max = p0.eta_max;
+    bc.eta_min = p0.eta_min;
+    bc.eta_rej = p0.eta_reject_min;
+    bc.max_rejects = p0.max_rejects;
+    bc.q = tb.emb_order + 1;
+    // per-call device state: one MemberCtl and (s + 2) coefficient sets per member
+    MemberCtl* d_ctl = nullptr;
+    StageCoefDev* d_coef = nullptr;
+    MemberCtl* h_ctl = nullptr;
+    const int ncoef = tb.s + 2;
+    int rc = dalloc(c0, &d_ctl, sizeof(MemberCtl) * n);
+    rc = rc ? rc : dalloc(c0, &d_coef, sizeof(StageCoefDev) * n * ncoef);
+    if (!rc && cudaMallocHost((void**)&h_ctl, sizeof(MemberCtl) * n) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(c0, PF_ENOMEM, "cudaMallocHost failed");
     }
-    return PF_OK;
+    std::vector<cudaGraph_t> graphs(n, nullptr);
+    cudaGraph_t batch = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    for (int m = 0; m < n && !rc; ++m) {
+        pf_ctx* c = ctxs[m];
+        MemberCtl& h = h_ctl[m];
+        std::memset(&h, 0, sizeof h);
+        h.t = c->t;
+        h.h = tb.embedded ? c->h : c->prm.h0;
+        h.e_prev = c->e_prev;
+        h.after_reject = c->after_reject ? 1 : 0;
+        h.active = c->t < t_final * (1 - 1e-14) ? 1 : 0;
+        c->prm.rtol = rtol;
+        c->prm.atol = atol;
+    }
+    // a private stream forked from the members' stream: graphs are captured
+    // and replayed there (the legacy default stream cannot be captured)
+    cudaStream_t cap = nullptr;
+    cudaEvent_t fork = nullptr;
+    if (!rc) {
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, fork, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_ctl, h_ctl, sizeof(MemberCtl) * n, cudaMemcpyHostToDevice, cap);
+        if (e != cudaSuccess) rc = fail(c0, PF_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
+    }
+    const cudaStream_t s_user = s;
+    if (cap) s = cap;
+    // capture one round of each member: prep, stages, completion, norm,
+    // controller, accepted-state copy
+    for (int m = 0; m < n && !rc; ++m) {
+        pf_ctx* c = ctxs[m];
+        const bool prof = c->prof_on;
+        c->prof_on = false;
+        c->g.active = &d_ctl[m].active;
+        c->stream = cap;
+        StageCoefDev* coef = d_coef + (size_t)m * ncoef;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            launch_batch_prep(bc, d_ctl + m, coef, s);
+            int r2 = c->fp32 ? enqueue_step<float>(c, 1.0, tb.embedded, coef)
+                             : enqueue_step<double>(c, 1.0, tb.embedded, coef);
+            launch_batch_ctl(bc, d_ctl + m, c->d_scalar, 1.0, s);
+            launch_batch_accept(c->g, d_ctl + m, c->ynew, c->y, s);
+            e = cudaStreamEndCapture(s, &graphs[m]);
+            if (r2) rc = r2;
+        }
+        c->g.active = nullptr;
+        c->stream = s_user;
+        c->prof_on = prof;
+        if (!rc && e != cudaSuccess) rc = fail(c0, PF_ECUDA, "batch capture: %s", cudaGetErrorString(e));
+    }
+    if (!rc) {
+        cudaError_t e = cudaGraphCreate(&batch, 0);
+        for (int m = 0; m < n && e == cudaSuccess; ++m) {
+            cudaGraphNode_t node;
+            e = cudaGraphAddChildGraphNode(&node, batch, nullptr, 0, graphs[m]);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, batch, 0);
+        if (e != cudaSuccess) rc = fail(c0, PF_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+    }
+    // one graph launch advances every member by one attempt; poll for the end
+    long long rounds = 0;
+    while (!rc) {
+        cudaError_t e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+        rounds += 2;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_ctl, d_ctl, sizeof(MemberCtl) * n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = fail(c0, PF_ECUDA, "batch round: %s", cudaGetErrorString(e));
+            break;
+        }
+        int live = 0;
+        for (int m = 0; m < n; ++m) live += h_ctl[m].active;
+        if (!live) break;
+        if (rounds > 10000000) {
+            rc = fail(c0, PF_ESTEPFAIL, "pf_batch_advance: no progress");
+            break;
+        }
+    }
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int m = 0; m < n && h_ctl; ++m) {
+        pf_ctx* c = ctxs[m];
+        const MemberCtl& h = h_ctl[m];
+        if (rounds > 0) {
+            c->t = h.t;
+            if (tb.embedded) c->h = h.h;
+            c->e_prev = h.e_prev;
+            c->after_reject = h.after_reject != 0;
+            c->st.steps_accepted += h.n_acc;
+            c->st.steps_rejected += h.n_rej;
+            c->st.rhs_evals += h.n_rhs;
+            c->st.point_stages += h.n_rhs * c->g.N;
+            c->st.last_wrms = h.e_last;
+        }
+        c->st.wall_s += wall;
+        c->st.t = c->t;
+        c->st.h = c->h;
+        if (out) out[m] = c->st;
+        if (!rc && h.status) rc = fail(c, h.status, "pf_batch_advance: member %d failed at t=%g", m, h.t);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (batch) cudaGraphDestroy(batch);
+    for (cudaGraph_t g : graphs)
+        if (g) cudaGraphDestroy(g);
+    cudaStreamSynchronize(s);
+    if (cap) cudaStreamDestroy(cap);
+    if (fork) cudaEventDestroy(fork);
+    cudaFree(d_ctl);
+    cudaFree(d_coef);
+    if (h_ctl) cudaFreeHost(h_ctl);
+    return rc;
 }
 
 int pf_free_energy(pf_ctx* c, double* F_out) {

@@ -1,0 +1,776 @@
+// Fourier neural operator surrogate: forward, backward and Adam, all on the
+// GPU (FP32 activations and accumulation; the spectral weights are read in
+// BF16 unless the FP32 checking mode is selected).
+//
+//   a_0 = P x + p
+//   for each layer l: A = F_K(a_l) (truncated DFT, kx < m, |ky|,|kz| < m),
+//                     O = W_l A per mode (complex C x C),
+//                     s = (1/N) Re sum_K w_kx O e^{ik.r},
+//                     z = V_l a_l + v_l + s,  a_{l+1} = GELU(z) (not after the last layer)
+//   h = GELU(Q1 a_L + q1), out = Q2 h + q2
+//
+// Truncated transforms and their adjoints are small dense contractions along
+// one axis (kernel k_axis with precomputed complex matrices).  The per-mode
+// channel mix is a batch-1 32x32 complex matvec per retained mode: it streams
+// the weights once per pass (weight-bandwidth bound), so it runs on CUDA cores
+// from BF16 storage rather than through the tensor cores.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pf.h"
+#include "pf_internal.h"
+
+using namespace pf;
+
+int pf_ctx_grid(pf_ctx* c, pf_grid* g);
+int pf_copy_dc(pf_ctx* c, const void* src);
+
+namespace {
+
+constexpr int kT = 256;
+
+struct FnoDims {
+    int nx, ny, nz, C, m, H, L, cin;
+    long long N;
+    int K;  // (2m)(2m)m retained modes
+};
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_g(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// out[o][k][i] (=|+=) sum_j M[k][j] in[o][j][i]; complex M [nk][nj]
+template <bool IN_REAL, bool OUT_REAL, bool ACCUM>
+__global__ void k_axis(const void* __restrict__ inp, void* __restrict__ outp, const float2* __restrict__ M, int nk,
+                       int nj, long long n_outer, int n_inner) {
+    extern __shared__ float2 Ms[];
+    for (int e = threadIdx.x; e < nk * nj; e += blockDim.x) Ms[e] = M[e];
+    __syncthreads();
+    const long long total = n_outer * nk * n_inner;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % n_inner);
+        const long long ok = idx / n_inner;
+        const int k = (int)(ok % nk);
+        const long long o = ok / nk;
+        float ar = 0.f, ai = 0.f;
+        const long long ib = o * nj * (long long)n_inner + i;
+        for (int j = 0; j < nj; ++j) {
+            const float2 m = Ms[k * nj + j];
+            if (IN_REAL) {
+                const float v = reinterpret_cast<const float*>(inp)[ib + (long long)j * n_inner];
+                ar += m.x * v;
+                ai += m.y * v;
+            } else {
+                const float2 v = reinterpret_cast<const float2*>(inp)[ib + (long long)j * n_inner];
+                ar += m.x * v.x - m.y * v.y;
+                ai += m.x * v.y + m.y * v.x;
+            }
+        }
+        const long long ob = (o * nk + k) * (long long)n_inner + i;
+        if (OUT_REAL) {
+            float* out = reinterpret_cast<float*>(outp);
+            out[ob] = ACCUM ? out[ob] + ar : ar;
+        } else {
+            float2* out = reinterpret_cast<float2*>(outp);
+            out[ob] = ACCUM ? make_float2(out[ob].x + ar, out[ob].y + ai) : make_float2(ar, ai);
+        }
+    }
+}
+
+// spectral weight (re, im) of mode k, row c, column d
+__device__ __forceinline__ float2 wget(const float2* w32, const __nv_bfloat162* w16, long long e) {
+    if (w16) {
+        const __nv_bfloat162 b = w16[e];
+        return make_float2(__bfloat162float(b.x), __bfloat162float(b.y));
+    }
+    return w32[e];
+}
+
+// O[c][k] = sum_d W[k][c][d] A[d][k]
+__global__ void k_mix(const float2* __restrict__ A, float2* __restrict__ O, const float2* __restrict__ w32,
+                      const __nv_bfloat162* __restrict__ w16, int C, int K) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)C * K;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % K), c = (int)(idx / K);
+        float ar = 0.f, ai = 0.f;
+        const long long wb = ((long long)k * C + c) * C;
+        for (int d = 0; d < C; ++d) {
+            const float2 w = wget(w32, w16, wb + d);
+            const float2 a = A[(long long)d * K + k];
+            ar += w.x * a.x - w.y * a.y;
+            ai += w.x * a.y + w.y * a.x;
+        }
+        O[idx] = make_float2(ar, ai);
+    }
+}
+
+// backward of the mix: GA[d][k] = sum_c conj(W[k][c][d]) GO[c][k];
+// GW[k][c][d] = GO[c][k] conj(A[d][k])
+__global__ void k_mix_bwd(const float2* __restrict__ GO, const float2* __restrict__ A, float2* __restrict__ GA,
+                          float2* __restrict__ GW, const float2* __restrict__ w32,
+                          const __nv_bfloat162* __restrict__ w16, int C, int K) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)C * K;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % K), d = (int)(idx / K);
+        float ar = 0.f, ai = 0.f;
+        const float2 a = A[(long long)d * K + k];
+        for (int c = 0; c < C; ++c) {
+            const long long e = ((long long)k * C + c) * C + d;
+            const float2 w = wget(w32, w16, e);
+            const float2 g = GO[(long long)c * K + k];
+            ar += w.x * g.x + w.y * g.y;  // conj(w) g
+            ai += w.x * g.y - w.y * g.x;
+            GW[e] = make_float2(g.x * a.x + g.y * a.y, g.y * a.x - g.x * a.y);  // g conj(a)
+        }
+        GA[idx] = make_float2(ar, ai);
+    }
+}
+
+// y[a][p] = sum_b Mw[a][b] x[b][p] + bias[a] (+ add[a][p]); optional GELU
+// output, pre-activation kept in zout
+__global__ void k_dense(const float* __restrict__ x, float* __restrict__ y, float* __restrict__ zout,
+                        const float* __restrict__ Mw, const float* __restrict__ bias, const float* __restrict__ add,
+                        int A, int B, long long N, int act) {
+    extern __shared__ float sm[];
+    for (int e = threadIdx.x; e < A * B + A; e += blockDim.x) sm[e] = e < A * B ? Mw[e] : bias[e - A * B];
+    __syncthreads();
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        for (int a = 0; a < A; ++a) {
+            float acc = sm[A * B + a];
+            for (int b = 0; b < B; ++b) acc += sm[a * B + b] * x[(long long)b * N + p];
+            if (add) acc += add[(long long)a * N + p];
+            if (zout) zout[(long long)a * N + p] = acc;
+            y[(long long)a * N + p] = act ? gelu_f(acc) : acc;
+        }
+    }
+}
+
+// dx[b][p] (=|+=) sum_a Mw[a][b] dy[a][p]
+__global__ void k_dense_t(const float* __restrict__ dy, float* __restrict__ dx, const float* __restrict__ Mw, int A,
+                          int B, long long N, int accum) {
+    extern __shared__ float sm[];
+    for (int e = threadIdx.x; e < A * B; e += blockDim.x) sm[e] = Mw[e];
+    __syncthreads();
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        for (int b = 0; b < B; ++b) {
+            float acc = 0.f;
+            for (int a = 0; a < A; ++a) acc += sm[a * B + b] * dy[(long long)a * N + p];
+            const long long i = (long long)b * N + p;
+            dx[i] = accum ? dx[i] + acc : acc;
+        }
+    }
+}
+
+// g[i] *= GELU'(z[i])
+__global__ void k_gelu_bwd(float* __restrict__ g, const float* __restrict__ z, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        g[i] *= gelu_g(z[i]);
+}
+
+// per-block partial sums of G[a][b] = sum_p U[a][p] V[b][p] (V = ones when
+// null: column sums of U), written to part[block][a][b]
+constexpr int kCh = 32;
+__global__ void k_outer_partial(const float* __restrict__ U, const float* __restrict__ V, int A, int B, long long N,
+                                float* __restrict__ part) {
+    extern __shared__ float sm[];
+    float* su = sm;
+    float* sv = sm + A * kCh;
+    const int E = A * B;
+    float acc[16];
+    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+    const long long per = (N + gridDim.x - 1) / gridDim.x;
+    const long long p0 = blockIdx.x * per, p1 = min(N, p0 + per);
+    for (long long pc = p0; pc < p1; pc += kCh) {
+        const int np = (int)min((long long)kCh, p1 - pc);
+        __syncthreads();
+        for (int e = threadIdx.x; e < A * kCh; e += blockDim.x) {
+            const int a = e / kCh, q = e % kCh;
+            su[e] = q < np ? U[(long long)a * N + pc + q] : 0.f;
+        }
+        for (int e = threadIdx.x; e < B * kCh; e += blockDim.x) {
+            const int b = e / kCh, q = e % kCh;
+            sv[e] = q < np ? (V ? V[(long long)b * N + pc + q] : 1.f) : 0.f;
+        }
+        __syncthreads();
+        for (int q = 0; q < 16; ++q) {
+            const int e = threadIdx.x + q * blockDim.x;
+            if (e >= E) break;
+            const int a = e / B, b = e % B;
+            float s = 0.f;
+            for (int t = 0; t < kCh; ++t) s += su[a * kCh + t] * sv[b * kCh + t];
+            acc[q] += s;
+        }
+    }
+    for (int q = 0; q < 16; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < E) part[(long long)blockIdx.x * E + e] = acc[q];
+    }
+}
+
+// G[e] = sum_blocks part[blk][e] (fixed order)
+__global__ void k_sum_partials(const float* __restrict__ part, int nblk, int E, float* __restrict__ G) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nblk; ++b) s += part[(long long)b * E + e];
+        G[e] = s;
+    }
+}
+
+// dout = 2 (out - tgt) / n_el and per-block sums of (out - tgt)^2
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ tgt, float* __restrict__ dout,
+                      long long n, double* __restrict__ part) {
+    __shared__ double red[kT / 32];
+    double acc = 0.0;
+    const float sc = 2.0f / (float)n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = out[i] - tgt[i];
+        dout[i] = sc * d;
+        acc += (double)d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+__global__ void k_to_bf16(const float2* __restrict__ w, __nv_bfloat162* __restrict__ o, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        o[i] = __floats2bfloat162_rn(w[i].x, w[i].y);
+}
+
+// real-space state (FP64, [4][N]) -> normalised FP32 network input
+__global__ void k_norm_in(const double* __restrict__ y, float* __restrict__ x, long long N, float4 mean, float4 istd) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 4 * N; i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i / N);
+        const float mu = f == 0 ? mean.x : f == 1 ? mean.y : f == 2 ? mean.z : mean.w;
+        const float is = f == 0 ? istd.x : f == 1 ? istd.y : f == 2 ? istd.z : istd.w;
+        x[i] = ((float)y[i] - mu) * is;
+    }
+}
+
+// proposal: y_real += out * out_std (per channel), in FP64
+__global__ void k_apply_delta(double* __restrict__ y, const float* __restrict__ out, long long N, float4 ostd) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 4 * N; i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i / N);
+        const float s = f == 0 ? ostd.x : f == 1 ? ostd.y : f == 2 ? ostd.z : ostd.w;
+        y[i] += (double)(out[i] * s);
+    }
+}
+
+inline int grid_for(long long n) {
+    long long g = (n + kT - 1) / kT;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// object
+// ---------------------------------------------------------------------------
+struct pf_fno {
+    FnoDims d{};
+    int dev = 0;
+    cudaStream_t s = nullptr;
+    int bf16 = 1;
+    long long npar = 0;
+    // parameter offsets
+    long long oP, op, oQ1, oq1, oQ2, oq2;
+    std::vector<long long> oW, oV, ov;
+    float *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
+    __nv_bfloat162* wbf = nullptr;  // BF16 copies of all spectral weights (same layout)
+    long long nW = 0;               // complex entries per layer (K C C)
+    int adam_t = 0;
+    // DFT matrices
+    float2 *Mx = nullptr, *Mxw = nullptr, *My = nullptr, *Mz = nullptr;      // forward (Mxw: scaled w/N)
+    float2 *IXw = nullptr, *IX1 = nullptr, *IY = nullptr, *IZ = nullptr;     // inverse
+    // activations / work
+    float *x = nullptr, *act = nullptr, *zs = nullptr, *hpre = nullptr, *hh = nullptr, *out = nullptr;
+    float2 *Ak = nullptr;            // A_l per layer [L][C][K]
+    float2 *T1 = nullptr, *T2 = nullptr, *Ok = nullptr, *Gk = nullptr;
+    float *sbuf = nullptr, *da = nullptr, *dz = nullptr, *dh = nullptr, *dout = nullptr;
+    float* part = nullptr;
+    int npart_blk = 0;
+    double* dpart = nullptr;
+    double* hsum = nullptr;  // pinned
+    float4 in_mean{0, 0, 0, 0}, in_istd{1, 1, 1, 1}, out_std{1, 1, 1, 1};
+    double2* backup = nullptr;  // state copy for a rejected proposal
+    double* realbuf = nullptr;  // real-space FP64 state [4][N]
+    long long backup_nk = 0;
+    char err[256] = "no error";
+};
+
+namespace {
+
+thread_local char g_fno_err[256] = "no error";
+
+int ffail(pf_fno* f, int code, const char* msg, cudaError_t e = cudaSuccess) {
+    char* dst = f ? f->err : g_fno_err;
+    if (e != cudaSuccess)
+        std::snprintf(dst, 256, "%s: %s", msg, cudaGetErrorString(e));
+    else
+        std::snprintf(dst, 256, "%s", msg);
+    return code;
+}
+
+template <typename P>
+cudaError_t falloc(P** p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+}
+
+void fno_free(pf_fno* f) {
+    void* ps[] = {f->theta, f->grad, f->am, f->av, f->wbf, f->Mx, f->Mxw, f->My, f->Mz, f->IXw, f->IX1, f->IY,
+                  f->IZ, f->x, f->act, f->zs, f->hpre, f->hh, f->out, f->Ak, f->T1, f->T2, f->Ok, f->Gk,
+                  f->sbuf, f->da, f->dz, f->dh, f->dout, f->part, f->dpart, f->backup, f->realbuf};
+    for (void* p : ps) cudaFree(p);
+    if (f->hsum) cudaFreeHost(f->hsum);
+}
+
+void axis_launch(cudaStream_t s, bool in_real, bool out_real, bool accum, const void* in, void* out,
+                 const float2* M, int nk, int nj, long long n_outer, int n_inner) {
+    const size_t sm = (size_t)nk * nj * sizeof(float2);
+    const int g = grid_for(n_outer * nk * n_inner);
+    if (in_real && !out_real)
+        k_axis<true, false, false><<<g, kT, sm, s>>>(in, out, M, nk, nj, n_outer, n_inner);
+    else if (!in_real && !out_real)
+        k_axis<false, false, false><<<g, kT, sm, s>>>(in, out, M, nk, nj, n_outer, n_inner);
+    else if (!accum)
+        k_axis<false, true, false><<<g, kT, sm, s>>>(in, out, M, nk, nj, n_outer, n_inner);
+    else
+        k_axis<false, true, true><<<g, kT, sm, s>>>(in, out, M, nk, nj, n_outer, n_inner);
+}
+
+// A = F_K(a): a [C][nz][ny][nx] real -> A [C][2m][2m][m]
+void trunc_dft(pf_fno* f, const float* a, float2* A, const float2* Mx) {
+    const FnoDims& d = f->d;
+    axis_launch(f->s, true, false, false, a, f->T1, Mx, d.m, d.nx, (long long)d.C * d.nz * d.ny, 1);
+    axis_launch(f->s, false, false, false, f->T1, f->T2, f->My, 2 * d.m, d.ny, (long long)d.C * d.nz, d.m);
+    axis_launch(f->s, false, false, false, f->T2, A, f->Mz, 2 * d.m, d.nz, (long long)d.C, 2 * d.m * d.m);
+}
+
+// r (=|+=) Re F^-1 (O) with the x matrix IX (weights and 1/N folded in)
+void trunc_inv(pf_fno* f, const float2* O, float* r, const float2* IX, bool accum) {
+    const FnoDims& d = f->d;
+    axis_launch(f->s, false, false, false, O, f->T2, f->IZ, d.nz, 2 * d.m, (long long)d.C, 2 * d.m * d.m);
+    axis_launch(f->s, false, false, false, f->T2, f->T1, f->IY, d.ny, 2 * d.m, (long long)d.C * d.nz, d.m);
+    axis_launch(f->s, false, true, accum, f->T1, r, IX, d.nx, d.m, (long long)d.C * d.nz * d.ny, 1);
+}
+
+// G[A][B] = sum_p U[a][p] V[b][p] into dst (V null: sums of U rows)
+void outer_reduce(pf_fno* f, const float* U, const float* V, int A, int B, float* dst) {
+    const int nb = f->npart_blk;
+    const size_t sm = (size_t)(A + B) * kCh * sizeof(float);
+    k_outer_partial<<<nb, kT, sm, f->s>>>(U, V, A, B, f->d.N, f->part);
+    k_sum_partials<<<grid_for(A * B), kT, 0, f->s>>>(f->part, nb, A * B, dst);
+}
+
+void dense(pf_fno* f, const float* x, float* y, float* zout, const float* Mw, const float* b, const float* add, int A,
+           int B, int act) {
+    const size_t sm = (size_t)(A * B + A) * sizeof(float);
+    k_dense<<<grid_for(f->d.N), kT, sm, f->s>>>(x, y, zout, Mw, b, add, A, B, f->d.N, act);
+}
+
+void dense_t(pf_fno* f, const float* dy, float* dx, const float* Mw, int A, int B, int accum) {
+    const size_t sm = (size_t)(A * B) * sizeof(float);
+    k_dense_t<<<grid_for(f->d.N), kT, sm, f->s>>>(dy, dx, Mw, A, B, f->d.N, accum);
+}
+
+int fno_forward(pf_fno* f, const float* x) {
+    const FnoDims& d = f->d;
+    const long long N = d.N;
+    cudaStream_t s = f->s;
+    if (x != f->x) cudaMemcpyAsync(f->x, x, sizeof(float) * 4 * N, cudaMemcpyDeviceToDevice, s);
+    float* a0 = f->act;
+    dense(f, f->x, a0, nullptr, f->theta + f->oP, f->theta + f->op, nullptr, d.C, d.cin, 0);
+    for (int l = 0; l < d.L; ++l) {
+        float* a = f->act + (size_t)l * d.C * N;
+        float* an = f->act + (size_t)(l + 1) * d.C * N;
+        float2* A = f->Ak + (size_t)l * d.C * d.K;
+        trunc_dft(f, a, A, f->Mx);
+        const float2* w32 = reinterpret_cast<const float2*>(f->theta + f->oW[l]);
+        const __nv_bfloat162* w16 = f->bf16 ? f->wbf + (size_t)l * f->nW : nullptr;
+        k_mix<<<grid_for((long long)d.C * d.K), kT, 0, s>>>(A, f->Ok, w32, w16, d.C, d.K);
+        trunc_inv(f, f->Ok, f->sbuf, f->IXw, false);
+        dense(f, a, an, f->zs + (size_t)l * d.C * N, f->theta + f->oV[l], f->theta + f->ov[l], f->sbuf, d.C, d.C,
+              l < d.L - 1 ? 1 : 0);
+    }
+    float* aL = f->act + (size_t)d.L * d.C * N;
+    dense(f, aL, f->hh, f->hpre, f->theta + f->oQ1, f->theta + f->oq1, nullptr, d.H, d.C, 1);
+    dense(f, f->hh, f->out, nullptr, f->theta + f->oQ2, f->theta + f->oq2, nullptr, d.cin, d.H, 0);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PF_OK : ffail(f, PF_ECUDA, "fno forward", e);
+}
+
+int fno_backward(pf_fno* f, const float* tgt, double* loss) {
+    const FnoDims& d = f->d;
+    const long long N = d.N;
+    cudaStream_t s = f->s;
+    const int nb = 152 * 4;
+    k_mse<<<nb, kT, 0, s>>>(f->out, tgt, f->dout, 4 * N, f->dpart);
+    float* G = f->grad;
+    outer_reduce(f, f->dout, f->hh, d.cin, d.H, G + f->oQ2);
+    outer_reduce(f, f->dout, nullptr, d.cin, 1, G + f->oq2);
+    dense_t(f, f->dout, f->dh, f->theta + f->oQ2, d.cin, d.H, 0);
+    k_gelu_bwd<<<grid_for((long long)d.H * N), kT, 0, s>>>(f->dh, f->hpre, (long long)d.H * N);
+    float* aL = f->act + (size_t)d.L * d.C * N;
+    outer_reduce(f, f->dh, aL, d.H, d.C, G + f->oQ1);
+    outer_reduce(f, f->dh, nullptr, d.H, 1, G + f->oq1);
+    dense_t(f, f->dh, f->da, f->theta + f->oQ1, d.H, d.C, 0);
+    for (int l = d.L - 1; l >= 0; --l) {
+        float* a = f->act + (size_t)l * d.C * N;
+        float* z = f->zs + (size_t)l * d.C * N;
+        cudaMemcpyAsync(f->dz, f->da, sizeof(float) * d.C * N, cudaMemcpyDeviceToDevice, s);
+        if (l < d.L - 1) k_gelu_bwd<<<grid_for((long long)d.C * N), kT, 0, s>>>(f->dz, z, (long long)d.C * N);
+        outer_reduce(f, f->dz, a, d.C, d.C, G + f->oV[l]);
+        outer_reduce(f, f->dz, nullptr, d.C, 1, G + f->ov[l]);
+        dense_t(f, f->dz, f->da, f->theta + f->oV[l], d.C, d.C, 0);
+        // spectral: GO = (w/N) F(dz); GW, GA; da += Re F^-1 (GA) (unweighted)
+        trunc_dft(f, f->dz, f->Gk, f->Mxw);
+        const float2* w32 = reinterpret_cast<const float2*>(f->theta + f->oW[l]);
+        const __nv_bfloat162* w16 = f->bf16 ? f->wbf + (size_t)l * f->nW : nullptr;
+        float2* A = f->Ak + (size_t)l * d.C * d.K;
+        k_mix_bwd<<<grid_for((long long)d.C * d.K), kT, 0, s>>>(f->Gk, A, f->Ok, reinterpret_cast<float2*>(G + f->oW[l]),
+                                                                w32, w16, d.C, d.K);
+        trunc_inv(f, f->Ok, f->da, f->IX1, true);
+    }
+    outer_reduce(f, f->da, f->x, d.C, d.cin, G + f->oP);
+    outer_reduce(f, f->da, nullptr, d.C, 1, G + f->op);
+    if (loss) {
+        double* tot = f->dpart + nb;
+        launch_reduce(f->dpart, nb, 1.0 / (4.0 * (double)N), tot, s);
+        cudaMemcpyAsync(f->hsum, tot, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return ffail(f, PF_ECUDA, "fno backward", e);
+        *loss = f->hsum[0];
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PF_OK : ffail(f, PF_ECUDA, "fno backward", e);
+}
+
+void refresh_bf16(pf_fno* f) {
+    for (int l = 0; l < f->d.L; ++l)
+        k_to_bf16<<<grid_for(f->nW), kT, 0, f->s>>>(reinterpret_cast<const float2*>(f->theta + f->oW[l]),
+                                                   f->wbf + (size_t)l * f->nW, f->nW);
+}
+
+void build_matrices(pf_fno* f, std::vector<float2>& Mx, std::vector<float2>& Mxw, std::vector<float2>& My,
+                    std::vector<float2>& Mz, std::vector<float2>& IXw, std::vector<float2>& IX1,
+                    std::vector<float2>& IY, std::vector<float2>& IZ) {
+    const FnoDims& d = f->d;
+    const double tp = 6.283185307179586476925286766559;
+    auto kidx = [&](int n, int j) { return j < d.m ? j : n - 2 * d.m + j; };
+    Mx.resize((size_t)d.m * d.nx);
+    Mxw.resize(Mx.size());
+    IXw.resize((size_t)d.nx * d.m);
+    IX1.resize(IXw.size());
+    for (int k = 0; k < d.m; ++k)
+        for (int x = 0; x < d.nx; ++x) {
+            const double th = tp * (double)((long long)k * x % d.nx) / d.nx;
+            const double c = std::cos(th), sn = std::sin(th), w = (k == 0 ? 1.0 : 2.0);
+            Mx[(size_t)k * d.nx + x] = make_float2((float)c, (float)-sn);
+            Mxw[(size_t)k * d.nx + x] = make_float2((float)(c * w / d.N), (float)(-sn * w / d.N));
+            IXw[(size_t)x * d.m + k] = make_float2((float)(c * w / d.N), (float)(sn * w / d.N));
+            IX1[(size_t)x * d.m + k] = make_float2((float)c, (float)sn);
+        }
+    auto axis = [&](int n, std::vector<float2>& F, std::vector<float2>& I) {
+        F.resize((size_t)2 * d.m * n);
+        I.resize(F.size());
+        for (int j = 0; j < 2 * d.m; ++j) {
+            const int k = kidx(n, j);
+            for (int x = 0; x < n; ++x) {
+                const double th = tp * (double)((long long)k * x % n) / n;
+                F[(size_t)j * n + x] = make_float2((float)std::cos(th), (float)-std::sin(th));
+                I[(size_t)x * 2 * d.m + j] = make_float2((float)std::cos(th), (float)std::sin(th));
+            }
+        }
+    };
+    axis(d.ny, My, IY);
+    axis(d.nz, Mz, IZ);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int pf_fno_create(int nx, int ny, int nz, int C, int modes, int H, int L, int bf16, void* cuda_stream, pf_fno** out) {
+    if (!out) return ffail(nullptr, PF_EINVAL, "pf_fno_create: NULL out");
+    *out = nullptr;
+    if (nx < 4 || ny < 4 || nz < 4 || C < 1 || C > 64 || H < 1 || H > 256 || L < 1 || L > 8 || modes < 1 ||
+        2 * modes > ny || 2 * modes > nz || modes > nx / 2 || C * H > 4096 || C * C > 4096)
+        return ffail(nullptr, PF_EINVAL, "pf_fno_create: unsupported dimensions");
+    pf_fno* f = new (std::nothrow) pf_fno();
+    if (!f) return ffail(nullptr, PF_ENOMEM, "host allocation failed");
+    cudaGetDevice(&f->dev);
+    f->s = (cudaStream_t)cuda_stream;
+    f->bf16 = bf16 ? 1 : 0;
+    FnoDims& d = f->d;
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = nz;
+    d.C = C;
+    d.m = modes;
+    d.H = H;
+    d.L = L;
+    d.cin = 4;
+    d.N = (long long)nx * ny * nz;
+    d.K = 4 * modes * modes * modes;
+    f->nW = (long long)d.K * C * C;
+    long long o = 0;
+    f->oP = o;
+    o += (long long)C * d.cin;
+    f->op = o;
+    o += C;
+    for (int l = 0; l < L; ++l) {
+        f->oW.push_back(o);
+        o += 2 * f->nW;
+        f->oV.push_back(o);
+        o += (long long)C * C;
+        f->ov.push_back(o);
+        o += C;
+    }
+    f->oQ1 = o;
+    o += (long long)H * C;
+    f->oq1 = o;
+    o += H;
+    f->oQ2 = o;
+    o += (long long)d.cin * H;
+    f->oq2 = o;
+    o += d.cin;
+    f->npar = o;
+    const long long N = d.N;
+    f->npart_blk = 152 * 4;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = falloc(p, bytes);
+    };
+    A(&f->theta, sizeof(float) * f->npar);
+    A(&f->grad, sizeof(float) * f->npar);
+    A(&f->am, sizeof(float) * f->npar);
+    A(&f->av, sizeof(float) * f->npar);
+    A(&f->wbf, sizeof(__nv_bfloat162) * f->nW * L);
+    A(&f->x, sizeof(float) * 4 * N);
+    A(&f->act, sizeof(float) * (size_t)(L + 1) * C * N);
+    A(&f->zs, sizeof(float) * (size_t)L * C * N);
+    A(&f->hpre, sizeof(float) * (size_t)H * N);
+    A(&f->hh, sizeof(float) * (size_t)H * N);
+    A(&f->out, sizeof(float) * 4 * N);
+    A(&f->Ak, sizeof(float2) * (size_t)L * C * d.K);
+    A(&f->T1, sizeof(float2) * (size_t)C * nz * ny * modes);
+    A(&f->T2, sizeof(float2) * (size_t)C * nz * 2 * modes * modes);
+    A(&f->Ok, sizeof(float2) * (size_t)C * d.K);
+    A(&f->Gk, sizeof(float2) * (size_t)C * d.K);
+    A(&f->sbuf, sizeof(float) * (size_t)C * N);
+    A(&f->da, sizeof(float) * (size_t)C * N);
+    A(&f->dz, sizeof(float) * (size_t)C * N);
+    A(&f->dh, sizeof(float) * (size_t)H * N);
+    A(&f->dout, sizeof(float) * 4 * N);
+    A(&f->part, sizeof(float) * (size_t)f->npart_blk * (size_t)(H * C > C * C ? H * C : C * C));
+    A(&f->dpart, sizeof(double) * (152 * 4 + 2));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&f->hsum, sizeof(double) * 2);
+    std::vector<float2> Mx, Mxw, My, Mz, IXw, IX1, IY, IZ;
+    build_matrices(f, Mx, Mxw, My, Mz, IXw, IX1, IY, IZ);
+    A(&f->Mx, Mx.size() * sizeof(float2));
+    A(&f->Mxw, Mxw.size() * sizeof(float2));
+    A(&f->My, My.size() * sizeof(float2));
+    A(&f->Mz, Mz.size() * sizeof(float2));
+    A(&f->IXw, IXw.size() * sizeof(float2));
+    A(&f->IX1, IX1.size() * sizeof(float2));
+    A(&f->IY, IY.size() * sizeof(float2));
+    A(&f->IZ, IZ.size() * sizeof(float2));
+    if (e == cudaSuccess) {
+        struct {
+            float2* d;
+            std::vector<float2>* h;
+        } cp[] = {{f->Mx, &Mx}, {f->Mxw, &Mxw}, {f->My, &My}, {f->Mz, &Mz},
+                  {f->IXw, &IXw}, {f->IX1, &IX1}, {f->IY, &IY}, {f->IZ, &IZ}};
+        for (auto& c : cp)
+            if (e == cudaSuccess) e = cudaMemcpy(c.d, c.h->data(), c.h->size() * sizeof(float2), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(f->am, 0, sizeof(float) * f->npar);
+    if (e == cudaSuccess) e = cudaMemset(f->av, 0, sizeof(float) * f->npar);
+    if (e == cudaSuccess) e = cudaMemset(f->theta, 0, sizeof(float) * f->npar);
+    if (e != cudaSuccess) {
+        ffail(nullptr, e == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA, "pf_fno_create", e);
+        fno_free(f);
+        delete f;
+        return e == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA;
+    }
+    *out = f;
+    return PF_OK;
+}
+
+void pf_fno_destroy(pf_fno* f) {
+    if (!f) return;
+    cudaSetDevice(f->dev);
+    cudaStreamSynchronize(f->s);
+    fno_free(f);
+    delete f;
+}
+
+long long pf_fno_num_params(const pf_fno* f) { return f ? f->npar : -1; }
+
+int pf_fno_set_params(pf_fno* f, const float* theta, long long n) {
+    if (!f || !theta || n != f->npar) return ffail(f, PF_EINVAL, "pf_fno_set_params: bad argument");
+    cudaSetDevice(f->dev);
+    cudaError_t e = cudaMemcpyAsync(f->theta, theta, sizeof(float) * n, cudaMemcpyHostToDevice, f->s);
+    if (e == cudaSuccess) {
+        refresh_bf16(f);
+        e = cudaStreamSynchronize(f->s);
+    }
+    f->adam_t = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->am, 0, sizeof(float) * n, f->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->av, 0, sizeof(float) * n, f->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->s);
+    return e == cudaSuccess ? PF_OK : ffail(f, PF_ECUDA, "pf_fno_set_params", e);
+}
+
+int pf_fno_get_params(pf_fno* f, float* theta, long long n) {
+    if (!f || !theta || n != f->npar) return ffail(f, PF_EINVAL, "pf_fno_get_params: bad argument");
+    cudaSetDevice(f->dev);
+    cudaError_t e = cudaMemcpyAsync(theta, f->theta, sizeof(float) * n, cudaMemcpyDeviceToHost, f->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->s);
+    return e == cudaSuccess ? PF_OK : ffail(f, PF_ECUDA, "pf_fno_get_params", e);
+}
+
+int pf_fno_get_grads(pf_fno* f, float* g, long long n) {
+    if (!f || !g || n != f->npar) return ffail(f, PF_EINVAL, "pf_fno_get_grads: bad argument");
+    cudaSetDevice(f->dev);
+    cudaError_t e = cudaMemcpyAsync(g, f->grad, sizeof(float) * n, cudaMemcpyDeviceToHost, f->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->s);
+    return e == cudaSuccess ? PF_OK : ffail(f, PF_ECUDA, "pf_fno_get_grads", e);
+}
+
+int pf_fno_set_norm(pf_fno* f, const float* in_mean, const float* in_std, const float* out_std) {
+    if (!f || !in_mean || !in_std || !out_std) return ffail(f, PF_EINVAL, "pf_fno_set_norm: NULL argument");
+    f->in_mean = make_float4(in_mean[0], in_mean[1], in_mean[2], in_mean[3]);
+    f->in_istd = make_float4(1.f / in_std[0], 1.f / in_std[1], 1.f / in_std[2], 1.f / in_std[3]);
+    f->out_std = make_float4(out_std[0], out_std[1], out_std[2], out_std[3]);
+    return PF_OK;
+}
+
+int pf_fno_forward(pf_fno* f, const float* x_dev, float* out_dev) {
+    if (!f || !x_dev) return ffail(f, PF_EINVAL, "pf_fno_forward: NULL argument");
+    cudaSetDevice(f->dev);
+    int rc = fno_forward(f, x_dev);
+    if (rc) return rc;
+    if (out_dev)
+        cudaMemcpyAsync(out_dev, f->out, sizeof(float) * 4 * f->d.N, cudaMemcpyDeviceToDevice, f->s);
+    cudaError_t e = cudaStreamSynchronize(f->s);
+    return e == cudaSuccess ? PF_OK : ffail(f, PF_ECUDA, "pf_fno_forward", e);
+}
+
+int pf_fno_backward(pf_fno* f, const float* target_dev, double* loss_out) {
+    if (!f || !target_dev) return ffail(f, PF_EINVAL, "pf_fno_backward: NULL argument");
+    cudaSetDevice(f->dev);
+    double l = 0.0;
+    int rc = fno_backward(f, target_dev, &l);
+    if (loss_out) *loss_out = l;
+    return rc;
+}
+
+int pf_fno_adam(pf_fno* f, float lr, float b1, float b2, float eps) {
+    if (!f) return ffail(f, PF_EINVAL, "pf_fno_adam: NULL argument");
+    cudaSetDevice(f->dev);
+    f->adam_t += 1;
+    const float c1 = 1.f - powf(b1, (float)f->adam_t), c2 = 1.f - powf(b2, (float)f->adam_t);
+    k_adam<<<grid_for(f->npar), kT, 0, f->s>>>(f->theta, f->grad, f->am, f->av, f->npar, lr, b1, b2, eps, c1, c2);
+    refresh_bf16(f);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PF_OK : ffail(f, PF_ECUDA, "pf_fno_adam", e);
+}
+
+int pf_fno_train_step(pf_fno* f, const float* x_dev, const float* target_dev, float lr, double* loss_out) {
+    if (!f || !x_dev || !target_dev) return ffail(f, PF_EINVAL, "pf_fno_train_step: NULL argument");
+    cudaSetDevice(f->dev);
+    int rc = fno_forward(f, x_dev);
+    if (!rc) rc = pf_fno_backward(f, target_dev, loss_out);
+    if (!rc) rc = pf_fno_adam(f, lr, 0.9f, 0.999f, 1e-8f);
+    return rc;
+}
+
+const char* pf_fno_last_error(const pf_fno* f) { return f ? f->err : g_fno_err; }
+
+// Surrogate proposal + judge (one call = one proposal).
+int pf_surrogate_step(pf_ctx* ctx, pf_fno* f, double tau, double h, double rtol, double atol, int* accepted,
+                      double* lte) {
+    if (!ctx || !f || !accepted || !(tau > 0) || !(h > 0)) return ffail(f, PF_EINVAL, "pf_surrogate_step: bad argument");
+    pf_grid g{};
+    double t0 = 0, h0 = 0;
+    pf_get_time(ctx, &t0, &h0);
+    cudaSetDevice(f->dev);
+    int rc = pf_ctx_grid(ctx, &g);
+    if (rc) return rc;
+    if (g.nx != f->d.nx || g.ny != f->d.ny || g.nz != f->d.nz)
+        return ffail(f, PF_EINVAL, "pf_surrogate_step: network and simulation grids differ");
+    const long long N = f->d.N;
+    const long long nk4 = 4LL * g.nz * g.ny * (g.nx / 2 + 1);
+    cudaError_t e = cudaSuccess;
+    if (!f->backup) {
+        e = falloc(&f->backup, sizeof(double2) * nk4);
+        if (e == cudaSuccess) e = falloc(&f->realbuf, sizeof(double) * 4 * N);
+        if (e != cudaSuccess) return ffail(f, PF_ENOMEM, "pf_surrogate_step: allocation", e);
+        f->backup_nk = nk4;
+    }
+    // y(t) -> backup (k space) and real space
+    rc = pf_get_state_hat(ctx, f->backup, 1);
+    if (!rc) rc = pf_get_state(ctx, f->realbuf, 1);
+    if (rc) return rc;
+    k_norm_in<<<grid_for(4 * N), kT, 0, f->s>>>(f->realbuf, f->x, N, f->in_mean, f->in_istd);
+    rc = fno_forward(f, f->x);
+    if (rc) return rc;
+    k_apply_delta<<<grid_for(4 * N), kT, 0, f->s>>>(f->realbuf, f->out, N, f->out_std);
+    e = cudaStreamSynchronize(f->s);
+    if (e != cudaSuccess) return ffail(f, PF_ECUDA, "pf_surrogate_step: proposal", e);
+    // proposal y^ in k space, with the composition mean of y(t) kept exactly
+    rc = pf_set_state(ctx, f->realbuf, 1);
+    if (!rc) rc = pf_copy_dc(ctx, f->backup);
+    if (rc) return rc;
+    pf_set_time(ctx, t0 + tau, h);
+    double e_j = 0.0;
+    rc = pf_step(ctx, h, &e_j);
+    if (rc) return rc;
+    if (lte) *lte = e_j;
+    if (std::isfinite(e_j) && e_j <= 1.0) {
+        *accepted = 1;
+        pf_set_time(ctx, t0 + tau + h, h0);
+        return PF_OK;
+    }
+    // rejected: restore y(t)
+    *accepted = 0;
+    rc = pf_set_state_hat(ctx, f->backup, 1);
+    pf_set_time(ctx, t0, h0);
+    return rc;
+}
+
+}  // extern "C"

@@ -41,6 +41,7 @@ struct Geo {
     const float* kz32;
     AxisPlan px, py, pz;
     unsigned mul_nx, mul_nxh;  // division magic for nx and nx/2+1
+    const int* active;         // batch member flag: kernels return at once when *active == 0
     int tx_y, tx_z, tx_el;  // tile widths (kx columns) of the strided passes
     int rp;                  // row pairs per CTA in the x passes
 };
@@ -62,6 +63,14 @@ struct Phys {
     double cvq[3][3];     // eps*_v : C : eps*_q
 };
 
+// Device-resident coefficients of one stage (or step completion) pass, written
+// each round by the batch prep kernel from the member's own step size.
+struct StageCoefDev {
+    double cI[kMaxStages], cE[kMaxStages];
+    double gamma, qgamma;
+    float cEh[kMaxStages], cEl[kMaxStages];
+};
+
 // Coefficients of one stage assembly / step completion pass.
 struct StageTerms {
     int n;                             // number of previous-stage terms
@@ -77,6 +86,25 @@ struct StageTerms {
     const double* qin;                 // table of 1/(1 - gamma lambda) for this gamma, or null
     double* qout;                      // if set: write 1/(1 - qgamma lambda) (once per step)
     double qgamma;
+    const StageCoefDev* dc;            // if set: cI, cE, cEh, cEl, gamma, qgamma come from here
+};
+
+// Step control of one ensemble member, on the device.
+struct MemberCtl {
+    double t, h, dt, e_prev, e_last;
+    int after_reject, nrej, active, accepted_now, status;
+    long long n_acc, n_rej, n_rhs;
+};
+
+// Butcher arrays and controller constants shared by the members of a batch.
+struct BatchConst {
+    int s, embedded, nrhs;
+    double AE[kMaxStages][kMaxStages], AI[kMaxStages][kMaxStages];
+    double bE[kMaxStages], bI[kMaxStages], btE[kMaxStages], btI[kMaxStages];
+    double gdiag;
+    double t_final, h_min, h_max, h0;
+    double safety, k1, k2, eta_max, eta_min, eta_rej;
+    int max_rejects, q;
 };
 
 enum XMode {
@@ -112,6 +140,10 @@ void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, cons
                             double2* zout, cudaStream_t s);
 void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s);
 void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, cudaStream_t s);
+// batch round: coefficients from the member's step, controller, accepted-state copy
+void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef, cudaStream_t s);
+void launch_batch_ctl(const BatchConst& bc, MemberCtl* ctl, const double* wrms_sum, double scale, cudaStream_t s);
+void launch_batch_accept(const Geo& g, const MemberCtl* ctl, const double2* ynew, double2* y, cudaStream_t s);
 void launch_reduce(const double* partials, int n, double scale, double* out, cudaStream_t s);
 void launch_energy_k(const Geo& g, const Phys& ph, const double2* y, const double2* hk, double* partials,
                      cudaStream_t s);

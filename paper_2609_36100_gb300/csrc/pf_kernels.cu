@@ -50,6 +50,17 @@ __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
 template <>
 __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
 
+// stage coefficients: kernel parameters, or the batch member's device copy
+__device__ __forceinline__ double cI_of(const StageTerms& st, int j) { return st.dc ? st.dc->cI[j] : st.cI[j]; }
+__device__ __forceinline__ double cE_of(const StageTerms& st, int j) { return st.dc ? st.dc->cE[j] : st.cE[j]; }
+__device__ __forceinline__ float cEh_of(const StageTerms& st, int j) { return st.dc ? st.dc->cEh[j] : st.cEh[j]; }
+__device__ __forceinline__ float cEl_of(const StageTerms& st, int j) { return st.dc ? st.dc->cEl[j] : st.cEl[j]; }
+__device__ __forceinline__ double gamma_of(const StageTerms& st) { return st.dc ? st.dc->gamma : st.gamma; }
+__device__ __forceinline__ double qgamma_of(const StageTerms& st) { return st.dc ? st.dc->qgamma : st.qgamma; }
+// batch members that reached t_final (or failed) skip all work
+#define PF_SKIP_INACTIVE(g) \
+    if ((g).active && *(g).active == 0) return
+
 template <typename T2>
 __device__ __forceinline__ double2 load_f(const void* p, long long i) {
     return to_d2(reinterpret_cast<const T2*>(p)[i]);
@@ -241,6 +252,7 @@ template <typename T, int TX>
 __global__ void __launch_bounds__(kThreads) k_z_stage(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st,
                                                       double2* __restrict__ zout,
                                                       typename Cx<T>::t* __restrict__ W) {
+    PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
@@ -260,20 +272,20 @@ __global__ void __launch_bounds__(kThreads) k_z_stage(Geo g, Phys ph, const doub
 #pragma unroll
         for (int j = 0; j < kMaxStages; ++j) {
             if (j < st.n) {
-                if ((st.mI >> j) & 1u) axpy(zi, st.cI[j], st.z[j][gi]);
+                if ((st.mI >> j) & 1u) axpy(zi, cI_of(st, j), st.z[j][gi]);
                 if ((st.mE >> j) & 1u) {
                     if (sizeof(T) == 4)
-                        fs.add(st.cEh[j], st.cEl[j], reinterpret_cast<const float2*>(st.f[j])[gi]);
+                        fs.add(cEh_of(st, j), cEl_of(st, j), reinterpret_cast<const float2*>(st.f[j])[gi]);
                     else
-                        axpy(r, st.cE[j], load_f<T2>(st.f[j], gi));
+                        axpy(r, cE_of(st, j), load_f<T2>(st.f[j], gi));
                 }
             }
         }
         axpy(r, lam, zi);
         if (sizeof(T) == 4) fs.flush(r);
-        if (st.qout) st.qout[gi] = 1.0 / (1.0 - st.qgamma * lam);
+        if (st.qout) st.qout[gi] = 1.0 / (1.0 - qgamma_of(st) * lam);
         if (st.has_gamma) {
-            const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - st.gamma * lam);
+            const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - gamma_of(st) * lam);
             r.x *= q;
             r.y *= q;
         }
@@ -302,6 +314,7 @@ void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageT
 // ---------------------------------------------------------------------------
 template <typename T, int SIGN, int TX>
 __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* __restrict__ buf) {
+    PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
@@ -341,6 +354,7 @@ void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
 template <typename T, typename OT2, int TX>
 __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typename Cx<T>::t* __restrict__ W,
                                                     OT2* __restrict__ out, int mode) {
+    PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
     using OT = decltype(OT2{}.x);
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -442,6 +456,7 @@ __device__ __forceinline__ void elastic_kernel(const PhysT<T>& pt, T kx, T ky, T
 
 template <typename T, int TX>
 __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename Cx<T>::t* __restrict__ H) {
+    PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int tile = TX * g.nz;
@@ -520,6 +535,7 @@ template <typename T, int TX>
 __global__ void __launch_bounds__(kThreads) k_z_final(Geo g, Phys ph, const double2* __restrict__ y, StageTerms bt,
                                                       StageTerms dt, int want_lte, double2* __restrict__ ynew,
                                                       typename Cx<T>::t* __restrict__ W) {
+    PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
@@ -544,18 +560,18 @@ __global__ void __launch_bounds__(kThreads) k_z_final(Geo g, Phys ph, const doub
                 const bool lI = want_lte && ((dt.mI >> j) & 1u), lE = want_lte && ((dt.mE >> j) & 1u);
                 if (bI || lI) {
                     const double2 zj = bt.z[j][gi];
-                    if (bI) axpy(zr, bt.cI[j], zj);
-                    if (lI) axpy(zl, dt.cI[j], zj);
+                    if (bI) axpy(zr, cI_of(bt, j), zj);
+                    if (lI) axpy(zl, cI_of(dt, j), zj);
                 }
                 if (bE || lE) {
                     if (sizeof(T) == 4) {
                         const float2 fj = reinterpret_cast<const float2*>(bt.f[j])[gi];
-                        if (bE) rs.add(bt.cEh[j], bt.cEl[j], fj);
-                        if (lE) ls.add(dt.cEh[j], dt.cEl[j], fj);
+                        if (bE) rs.add(cEh_of(bt, j), cEl_of(bt, j), fj);
+                        if (lE) ls.add(cEh_of(dt, j), cEl_of(dt, j), fj);
                     } else {
                         const double2 fj = load_f<T2>(bt.f[j], gi);
-                        if (bE) axpy(r, bt.cE[j], fj);
-                        if (lE) axpy(l, dt.cE[j], fj);
+                        if (bE) axpy(r, cE_of(bt, j), fj);
+                        if (lE) axpy(l, cE_of(dt, j), fj);
                     }
                 }
             }
@@ -691,6 +707,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
                                                      const T* __restrict__ Rin, double* __restrict__ partials,
                                                      double rtol, double atol, const double* __restrict__ real_in,
                                                      double* __restrict__ real_out, int P) {
+    PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx;
@@ -962,6 +979,7 @@ void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void*
 // ---------------------------------------------------------------------------
 __global__ void k_stage_pointwise(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st, int fe32,
                                   double2* __restrict__ zout) {
+    PF_SKIP_INACTIVE(g);
     const long long total = 4LL * g.NK;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
          gi += (long long)gridDim.x * blockDim.x) {
@@ -975,13 +993,13 @@ __global__ void k_stage_pointwise(Geo g, Phys ph, const double2* __restrict__ y,
 #pragma unroll
         for (int j = 0; j < kMaxStages; ++j) {
             if (j < st.n) {
-                if ((st.mI >> j) & 1u) axpy(v, st.cI[j] * lam, st.z[j][gi]);
+                if ((st.mI >> j) & 1u) axpy(v, cI_of(st, j) * lam, st.z[j][gi]);
                 if ((st.mE >> j) & 1u)
-                    axpy(v, st.cE[j], fe32 ? load_f<float2>(st.f[j], gi) : load_f<double2>(st.f[j], gi));
+                    axpy(v, cE_of(st, j), fe32 ? load_f<float2>(st.f[j], gi) : load_f<double2>(st.f[j], gi));
             }
         }
         if (st.has_gamma) {
-            const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - st.gamma * lam);
+            const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - gamma_of(st) * lam);
             v.x *= q;
             v.y *= q;
         }
@@ -1028,6 +1046,105 @@ __global__ void k_lambda_table(Geo g, Phys ph, double* __restrict__ lam) {
 
 void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, cudaStream_t s) {
     k_lambda_table<<<152 * 8, 256, 0, s>>>(g, ph, lam);
+}
+
+// ---------------------------------------------------------------------------
+// batch round kernels (one thread each, or a grid-stride copy)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fill_coef(StageCoefDev& c, int n, const double* aI, const double* aE, double dt,
+                                          double gam, double qgam) {
+    for (int j = 0; j < kMaxStages; ++j) {
+        const double ci = j < n ? dt * aI[j] : 0.0;
+        const double ce = j < n ? dt * aE[j] : 0.0;
+        c.cI[j] = ci;
+        c.cE[j] = ce;
+        const float h = (float)ce;
+        c.cEh[j] = h;
+        c.cEl[j] = (float)(ce - (double)h);
+    }
+    c.gamma = gam;
+    c.qgamma = qgam;
+}
+
+// step size of this round's attempt (clipped to t_final) and the stage /
+// completion coefficients built from it, as the host driver builds them
+__global__ void k_batch_prep(BatchConst bc, MemberCtl* __restrict__ ctl, StageCoefDev* __restrict__ coef) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    MemberCtl& m = *ctl;
+    if (!m.active) return;
+    const double dt = fmin(m.h, bc.t_final - m.t);
+    m.dt = dt;
+    for (int i = 0; i < bc.s; ++i)
+        fill_coef(coef[i], i, bc.AI[i], bc.AE[i], dt, dt * bc.AI[i][i], dt * bc.gdiag);
+    double dI[kMaxStages], dE[kMaxStages];
+    for (int j = 0; j < kMaxStages; ++j) {
+        dI[j] = bc.embedded ? bc.bI[j] - bc.btI[j] : 0.0;
+        dE[j] = bc.embedded ? bc.bE[j] - bc.btE[j] : 0.0;
+    }
+    fill_coef(coef[bc.s], bc.s, bc.bI, bc.bE, dt, 0.0, 0.0);
+    fill_coef(coef[bc.s + 1], bc.s, dI, dE, dt, 0.0, 0.0);
+}
+
+// accept / reject and the next step size (same PI rule as the host driver)
+__global__ void k_batch_ctl(BatchConst bc, MemberCtl* __restrict__ ctl, const double* __restrict__ wsum, double scale) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    MemberCtl& m = *ctl;
+    m.accepted_now = 0;
+    if (!m.active) return;
+    const double e = bc.embedded ? sqrt(wsum[0] * scale) : 0.0;
+    m.e_last = e;
+    m.n_rhs += bc.nrhs;
+    const bool ok = isfinite(e) && e <= 1.0;
+    const double h = m.dt;
+    double hn;
+    if (ok) {
+        m.t += h;
+        m.n_acc += 1;
+        m.nrej = 0;
+        m.accepted_now = 1;
+        if (bc.embedded) {
+            const double ee = e < 1e-10 ? 1e-10 : e;
+            double eta = bc.safety * pow(ee, -bc.k1 / bc.q) * pow(m.e_prev, bc.k2 / bc.q);
+            const double cap = m.after_reject ? 1.0 : bc.eta_max;
+            eta = fmin(cap, fmax(bc.eta_min, eta));
+            m.e_prev = ee;
+            m.after_reject = 0;
+            hn = h * eta;
+        } else {
+            hn = bc.h0;
+        }
+    } else {
+        m.n_rej += 1;
+        if (++m.nrej > bc.max_rejects) {
+            m.status = isfinite(e) ? -5 : -4;  // PF_ESTEPFAIL / PF_ENONFINITE
+            m.active = 0;
+            return;
+        }
+        m.after_reject = 1;
+        hn = isfinite(e) ? h * fmax(bc.eta_rej, bc.safety * pow(e, -1.0 / bc.q)) : h * 0.25;
+    }
+    m.h = fmin(fmax(hn, bc.h_min), bc.h_max);
+    if (!(m.t < bc.t_final * (1 - 1e-14))) m.active = 0;
+}
+
+// y <- y_new for an accepted attempt
+__global__ void k_batch_accept(Geo g, const MemberCtl* __restrict__ ctl, const double2* __restrict__ ynew,
+                               double2* __restrict__ y) {
+    if (!ctl->accepted_now) return;
+    const long long total = 4LL * g.NK;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = ynew[i];
+}
+
+void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef, cudaStream_t s) {
+    k_batch_prep<<<1, 32, 0, s>>>(bc, ctl, coef);
+}
+void launch_batch_ctl(const BatchConst& bc, MemberCtl* ctl, const double* wrms_sum, double scale, cudaStream_t s) {
+    k_batch_ctl<<<1, 32, 0, s>>>(bc, ctl, wrms_sum, scale);
+}
+void launch_batch_accept(const Geo& g, const MemberCtl* ctl, const double2* ynew, double2* y, cudaStream_t s) {
+    k_batch_accept<<<152 * 4, 256, 0, s>>>(g, ctl, ynew, y);
 }
 
 // deterministic single-CTA reduction: out = sum(partials) * scale (FP64)
