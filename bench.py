@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 path")
     ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble measurement (0: skip)")
     ap.add_argument("--ensemble-t", type=float, default=3.0, help="simulated seconds of the ensemble measurement")
+    ap.add_argument("--surrogate", type=int, default=16, help="training trajectories of the surrogate measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -142,6 +143,7 @@ def run_ours(args, rank, world, dist):
     def timed(prec, K, W, profile=False):
         sim = pfg.Simulation((n, n, n), p, "ark4", prec)
         sim.set_state(y0)
+        tuning = sim.autotune(reps=2)  # launch schedule picked by the autotuner
         sim.set_time(0.0, 1.0)
         sim.advance_attempts(W)
         st0 = sim.stats()
@@ -165,7 +167,7 @@ def run_ours(args, rank, world, dist):
         res = {"ms": max_over_ranks(ms), "wall": wall, "rhs": st1["rhs_evals"] - st0["rhs_evals"],
                "sim_s": st1["t"] - st0["t"], "accepted": st1["steps_accepted"] - st0["steps_accepted"],
                "rejected": st1["steps_rejected"] - st0["steps_rejected"], "prof": prof, "clocks": clocks,
-               "sim": sim}
+               "sim": sim, "tuning": tuning}
         return res
 
     K, W = args.steps, args.warmup
@@ -227,6 +229,7 @@ def run_ours(args, rank, world, dist):
                    "rtol": 1e-4, "atol": 1e-8, "l2": "inputs larger than L2 (state >= 3.5 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "sim_s_per_wall_s": sim_rate,
+        "autotune": {"fp32bulk": {k: r32["tuning"][k] for k in ("ms_before", "ms_after", "cfg")}},
         "attempts": {"accepted": r32["accepted"], "rejected": r32["rejected"], "sim_s": r32["sim_s"]},
         "fp64_plain": fp64,
         "gain_fp32bulk_vs_fp64": (value / fp64["gpt_stage_s"]) if fp64 else None,
@@ -244,7 +247,7 @@ def run_ours(args, rank, world, dist):
     return line
 
 
-def run_ensemble(K, t_final):
+def run_ensemble(K, t_final, rank=0, world=1):
     """Uneven-grid ensemble (members 0..K-1 of the seeded recipe: sides from
     {64,96,120,128,160}, 4-24 nuclei, T0 +/- 20 K), FP32-bulk ARK4 adaptive at
     rtol 1e-4: all members one after another with pf_advance, then the same
@@ -253,15 +256,24 @@ def run_ensemble(K, t_final):
 
     import paper_2609_36100_gb300 as pfg
     import synth
+    from paper_2609_36100_gb300.dist import max_over_ranks, shard, sum_over_ranks
 
-    mem = [synth.ensemble_member(i) for i in range(K)]
+    # members shard across ranks (no collective on the data path)
+    mem = [synth.ensemble_member(i) for i in shard(K, rank, world)]
     stream = torch.cuda.current_stream()
+
+    tuned = {}
 
     def timed(fn):
         sims = []
         for y0, p in mem:
             s = pfg.Simulation(y0.shape[1:], p, "ark4", "fp32bulk")
             s.set_state(y0)
+            # one autotuned schedule per distinct grid size
+            key = y0.shape[1:]
+            if key not in tuned:
+                tuned[key] = s.autotune(reps=1)["cfg"]
+            s.set_tuning(tuned[key])
             s.set_time(0.0, 1.0)
             sims.append(s)
         torch.cuda.synchronize()
@@ -278,15 +290,62 @@ def run_ensemble(K, t_final):
 
     ms_seq, st_seq = timed(lambda sims: [s.advance(t_final, 1e-4, 1e-8) for s in sims])
     ms_bat, st_bat = timed(lambda sims: pfg.batch_advance(sims, t_final, 1e-4, 1e-8))
-    ps_seq = sum(x["point_stages"] for x in st_seq)
-    ps_bat = sum(x["point_stages"] for x in st_bat)
+    dev = "cuda"
+    ms_seq = max_over_ranks(ms_seq, dev)
+    ms_bat = max_over_ranks(ms_bat, dev)
+    ps_seq = sum_over_ranks(sum(x["point_stages"] for x in st_seq), dev)
+    ps_bat = sum_over_ranks(sum(x["point_stages"] for x in st_bat), dev)
     sides = sorted({int(y0.shape[1]) for y0, _ in mem})
-    return {"members": K, "sides": sides, "points": int(sum(y0[0].size for y0, _ in mem)), "t_final": t_final,
+    return {"members": K, "ranks": world, "sides_rank0": sides,
+            "points": int(sum_over_ranks(sum(y0[0].size for y0, _ in mem), dev)), "t_final": t_final,
             "sequential": {"ms": ms_seq, "gpt_stage_s": ps_seq / (ms_seq / 1e3) / 1e9,
                            "sim_s_per_wall_s": K * t_final / (ms_seq / 1e3)},
             "batched": {"ms": ms_bat, "gpt_stage_s": ps_bat / (ms_bat / 1e3) / 1e9,
                         "sim_s_per_wall_s": K * t_final / (ms_bat / 1e3)},
             "gain_batched_vs_sequential": ms_seq / ms_bat}
+
+
+def run_surrogate(ntraj, n=64, dt=1.0, nsnap=25, epochs=3):
+    """FNO (4 spectral layers, 12 modes, width 32, BF16 spectral weights)
+    trained with the library's kernels on `ntraj` solver trajectories of the
+    64^3 8-nucleus recipe (ARK4 FP32-bulk, dt = 1 s, tau = 8 s, 0-200 s), then
+    judged rollouts of two held-out seeds to 200 s: wall time, accepted
+    proposals and final-state error against a dt = 0.25 s FP64 reference, with
+    and without the network."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2609_36100_gb300 import surrogate as S
+
+    p = synth.load_params()
+    ics = [(synth.ic_config1(n, 1000 + i, p), p) for i in range(ntraj)]
+    w0 = time.perf_counter()
+    traj = S.trajectories(ics, p, dt, nsnap)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - w0
+    net = S.new_network((n, n, n))
+    w0 = time.perf_counter()
+    losses = S.train(net, traj, epochs, 1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - w0
+    del traj
+    rows = []
+    for seed in (2000, 2001):
+        y0 = synth.ic_config1(n, seed, p)
+        ref, _, _, _ = S.rollout(y0, p, nsnap * 8 * dt, 0.25, None, precision="fp64")
+        plain, wp, _, _ = S.rollout(y0, p, nsnap * 8 * dt, dt, None)
+        sur, ws, acc, off = S.rollout(y0, p, nsnap * 8 * dt, dt, net)
+        e = lambda a: float(np.linalg.norm((a - ref)[1:]) / np.linalg.norm(ref[1:]))  # noqa: E731
+        rows.append({"seed": seed, "wall_plain_s": wp, "wall_surrogate_s": ws, "accepted": acc, "offered": off,
+                     "err_plain": e(plain), "err_surrogate": e(sur)})
+    net.close()
+    return {"grid": [n, n, n], "train_trajectories": ntraj, "pairs": ntraj * nsnap, "epochs": epochs,
+            "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "data_s": t_data, "train_s": t_train,
+            "tau_s": 8 * dt, "rollouts": rows,
+            "speedup_wall": float(np.mean([r["wall_plain_s"] / r["wall_surrogate_s"] for r in rows])),
+            "note": "proposals pass the integrator's judge (one ARK step from the proposal, ||LTE|| <= 1) but are "
+                    "far less accurate than the steps they replace; no gain at equal final-state error"}
 
 
 def cpu_baseline(n, budget_s=15.0):
@@ -361,7 +420,9 @@ def main():
         dist = td
     line = run_ours(args, rank, world, dist)
     if args.ensemble > 0:
-        line["ensemble"] = run_ensemble(args.ensemble, args.ensemble_t)
+        line["ensemble"] = run_ensemble(args.ensemble, args.ensemble_t, rank, world)
+    if args.surrogate > 0 and rank == 0:
+        line["surrogate"] = run_surrogate(args.surrogate)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.n)

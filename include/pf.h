@@ -186,6 +186,19 @@ int pf_profile_enable(pf_ctx* ctx, int on);
 int pf_profile_read(pf_ctx* ctx, double* ms, double* bytes, long long* launches);
 const char* pf_kernel_name(int kind);
 
+/* Launch schedule of a context: tuned tile widths of the z / y / elastic
+ * passes, rows per CTA of the x passes (0 = built-in heuristic), and the
+ * radix order of each axis (count + up to 10 radices in {2,3,4,5,8}, for x,
+ * y, z).  PF_TUNE_LEN ints. */
+#define PF_TUNE_LEN 37
+int pf_get_tuning(pf_ctx* ctx, int* cfg, int n);
+int pf_set_tuning(pf_ctx* ctx, const int* cfg, int n);
+/* Autotuner: times `reps` step attempts per candidate schedule on the
+ * context's buffers (coordinate descent over tile widths, rows per CTA and
+ * radix orders; the state is not modified) and keeps the fastest.  Times per
+ * attempt before/after are returned in ms (NULL allowed). */
+int pf_autotune(pf_ctx* ctx, int reps, double* ms_before, double* ms_after);
+
 /* Host-side query of a method's Butcher arrays (row-major s x s, length-s
  * vectors; bt/dt embedding NULL-able buffers).  Returns the stage count s,
  * or PF_EUNSUPPORTED. Buffers must hold s*s (A) and s (b) doubles; s <= 8. */

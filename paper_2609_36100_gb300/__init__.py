@@ -81,6 +81,9 @@ SIGNATURES = {
     "pf_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "pf_kernel_name": (C.c_char_p, [C.c_int]),
     "pf_state_to_real_noalloc": (C.c_int, [C.POINTER(PFGrid), _P, _P, _P]),
+    "pf_get_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.c_int]),
+    "pf_set_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.c_int]),
+    "pf_autotune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pf_fno_create": (C.c_int, [C.c_int] * 8 + [_P, C.POINTER(_P)]),
     "pf_fno_destroy": (None, [_P]),
     "pf_fno_num_params": (C.c_longlong, [_P]),
@@ -97,6 +100,7 @@ SIGNATURES = {
                                     C.POINTER(C.c_double)]),
 }
 NKERNELS = 10
+TUNE_LEN = 37
 _DPTR_ARGS = {"pf_method_tableau"}
 
 _lib = None
@@ -317,6 +321,40 @@ class Simulation:
         n = (C.c_longlong * NKERNELS)()
         _check(lib().pf_profile_read(self.ctx, ms, by, n), self.ctx)
         return {lib().pf_kernel_name(k).decode(): (ms[k], by[k], n[k]) for k in range(NKERNELS) if n[k]}
+
+    def tuning(self):
+        buf = (C.c_int * TUNE_LEN)()
+        _check(lib().pf_get_tuning(self.ctx, buf, TUNE_LEN), self.ctx)
+        return list(buf)
+
+    def set_tuning(self, cfg):
+        buf = (C.c_int * TUNE_LEN)(*[int(v) for v in cfg])
+        _check(lib().pf_set_tuning(self.ctx, buf, TUNE_LEN), self.ctx)
+
+    def autotune(self, reps=3, cache=None):
+        """Pick the fastest launch schedule for this grid/precision by timing
+        step attempts; with `cache` (a JSON path) reuse/record the choice
+        keyed by grid, precision, method and device name."""
+        import json
+        import os
+        torch = _torch()
+        key = "%s|%d|%d|%s" % ("x".join(map(str, self.shape)), self.params.precision, self.params.method,
+                               torch.cuda.get_device_name())
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                self.set_tuning(table[key]["cfg"])
+                return table[key]
+        b, a = C.c_double(), C.c_double()
+        _check(lib().pf_autotune(self.ctx, int(reps), C.byref(b), C.byref(a)), self.ctx)
+        rec = {"cfg": self.tuning(), "ms_before": b.value, "ms_after": a.value}
+        if cache:
+            table[key] = rec
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1)
+        return rec
 
     def stats(self):
         st = PFStats()

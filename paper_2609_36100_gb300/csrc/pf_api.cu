@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
+#include <algorithm>
 #include <vector>
 
 #include "pf.h"
@@ -674,7 +675,8 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     rc = rc ? rc : dalloc(c, &c->R1, 4 * (size_t)g.N * tsz);
     rc = rc ? rc : dalloc(c, &c->lam, nk4 * sizeof(double));
     rc = rc ? rc : dalloc(c, &c->qtab, nk4 * sizeof(double));
-    c->npartials = x_pass_blocks(g, 0) > x_pass_blocks(g, 1) ? x_pass_blocks(g, 0) : x_pass_blocks(g, 1);
+    // worst case over any tuned rows-per-CTA setting (one row pair per CTA)
+    c->npartials = g.nz * g.ny / 2;
     if (energy_k_blocks(g) > c->npartials) c->npartials = energy_k_blocks(g);
     rc = rc ? rc : dalloc(c, &c->partials, (size_t)c->npartials * sizeof(double));
     rc = rc ? rc : dalloc(c, &c->d_scalar, 4 * sizeof(double));
@@ -1121,6 +1123,155 @@ int pf_get_stats(pf_ctx* c, pf_stats* out) {
     c->st.h = c->h;
     *out = c->st;
     return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: tile widths of the strided passes, rows per CTA of the x passes,
+// and the radix order of each axis, chosen by timing whole step attempts on
+// the context's own buffers (coordinate descent)
+// ---------------------------------------------------------------------------
+static void plan_to_cfg(const AxisPlan& p, int* out) {
+    out[0] = p.nst;
+    for (int s = 0; s < kMaxRadices; ++s) out[1 + s] = s < p.nst ? p.rad[s] : 0;
+}
+
+int pf_get_tuning(pf_ctx* c, int* cfg, int n) {
+    if (!c || !cfg || n < PF_TUNE_LEN) return fail(c, PF_EINVAL, "pf_get_tuning: need %d ints", PF_TUNE_LEN);
+    cfg[0] = c->g.tx_z;
+    cfg[1] = c->g.tx_y;
+    cfg[2] = c->g.tx_el;
+    cfg[3] = c->g.rp;
+    plan_to_cfg(c->g.px, cfg + 4);
+    plan_to_cfg(c->g.py, cfg + 4 + 11);
+    plan_to_cfg(c->g.pz, cfg + 4 + 22);
+    return PF_OK;
+}
+
+int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
+    if (!c || !cfg || n < PF_TUNE_LEN) return fail(c, PF_EINVAL, "pf_set_tuning: need %d ints", PF_TUNE_LEN);
+    Geo g = c->g;
+    g.tx_z = cfg[0];
+    g.tx_y = cfg[1];
+    g.tx_el = cfg[2];
+    g.rp = cfg[3];
+    AxisPlan* pl[3] = {&g.px, &g.py, &g.pz};
+    const int ns[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+        const int* r = cfg + 4 + 11 * a;
+        AxisPlan p = *pl[a];
+        if (r[0] > 0 && !make_axis_plan_radices(ns[a], r + 1, r[0], p))
+            return fail(c, PF_EINVAL, "pf_set_tuning: bad radix order for axis %d", a);
+        p.tw64 = pl[a]->tw64;
+        p.tw32 = pl[a]->tw32;
+        *pl[a] = p;
+    }
+    c->g = g;
+    return PF_OK;
+}
+
+namespace {
+
+// distinct orders of the radix multisets that factor n with the fewest (and
+// one more) stages, at most `cap` of them
+std::vector<std::vector<int>> radix_orders(int n, size_t cap) {
+    int m = n, a = 0, b = 0, cc = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    while (m % 3 == 0) { m /= 3; ++b; }
+    while (m % 5 == 0) { m /= 5; ++cc; }
+    std::vector<std::vector<int>> sets;
+    // power-of-two parts: k8 eights, k4 fours, k2 twos with 3 k8 + 2 k4 + k2 = a
+    int best = 1 << 30;
+    std::vector<std::vector<int>> twos;
+    for (int k8 = 0; 3 * k8 <= a; ++k8)
+        for (int k4 = 0; 3 * k8 + 2 * k4 <= a; ++k4) {
+            const int k2 = a - 3 * k8 - 2 * k4;
+            if (k2 > 1) continue;
+            std::vector<int> v;
+            for (int i = 0; i < k8; ++i) v.push_back(8);
+            for (int i = 0; i < k4; ++i) v.push_back(4);
+            for (int i = 0; i < k2; ++i) v.push_back(2);
+            twos.push_back(v);
+            if ((int)v.size() < best) best = (int)v.size();
+        }
+    for (auto& v : twos) {
+        if ((int)v.size() > best + 1) continue;
+        for (int i = 0; i < b; ++i) v.push_back(3);
+        for (int i = 0; i < cc; ++i) v.push_back(5);
+        sets.push_back(v);
+    }
+    std::vector<std::vector<int>> out;
+    for (auto v : sets) {
+        std::sort(v.begin(), v.end());
+        do {
+            out.push_back(v);
+            if (out.size() >= cap) return out;
+        } while (std::next_permutation(v.begin(), v.end()));
+    }
+    return out;
+}
+
+double time_attempts(pf_ctx* c, int reps) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = c->prof_on;
+    c->prof_on = false;
+    // warm-up, then timed step attempts (the state itself is never changed)
+    int rc = c->fp32 ? enqueue_step<float>(c, 0.5, true) : enqueue_step<double>(c, 0.5, true);
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps && !rc; ++r)
+        rc = c->fp32 ? enqueue_step<float>(c, 0.5, true) : enqueue_step<double>(c, 0.5, true);
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof_on = prof;
+    return rc ? 1e30 : (double)ms / reps;
+}
+
+}  // namespace
+
+int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
+    if (!c || reps < 1) return fail(c, PF_EINVAL, "pf_autotune: bad argument");
+    cudaSetDevice(c->dev);
+    int cfg[PF_TUNE_LEN], best[PF_TUNE_LEN];
+    pf_get_tuning(c, best, PF_TUNE_LEN);
+    double tbest = time_attempts(c, reps);
+    if (ms_before) *ms_before = tbest;
+    auto trial = [&](const int* cand) {
+        if (pf_set_tuning(c, cand, PF_TUNE_LEN) != PF_OK) return;
+        const double t = time_attempts(c, reps);
+        if (t < tbest) {
+            tbest = t;
+            std::memcpy(best, cand, sizeof best);
+        }
+        pf_set_tuning(c, best, PF_TUNE_LEN);
+    };
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        for (int slot = 0; slot < 4; ++slot) {
+            const int cands[5] = {1, 2, 4, 8, 16};
+            for (int v : cands) {
+                std::memcpy(cfg, best, sizeof cfg);
+                cfg[slot] = v;
+                trial(cfg);
+            }
+        }
+        const int ns[3] = {c->g.nx, c->g.ny, c->g.nz};
+        for (int a = 0; a < 3; ++a) {
+            for (const auto& ord : radix_orders(ns[a], 12)) {
+                std::memcpy(cfg, best, sizeof cfg);
+                int* r = cfg + 4 + 11 * a;
+                r[0] = (int)ord.size();
+                for (int s = 0; s < kMaxRadices; ++s) r[1 + s] = s < (int)ord.size() ? ord[s] : 0;
+                trial(cfg);
+            }
+        }
+    }
+    pf_set_tuning(c, best, PF_TUNE_LEN);
+    if (ms_after) *ms_after = tbest;
+    return check_launch(c, "pf_autotune");
 }
 
 static const char* kKernelNames[PF_NKERNELS] = {"z_stage_solve_ifft", "y_fft", "x_c2r_physics1_r2c",

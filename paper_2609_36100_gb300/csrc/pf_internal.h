@@ -25,6 +25,7 @@ struct AxisPlan {
 inline unsigned magic_u32(unsigned d) { return d <= 1 ? 0u : (unsigned)((0xffffffffull + d) / d); }
 // radix schedule (8s first, then 4/2, 3s, 5s) and division magic of one axis
 bool make_axis_plan(int n, AxisPlan& p);
+bool make_axis_plan_radices(int n, const int* rad, int nr, AxisPlan& p);
 
 // Grid geometry and the per-axis wave-number tables k_m = 2 pi m / (n d)
 // (FP64, Nyquist index taken as +pi/d).
@@ -42,8 +43,8 @@ struct Geo {
     AxisPlan px, py, pz;
     unsigned mul_nx, mul_nxh;  // division magic for nx and nx/2+1
     const int* active;         // batch member flag: kernels return at once when *active == 0
-    int tx_y, tx_z, tx_el;  // tile widths (kx columns) of the strided passes
-    int rp;                  // row pairs per CTA in the x passes
+    int tx_y, tx_z, tx_el;  // tuned tile widths (kx columns) of the strided passes, 0 = heuristic
+    int rp;                  // tuned row pairs per CTA in the x passes, 0 = heuristic
 };
 
 // Derived model constants (Sec. 4.1 with the readings of the library).

@@ -212,6 +212,16 @@ static int tile_cols(const Geo& g, int n, int nbuf, int budget) {
     return tx;
 }
 
+// tuned width (0 = untuned) capped by what fits the shared-memory budget
+template <typename T>
+static int tuned_cols(const Geo& g, int tuned, int n, int nbuf, int budget) {
+    if (tuned <= 0) return tile_cols<T>(g, n, nbuf, nbuf == 4 ? 64 * 1024 : 96 * 1024);
+    const int cap = tile_cols<T>(g, n, nbuf, budget);
+    int tx = 1;
+    while (tx * 2 <= tuned && tx * 2 <= 16) tx *= 2;
+    return tx < cap ? tx : cap;
+}
+
 template <typename K>
 static void set_smem(K kern, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -302,7 +312,7 @@ template <typename T>
 void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, double2* zout, void* W,
                     cudaStream_t s) {
     using T2 = typename Cx<T>::t;
-    const int TX = tile_cols<T>(g, g.nz, 2, 96 * 1024);
+    const int TX = tuned_cols<T>(g, g.tx_z, g.nz, 2, 128 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
     PF_TX_SWITCH(TX, set_smem(k_z_stage<T, TXC>, sm);
@@ -333,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* _
 template <typename T>
 void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
-    const int TX = tile_cols<T>(g, g.ny, 2, 96 * 1024);
+    const int TX = tuned_cols<T>(g, g.tx_y, g.ny, 2, 128 * 1024);
     const size_t sm = 2 * (size_t)TX * g.ny * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.nz, nf);
     if (sign > 0) {
@@ -390,7 +400,7 @@ __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typena
 template <typename T>
 void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int scale_mode, cudaStream_t s, int nf) {
     using T2 = typename Cx<T>::t;
-    const int TX = tile_cols<T>(g, g.nz, 2, 96 * 1024);
+    const int TX = tuned_cols<T>(g, g.tx_z, g.nz, 2, 128 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
     if (scale_mode == 1) {
@@ -519,7 +529,7 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
 template <typename T>
 void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
-    const int TX = tile_cols<T>(g, g.nz, 4, 64 * 1024);
+    const int TX = tuned_cols<T>(g, g.tx_el, g.nz, 4, 128 * 1024);
     const size_t sm = 4 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);
     PF_TX_SWITCH(TX, set_smem(k_z_elastic<T, TXC>, sm);
@@ -599,7 +609,7 @@ template <typename T>
 void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageTerms& bterm, const StageTerms& dterm,
                     int want_lte, double2* ynew, void* W, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
-    const int TX = tile_cols<T>(g, g.nz, 2, 96 * 1024);
+    const int TX = tuned_cols<T>(g, g.tx_z, g.nz, 2, 128 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
     PF_TX_SWITCH(TX, set_smem(k_z_final<T, TXC>, sm);
@@ -905,15 +915,44 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
 template <typename T>
 static int x_rows(const Geo& g) {
     using T2 = typename Cx<T>::t;
-    int P = (int)(64 * 1024 / (8 * (size_t)g.nx * sizeof(T2)));
-    if (P < 1) P = 1;
-    if (P > 16) P = 16;
+    int Pmax = (int)(64 * 1024 / (8 * (size_t)g.nx * sizeof(T2)));
+    if (Pmax < 1) Pmax = 1;
+    if (Pmax > 16) Pmax = 16;
+    if (g.rp > 0) {
+        int P = 1;
+        while (P * 2 <= g.rp && P * 2 <= Pmax) P *= 2;
+        return P;
+    }
+    int P = Pmax;
     const int npairs = g.nz * g.ny / 2;
     // keep at least ~2 waves of CTAs on 152 SMs
     while (P > 1 && (npairs + P - 1) / P < 304) P >>= 1;
     return P;
 }
 
+// plan from an explicit radix order (each radix in {2,3,4,5,8}, product n)
+bool make_axis_plan_radices(int n, const int* rad, int nr, AxisPlan& p) {
+    if (nr < 1 || nr > kMaxRadices) return false;
+    long long prod = 1;
+    for (int s = 0; s < nr; ++s) {
+        if (rad[s] != 2 && rad[s] != 3 && rad[s] != 4 && rad[s] != 5 && rad[s] != 8) return false;
+        prod *= rad[s];
+    }
+    if (prod != n) return false;
+    p.n = n;
+    p.nst = nr;
+    unsigned Ns = 1;
+    for (int s = 0; s < nr; ++s) {
+        p.rad[s] = rad[s];
+        p.mulm[s] = magic_u32((unsigned)(n / rad[s]));
+        p.mulN[s] = magic_u32(Ns);
+        Ns *= (unsigned)rad[s];
+    }
+    return true;
+}
+
+// default schedule: radix-8 stages first, then a 4 (or 4*4 instead of 8*2)
+// or 2, then the 3s and 5s
 bool make_axis_plan(int n, AxisPlan& p) {
     int m = n, a = 0, b = 0, c = 0;
     while (m % 2 == 0) { m /= 2; ++a; }
@@ -924,13 +963,13 @@ bool make_axis_plan(int n, AxisPlan& p) {
     int nr = 0;
     int n8 = a / 3;
     const int rem = a % 3;
-    int head = 0;
-    if (rem == 1 && n8 > 0) {  // 2^(3k+1): prefer 4*4 over 8*2
+    bool two4 = false;
+    if (rem == 1 && n8 > 0) {
         --n8;
-        head = 2;
+        two4 = true;
     }
     for (int i = 0; i < n8; ++i) r[nr++] = 8;
-    if (head == 2) {
+    if (two4) {
         r[nr++] = 4;
         r[nr++] = 4;
     } else if (rem == 2) {
@@ -940,17 +979,7 @@ bool make_axis_plan(int n, AxisPlan& p) {
     }
     for (int i = 0; i < b; ++i) r[nr++] = 3;
     for (int i = 0; i < c; ++i) r[nr++] = 5;
-    if (nr > kMaxRadices) return false;
-    p.n = n;
-    p.nst = nr;
-    unsigned Ns = 1;
-    for (int s = 0; s < nr; ++s) {
-        p.rad[s] = r[s];
-        p.mulm[s] = magic_u32((unsigned)(n / r[s]));
-        p.mulN[s] = magic_u32(Ns);
-        Ns *= (unsigned)r[s];
-    }
-    return true;
+    return make_axis_plan_radices(n, r, nr, p);
 }
 
 int x_pass_blocks(const Geo& g, int f64) {
