@@ -159,6 +159,7 @@ struct pf_ctx {
     void* R = nullptr;
     void* R1 = nullptr;
     double* lam = nullptr;   // [4][NK] lambda(k), FP64
+    float2* lamdf = nullptr;  // [4][NK] lambda(k), double-float (FP32-bulk contexts)
     double* qtab = nullptr;  // [4][NK] 1/(1 - dt gamma lambda) of the current step (ESDIRK diagonal)
     double gdiag = 0.0;      // common nonzero implicit diagonal entry, or 0
     double* partials = nullptr;
@@ -214,6 +215,33 @@ int check_launch(pf_ctx* c, const char* where) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(c, PF_ECUDA, "%s: %s", where, cudaGetErrorString(e));
     return PF_OK;
+}
+
+template <typename T>
+void typed_phys(const Phys& ph, double invN, PhysT<T>& o) {
+    o.Bv = (T)ph.Bv;
+    o.Bm = (T)ph.Bm;
+    o.inv2Av = (T)ph.inv2Av;
+    o.inv2Am = (T)ph.inv2Am;
+    o.A0m = (T)ph.A0m;
+    o.A0v = (T)ph.A0v;
+    o.Am = (T)ph.Am;
+    o.Av = (T)ph.Av;
+    o.wb2 = (T)(2.0 * ph.wbar);
+    o.ie = (T)(1.0 / ph.pair_eps);
+    o.twoAm = (T)(2.0 * ph.Am);
+    o.C44 = (T)ph.C44;
+    o.Cm = (T)ph.Cmix;
+    o.Ca = (T)ph.Caniso;
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            o.w[a][b] = (T)ph.w[a][b];
+            o.cvq[a][b] = (T)ph.cvq[a][b];
+        }
+        for (int b = 0; b < 6; ++b) o.sig[a][b] = (T)ph.sig[a][b];
+    }
+    o.mN = (T)(-ph.M * invN);
+    o.lN = (T)(-ph.L * invN);
 }
 
 void derive_phys(const pf_params& p, Phys& ph) {
@@ -283,6 +311,7 @@ void free_all(pf_ctx* c) {
     cudaFree(c->R);
     cudaFree(c->R1);
     cudaFree(c->lam);
+    cudaFree(c->lamdf);
     cudaFree(c->qtab);
     cudaFree(c->partials);
     cudaFree(c->d_scalar);
@@ -365,13 +394,19 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef 
             terms += (st.cI[j] != 0.0 && !c->alias_y[j] ? 16.0 : 0.0) + (st.cE[j] != 0.0 ? (c->fp32 ? 8.0 : 16.0) : 0.0);
         }
         st.gamma = dt * tb.AI[i][i];
-        for (int j = 0; j < i; ++j) split_ds(st.cE[j], st.cEh[j], st.cEl[j]);
+        for (int j = 0; j < i; ++j) {
+            split_ds(st.cE[j], st.cEh[j], st.cEl[j]);
+            split_ds(st.cI[j], st.cIh[j], st.cIl[j]);
+            if (c->alias_y[j]) st.mY |= 1u << j;
+        }
+        split_ds(st.gamma, st.gh, st.gl);
         set_masks(st);
         st.dc = dcoef ? dcoef + i : nullptr;
         if (c->gdiag != 0.0) {
             if (i == 0) {
                 st.qout = c->qtab;
                 st.qgamma = dt * c->gdiag;
+                split_ds(st.qgamma, st.qgh, st.qgl);
             } else if (st.gamma != 0.0) {
                 st.qin = c->qtab;
             }
@@ -443,6 +478,9 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef 
         }
         split_ds(bt.cE[j], bt.cEh[j], bt.cEl[j]);
         split_ds(dtm.cE[j], dtm.cEh[j], dtm.cEl[j]);
+        split_ds(bt.cI[j], bt.cIh[j], bt.cIl[j]);
+        split_ds(dtm.cI[j], dtm.cIh[j], dtm.cIl[j]);
+        if (c->alias_y[j]) bt.mY = dtm.mY = bt.mY | (1u << j);
         set_masks(bt);
         set_masks(dtm);
         bt.dc = dcoef ? dcoef + tb.s : nullptr;
@@ -630,6 +668,10 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     g.nxh = g.nx / 2 + 1;
     g.NK = (long long)g.nz * g.ny * g.nxh;
     g.N = (long long)g.nz * g.ny * g.nx;
+    g.invN = 1.0 / (double)g.N;
+    g.invN32 = (float)g.invN;
+    typed_phys(c->ph, g.invN, c->ph.t64);
+    typed_phys(c->ph, g.invN, c->ph.t32);
     g.mul_nx = magic_u32((unsigned)g.nx);
     g.mul_nxh = magic_u32((unsigned)g.nxh);
     int rc = PF_OK;
@@ -674,6 +716,7 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     rc = rc ? rc : dalloc(c, &c->R, 4 * (size_t)g.N * tsz);
     rc = rc ? rc : dalloc(c, &c->R1, 4 * (size_t)g.N * tsz);
     rc = rc ? rc : dalloc(c, &c->lam, nk4 * sizeof(double));
+    if (c->fp32) rc = rc ? rc : dalloc(c, &c->lamdf, nk4 * sizeof(float2));
     rc = rc ? rc : dalloc(c, &c->qtab, nk4 * sizeof(double));
     // worst case over any tuned rows-per-CTA setting (one row pair per CTA)
     c->npartials = g.nz * g.ny / 2;
@@ -716,9 +759,10 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
         g.kx = c->d_kx;
         g.ky = c->d_ky;
         g.kz = c->d_kz;
-        launch_lambda_table(g, c->ph, c->lam, c->stream);
+        launch_lambda_table(g, c->ph, c->lam, c->lamdf, c->stream);
         e = cudaGetLastError();
         g.lam = c->lam;
+        g.lamdf = c->lamdf;
     }
     e = e ? e : cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {

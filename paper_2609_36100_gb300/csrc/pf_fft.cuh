@@ -144,10 +144,22 @@ struct FastDiv {
     __device__ __forceinline__ unsigned div(unsigned n) const { return d == 1 ? n : __umulhi(n, mul); }
 };
 
+// Skewed position of element i of a shared-memory line: one empty slot after
+// every 8 elements.  The first Stockham stages write with stride R (and R*Ns)
+// along a line; without the skew a warp's stores of 8- or 16-byte elements
+// fall on a few banks (16-way conflicts for a radix-8 first stage), with it
+// the radix-8 and 8x8 stages are conflict-free.
+template <bool SKEW>
+__device__ __forceinline__ int skew(int i) {
+    return SKEW ? i + (i >> 3) : i;
+}
+// line stride of n skewed elements
+__host__ __device__ __forceinline__ int skewed_len(int n) { return n + (n >> 3); }
+
 // One radix-R Stockham stage over all lines. LINE_FAST maps consecutive
 // threads to consecutive lines (strided tiles, lines are contiguous columns);
 // otherwise to consecutive butterflies of a line (contiguous x lines).
-template <int R, int SIGN, bool LINE_FAST, int NL, typename T2>
+template <int R, int SIGN, bool LINE_FAST, int NL, bool SKEW = false, typename T2>
 __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __restrict__ dst, int n, int nl, int es,
                                           int ls, int Ns, const T2* __restrict__ tw, FastDiv divm, FastDiv divN,
                                           FastDiv divl) {
@@ -171,7 +183,7 @@ __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __rest
         const T2* s = src + line * ls;
         T2 v[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = s[(j + t * m) * es];
+        for (int t = 0; t < R; ++t) v[t] = s[skew<SKEW>((j + t * m) * es)];
         const int jq = (int)divN.div((unsigned)j);
         const int k = j - jq * Ns;
         if (Ns > 1) {
@@ -186,14 +198,14 @@ __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __rest
         const int base = jq * Ns * R + k;
         T2* d = dst + line * ls;
 #pragma unroll
-        for (int t = 0; t < R; ++t) d[(base + t * Ns) * es] = v[t];
+        for (int t = 0; t < R; ++t) d[skew<SKEW>((base + t * Ns) * es)] = v[t];
     }
 }
 
 // Full transform of the lines in `a` (b is scratch).  Callers synchronise
 // before; returns the buffer holding the result (synchronised).  NL > 0 fixes
 // the line count at compile time (strided tiles of NL columns).
-template <int SIGN, bool LINE_FAST, int NL = 0, typename T2>
+template <int SIGN, bool LINE_FAST, int NL = 0, bool SKEW = false, typename T2>
 __device__ T2* fft_lines(T2* a, T2* b, const AxisPlan& p, int nl, int es, int ls, FastDiv divl = FastDiv(1, 0)) {
     const T2* tw = twiddles<T2>(p);
     T2* src = a;
@@ -203,11 +215,11 @@ __device__ T2* fft_lines(T2* a, T2* b, const AxisPlan& p, int nl, int es, int ls
         const int r = p.rad[s];
         const FastDiv dm((unsigned)(p.n / r), p.mulm[s]), dN((unsigned)Ns, p.mulN[s]);
         switch (r) {
-            case 2: fft_stage<2, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
-            case 3: fft_stage<3, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
-            case 4: fft_stage<4, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
-            case 5: fft_stage<5, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
-            default: fft_stage<8, SIGN, LINE_FAST, NL>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            case 2: fft_stage<2, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            case 3: fft_stage<3, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            case 4: fft_stage<4, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            case 5: fft_stage<5, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            default: fft_stage<8, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
         }
         __syncthreads();
         T2* t = src;
@@ -267,10 +279,41 @@ __device__ __forceinline__ void col_stage(int n, int Ns, FastDiv dN, const T2* _
     }
 }
 
-template <int SIGN, int TX, bool IN_PLACE = false, typename T2, class Src, class Dst>
+//
+// PRELOAD: every element is first formed by src into P by a plain loop over
+// the tile (one src inlined, its loads all independent and in flight
+// together), and the stages then run from shared memory.  For heavy
+// prologues (stage assembly from many global arrays) this keeps the memory
+// parallelism and the register count of the transform independent of the
+// prologue.
+template <int SIGN, int TX, bool IN_PLACE = false, bool PRELOAD = false, typename T2, class Src, class Dst>
 __device__ void fft_cols(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
     const T2* tw = twiddles<T2>(p);
     const int n = p.n;
+    if constexpr (PRELOAD) {
+        for (int e = threadIdx.x; e < TX * n; e += blockDim.x) P[e] = src(e / TX, e & (TX - 1));
+        __syncthreads();
+        auto none = [](int, int) -> T2 { return T2{}; };
+        const T2* in = P;
+        T2* out = Q;
+        int Ns = 1;
+        for (int s = 0; s < p.nst; ++s) {
+            const bool last = (s == p.nst - 1);
+            const FastDiv dN((unsigned)Ns, p.mulN[s]);
+            switch (p.rad[s]) {
+                case 2: col_stage<2, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
+                case 3: col_stage<3, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
+                case 4: col_stage<4, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
+                case 5: col_stage<5, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
+                default: col_stage<8, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
+            }
+            if (!last) __syncthreads();
+            in = out;
+            out = (out == P) ? Q : P;
+            Ns *= p.rad[s];
+        }
+        return;
+    }
     if (p.nst == 1 && IN_PLACE) {
         // single stage reading and writing the same global columns: stage
         // into P, then store

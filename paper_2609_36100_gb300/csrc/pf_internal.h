@@ -33,10 +33,13 @@ struct Geo {
     int nx, ny, nz, nxh;
     long long NK;  // nz * ny * nxh  (complex entries per field)
     long long N;   // nz * ny * nx   (real entries per field)
+    double invN;   // 1/N, and its FP32 rounding (no per-thread FP64 divide)
+    float invN32;
     const double* kx;  // [nxh]
     const double* ky;  // [ny]
     const double* kz;  // [nz]
     const double* lam;  // [4][NK] lambda(k) per field (FP64), or null (computed on the fly)
+    const float2* lamdf;  // [4][NK] lambda(k) as double-float {h, l} (FP32-bulk contexts)
     const float* kx32;  // FP32 copies of the wave-number tables (FP32-bulk kernels)
     const float* ky32;
     const float* kz32;
@@ -45,6 +48,23 @@ struct Geo {
     const int* active;         // batch member flag: kernels return at once when *active == 0
     int tx_y, tx_z, tx_el;  // tuned tile widths (kx columns) of the strided passes, 0 = heuristic
     int rp;                  // tuned row pairs per CTA in the x passes, 0 = heuristic
+};
+
+// Model constants of the real-space and elastic terms in one compute type,
+// rounded once on the host: a kernel reads them from its parameter space and
+// never converts or divides in FP64 per thread (the FP64 pipe of this GPU is
+// narrow enough for a few dozen conversions per thread to show up).
+template <typename T>
+struct PhysT {
+    T Bv, Bm, inv2Av, inv2Am, A0m, A0v, Am, Av;
+    T wb2;    // 2 omega_bar
+    T ie;     // 1 / pair_eps
+    T twoAm;  // 2 A^m
+    T w[3][3];
+    T C44, Cm, Ca;
+    T sig[3][6];
+    T cvq[3][3];
+    T mN, lN;  // -M / N, -L / N (explicit-term scalings after a forward transform)
 };
 
 // Derived model constants (Sec. 4.1 with the readings of the library).
@@ -62,6 +82,8 @@ struct Phys {
     double Caniso, Cmix, C44;  // C11 - C12 - 2 C44, C12 + C44, C44
     double sig[3][6];     // sigma*_v = C : eps*_v (Voigt)
     double cvq[3][3];     // eps*_v : C : eps*_q
+    PhysT<double> t64;    // the constants above in each compute type
+    PhysT<float> t32;
 };
 
 // Device-resident coefficients of one stage (or step completion) pass, written
@@ -70,6 +92,8 @@ struct StageCoefDev {
     double cI[kMaxStages], cE[kMaxStages];
     double gamma, qgamma;
     float cEh[kMaxStages], cEl[kMaxStages];
+    float cIh[kMaxStages], cIl[kMaxStages];
+    float gh, gl, qgh, qgl;
 };
 
 // Coefficients of one stage assembly / step completion pass.
@@ -78,14 +102,19 @@ struct StageTerms {
     unsigned mI, mE;                   // bit j set: cI[j] / cE[j] nonzero (integer tests keep
                                        // the per-element branches off the FP64 pipe)
     int has_gamma;                     // gamma != 0
-    const double2* z[kMaxStages];      // stage vectors z_j (FP64)
+    const double2* z[kMaxStages];      // stage vectors z_j: FP64, or in the FP32-bulk form
+                                       // double-float float4 {Re h, Im h, Re l, Im l}
     const void* f[kMaxStages];         // f^E_j (compute type)
     double cI[kMaxStages];             // dt * A^I_ij (or dt * b^I_j)
     double cE[kMaxStages];             // dt * A^E_ij (or dt * b^E_j)
     float cEh[kMaxStages], cEl[kMaxStages];  // cE = cEh + cEl (double-single split, FP32-bulk terms)
+    float cIh[kMaxStages], cIl[kMaxStages];  // cI = cIh + cIl
+    unsigned mY;                       // bit j set: z_j is y itself (explicit first stage)
     double gamma;                      // dt * A^I_ii (0: explicit stage)
+    float gh, gl, qgh, qgl;            // gamma and qgamma, double-float split
     const double* qin;                 // table of 1/(1 - gamma lambda) for this gamma, or null
-    double* qout;                      // if set: write 1/(1 - qgamma lambda) (once per step)
+    double* qout;                      // if set: write 1/(1 - qgamma lambda) (once per step);
+                                       // FP32-bulk form: float2 {h, l} entries
     double qgamma;
     const StageCoefDev* dc;            // if set: cI, cE, cEh, cEl, gamma, qgamma come from here
 };
@@ -140,7 +169,7 @@ void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageT
 void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, int fe_is_f32,
                             double2* zout, cudaStream_t s);
 void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s);
-void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, cudaStream_t s);
+void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamdf, cudaStream_t s);
 // batch round: coefficients from the member's step, controller, accepted-state copy
 void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef, cudaStream_t s);
 void launch_batch_ctl(const BatchConst& bc, MemberCtl* ctl, const double* wrms_sum, double scale, cudaStream_t s);

@@ -1,0 +1,271 @@
+// Pointwise and single-thread kernels: stage assembly without a transform,
+// the diagonal implicit solve, lambda tables, the batch controller kernels,
+// the deterministic reduction and the k-space free-energy sum.
+#include "pf_common.cuh"
+
+namespace pf {
+// ---------------------------------------------------------------------------
+// pointwise kernels (FP64)
+// ---------------------------------------------------------------------------
+__global__ void k_stage_pointwise(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st, int fe32,
+                                  double2* __restrict__ zout) {
+    PF_SKIP_INACTIVE(g);
+    const long long total = 4LL * g.NK;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(gi / g.NK);
+        const long long r = gi % g.NK;
+        const int kx = (int)(r % g.nxh);
+        const int ky = (int)((r / g.nxh) % g.ny);
+        const int kz = (int)(r / ((long long)g.nxh * g.ny));
+        const double lam = lam_at(g, ph, f, gi, g.kx[kx], g.ky[ky], g.kz[kz]);
+        double2 v = y[gi];
+#pragma unroll
+        for (int j = 0; j < kMaxStages; ++j) {
+            if (j < st.n) {
+                if ((st.mI >> j) & 1u) axpy(v, cI_of(st, j) * lam, st.z[j][gi]);
+                if ((st.mE >> j) & 1u)
+                    axpy(v, cE_of(st, j), fe32 ? load_f<float2>(st.f[j], gi) : load_f<double2>(st.f[j], gi));
+            }
+        }
+        if (st.has_gamma) {
+            const double q = st.qin ? st.qin[gi] : 1.0 / (1.0 - gamma_of(st) * lam);
+            v.x *= q;
+            v.y *= q;
+        }
+        zout[gi] = v;
+    }
+}
+
+// FP32-bulk form: the double-float stage value of the z pass, without the
+// transform (stages whose f^E no later stage or completion reads)
+__global__ void k_stage_pointwise_df(Geo g, const double2* __restrict__ y, StageTerms st, float4* __restrict__ zout) {
+    PF_SKIP_INACTIVE(g);
+    const long long total = 4LL * g.NK;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x)
+        stage_value_df(g, st, y, gi, zout);
+}
+
+void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, int fe_is_f32,
+                            double2* zout, cudaStream_t s) {
+    if (fe_is_f32)
+        k_stage_pointwise_df<<<152 * 8, 256, 0, s>>>(g, y, st, reinterpret_cast<float4*>(zout));
+    else
+        k_stage_pointwise<<<152 * 8, 256, 0, s>>>(g, ph, y, st, 0, zout);
+}
+
+__global__ void k_solve(Geo g, Phys ph, double gamma, const double2* r, double2* z) {
+    const long long total = 4LL * g.NK;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(gi / g.NK);
+        const long long q = gi % g.NK;
+        const int kx = (int)(q % g.nxh);
+        const int ky = (int)((q / g.nxh) % g.ny);
+        const int kz = (int)(q / ((long long)g.nxh * g.ny));
+        const double den = 1.0 - gamma * lambda_k(ph, f, g.kx[kx], g.ky[ky], g.kz[kz]);
+        const double2 v = r[gi];
+        z[gi] = make_double2(v.x / den, v.y / den);
+    }
+}
+
+void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s) {
+    k_solve<<<152 * 8, 256, 0, s>>>(g, ph, gamma, r, z);
+}
+
+__global__ void k_lambda_table(Geo g, Phys ph, double* __restrict__ lam, float2* __restrict__ lamdf) {
+    const long long total = 4LL * g.NK;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(gi / g.NK);
+        const long long q = gi % g.NK;
+        const int kx = (int)(q % g.nxh);
+        const int ky = (int)((q / g.nxh) % g.ny);
+        const int kz = (int)(q / ((long long)g.nxh * g.ny));
+        const double l = lambda_k(ph, f, g.kx[kx], g.ky[ky], g.kz[kz]);
+        lam[gi] = l;
+        if (lamdf) {
+            const float h = (float)l;
+            lamdf[gi] = make_float2(h, (float)(l - (double)h));
+        }
+    }
+}
+
+void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamdf, cudaStream_t s) {
+    k_lambda_table<<<152 * 8, 256, 0, s>>>(g, ph, lam, lamdf);
+}
+
+// ---------------------------------------------------------------------------
+// batch round kernels (one thread each, or a grid-stride copy)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fill_coef(StageCoefDev& c, int n, const double* aI, const double* aE, double dt,
+                                          double gam, double qgam) {
+    for (int j = 0; j < kMaxStages; ++j) {
+        const double ci = j < n ? dt * aI[j] : 0.0;
+        const double ce = j < n ? dt * aE[j] : 0.0;
+        c.cI[j] = ci;
+        c.cE[j] = ce;
+        const float h = (float)ce;
+        c.cEh[j] = h;
+        c.cEl[j] = (float)(ce - (double)h);
+        const float hi = (float)ci;
+        c.cIh[j] = hi;
+        c.cIl[j] = (float)(ci - (double)hi);
+    }
+    c.gamma = gam;
+    c.qgamma = qgam;
+    c.gh = (float)gam;
+    c.gl = (float)(gam - (double)c.gh);
+    c.qgh = (float)qgam;
+    c.qgl = (float)(qgam - (double)c.qgh);
+}
+
+// step size of this round's attempt (clipped to t_final) and the stage /
+// completion coefficients built from it, as the host driver builds them
+__global__ void k_batch_prep(BatchConst bc, MemberCtl* __restrict__ ctl, StageCoefDev* __restrict__ coef) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    MemberCtl& m = *ctl;
+    if (!m.active) return;
+    const double dt = fmin(m.h, bc.t_final - m.t);
+    m.dt = dt;
+    for (int i = 0; i < bc.s; ++i)
+        fill_coef(coef[i], i, bc.AI[i], bc.AE[i], dt, dt * bc.AI[i][i], dt * bc.gdiag);
+    double dI[kMaxStages], dE[kMaxStages];
+    for (int j = 0; j < kMaxStages; ++j) {
+        dI[j] = bc.embedded ? bc.bI[j] - bc.btI[j] : 0.0;
+        dE[j] = bc.embedded ? bc.bE[j] - bc.btE[j] : 0.0;
+    }
+    fill_coef(coef[bc.s], bc.s, bc.bI, bc.bE, dt, 0.0, 0.0);
+    fill_coef(coef[bc.s + 1], bc.s, dI, dE, dt, 0.0, 0.0);
+}
+
+// accept / reject and the next step size (same PI rule as the host driver)
+__global__ void k_batch_ctl(BatchConst bc, MemberCtl* __restrict__ ctl, const double* __restrict__ wsum, double scale) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    MemberCtl& m = *ctl;
+    m.accepted_now = 0;
+    if (!m.active) return;
+    const double e = bc.embedded ? sqrt(wsum[0] * scale) : 0.0;
+    m.e_last = e;
+    m.n_rhs += bc.nrhs;
+    const bool ok = isfinite(e) && e <= 1.0;
+    const double h = m.dt;
+    double hn;
+    if (ok) {
+        m.t += h;
+        m.n_acc += 1;
+        m.nrej = 0;
+        m.accepted_now = 1;
+        if (bc.embedded) {
+            const double ee = e < 1e-10 ? 1e-10 : e;
+            double eta = bc.safety * pow(ee, -bc.k1 / bc.q) * pow(m.e_prev, bc.k2 / bc.q);
+            const double cap = m.after_reject ? 1.0 : bc.eta_max;
+            eta = fmin(cap, fmax(bc.eta_min, eta));
+            m.e_prev = ee;
+            m.after_reject = 0;
+            hn = h * eta;
+        } else {
+            hn = bc.h0;
+        }
+    } else {
+        m.n_rej += 1;
+        if (++m.nrej > bc.max_rejects) {
+            m.status = isfinite(e) ? -5 : -4;  // PF_ESTEPFAIL / PF_ENONFINITE
+            m.active = 0;
+            return;
+        }
+        m.after_reject = 1;
+        hn = isfinite(e) ? h * fmax(bc.eta_rej, bc.safety * pow(e, -1.0 / bc.q)) : h * 0.25;
+    }
+    m.h = fmin(fmax(hn, bc.h_min), bc.h_max);
+    if (!(m.t < bc.t_final * (1 - 1e-14))) m.active = 0;
+}
+
+// y <- y_new for an accepted attempt
+__global__ void k_batch_accept(Geo g, const MemberCtl* __restrict__ ctl, const double2* __restrict__ ynew,
+                               double2* __restrict__ y) {
+    if (!ctl->accepted_now) return;
+    const long long total = 4LL * g.NK;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = ynew[i];
+}
+
+void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef, cudaStream_t s) {
+    k_batch_prep<<<1, 32, 0, s>>>(bc, ctl, coef);
+}
+void launch_batch_ctl(const BatchConst& bc, MemberCtl* ctl, const double* wrms_sum, double scale, cudaStream_t s) {
+    k_batch_ctl<<<1, 32, 0, s>>>(bc, ctl, wrms_sum, scale);
+}
+void launch_batch_accept(const Geo& g, const MemberCtl* ctl, const double2* ynew, double2* y, cudaStream_t s) {
+    k_batch_accept<<<152 * 4, 256, 0, s>>>(g, ctl, ynew, y);
+}
+
+// deterministic single-CTA reduction: out = sum(partials) * scale (FP64)
+__global__ void k_reduce(const double* __restrict__ p, int n, double scale, double* out) {
+    __shared__ double sh[1024];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a += p[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0] * scale;
+}
+
+void launch_reduce(const double* partials, int n, double scale, double* out, cudaStream_t s) {
+    k_reduce<<<1, 1024, 0, s>>>(partials, n, scale, out);
+}
+
+// k-space part of the free energy: sum_k w_k [ sum_v k.kappa_v.k |phi^_v|^2
+//                                              + sum_vq B_vq Re(h^_v conj h^_q) ]
+__global__ void k_energy_k(Geo g, Phys ph, const double2* __restrict__ y, const double2* __restrict__ hk,
+                           double* partials) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.NK;
+         r += (long long)gridDim.x * blockDim.x) {
+        const int kx = (int)(r % g.nxh);
+        const int ky = (int)((r / g.nxh) % g.ny);
+        const int kz = (int)(r / ((long long)g.nxh * g.ny));
+        const double w = (kx == 0 || (g.nx % 2 == 0 && kx == g.nx / 2)) ? 1.0 : 2.0;
+        const double KX = g.kx[kx], KY = g.ky[ky], KZ = g.kz[kz];
+        double s = 0.0;
+        for (int v = 0; v < 3; ++v) {
+            const double lam = lambda_k(ph, v + 1, KX, KY, KZ);  // -L k.kappa.k
+            const double2 a = y[(long long)(v + 1) * g.NK + r];
+            s += (-lam / ph.L) * (a.x * a.x + a.y * a.y);
+        }
+        if (ph.elastic) {
+            double Bm[3][3];
+            const PhysT<double>& pt = ph.t64;
+            elastic_kernel<double>(pt, KX, KY, KZ, Bm);
+            double2 h[3];
+            for (int v = 0; v < 3; ++v) h[v] = hk[(long long)v * g.NK + r];
+            for (int v = 0; v < 3; ++v)
+                for (int q = 0; q < 3; ++q) s += Bm[v][q] * (h[v].x * h[q].x + h[v].y * h[q].y);
+        }
+        acc += w * s;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        partials[blockIdx.x] = t;
+    }
+}
+
+int energy_k_blocks(const Geo& g) { return 152 * 4; }
+
+void launch_energy_k(const Geo& g, const Phys& ph, const double2* y, const double2* hk, double* partials,
+                     cudaStream_t s) {
+    k_energy_k<<<energy_k_blocks(g), 256, 0, s>>>(g, ph, y, hk, partials);
+}
+
+
+}  // namespace pf

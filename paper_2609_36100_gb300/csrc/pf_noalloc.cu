@@ -126,6 +126,8 @@ int pf_state_to_real_noalloc(const pf_grid* grid, const void* y_hat, double* fie
     g.nxh = g.nx / 2 + 1;
     g.NK = NK;
     g.N = (long long)g.nz * g.ny * g.nx;
+    g.invN = 1.0 / (double)g.N;
+    g.invN32 = (float)g.invN;
     g.mul_nx = magic_u32((unsigned)g.nx);
     g.mul_nxh = magic_u32((unsigned)g.nxh);
     AxisPlan* plans[3] = {&g.px, &g.py, &g.pz};

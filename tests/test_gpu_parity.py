@@ -190,3 +190,24 @@ def test_fp32bulk_state_error_after_steps(pfg, params):
     assert got[0, 0, 0, 0] == dc  # composition mean stays FP64-exact
     err = relerr(got, yh)
     assert np.all(err <= 1e-5), err
+
+
+def test_fp32bulk_keeps_increments_below_fp32_resolution(pfg, params):
+    """The FP32-bulk form keeps the state and the stage combination at
+    (close to) FP64 precision: over many tiny steps whose increments are far
+    below one FP32 ulp of the state, its accumulated change matches the FP64
+    path's to FP32-relative accuracy of the increment itself.  A state or a
+    combination carried in FP32 would drop these increments entirely."""
+    y0 = synth.ic_spheres(32, 3, 3.0, 5.0, 9, params)
+    d = {}
+    for prec in ("fp64", "fp32bulk"):
+        with pfg.Simulation(y0.shape[1:], params, "ark4", prec) as s:
+            s.set_state(y0)
+            h0 = to_np(s.state_hat())
+            for _ in range(40):
+                s.step(2e-9)
+            d[prec] = to_np(s.state_hat()) - h0
+    scale = np.linalg.norm(h0)
+    n64 = np.linalg.norm(d["fp64"])
+    assert 0 < n64 < 1e-8 * scale  # far below FP32 resolution of the state
+    assert np.linalg.norm(d["fp32bulk"] - d["fp64"]) <= 1e-4 * n64
