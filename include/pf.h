@@ -188,7 +188,7 @@ const char* pf_kernel_name(int kind);
 
 /* Launch schedule of a context: tuned tile widths of the z / y / elastic
  * passes, rows per CTA of the x passes (0 = built-in heuristic), and the
- * radix order of each axis (count + up to 10 radices in {2,3,4,5,8}, for x,
+ * radix order of each axis (count + up to 10 radices in {2,3,4,5,8,16}, for x,
  * y, z).  PF_TUNE_LEN ints. */
 #define PF_TUNE_LEN 37
 int pf_get_tuning(pf_ctx* ctx, int* cfg, int n);

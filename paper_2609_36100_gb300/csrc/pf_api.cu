@@ -690,7 +690,7 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     AxisPlan* plans[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
-        if (!make_axis_plan(ns[a], *plans[a])) {
+        if (!make_axis_plan(ns[a], *plans[a], c->fp32)) {
             delete c;
             return fail(nullptr, PF_EUNSUPPORTED, "cannot factor %d", ns[a]);
         }
@@ -1223,26 +1223,32 @@ std::vector<std::vector<int>> radix_orders(int n, size_t cap) {
     while (m % 3 == 0) { m /= 3; ++b; }
     while (m % 5 == 0) { m /= 5; ++cc; }
     std::vector<std::vector<int>> sets;
-    // power-of-two parts: k8 eights, k4 fours, k2 twos with 3 k8 + 2 k4 + k2 = a
+    // power-of-two parts: k16 sixteens, k8 eights, k4 fours, k2 twos with
+    // 4 k16 + 3 k8 + 2 k4 + k2 = a
     int best = 1 << 30;
     std::vector<std::vector<int>> twos;
-    for (int k8 = 0; 3 * k8 <= a; ++k8)
-        for (int k4 = 0; 3 * k8 + 2 * k4 <= a; ++k4) {
-            const int k2 = a - 3 * k8 - 2 * k4;
-            if (k2 > 1) continue;
-            std::vector<int> v;
-            for (int i = 0; i < k8; ++i) v.push_back(8);
-            for (int i = 0; i < k4; ++i) v.push_back(4);
-            for (int i = 0; i < k2; ++i) v.push_back(2);
-            twos.push_back(v);
-            if ((int)v.size() < best) best = (int)v.size();
-        }
+    for (int k16 = 0; 4 * k16 <= a; ++k16)
+        for (int k8 = 0; 4 * k16 + 3 * k8 <= a; ++k8)
+            for (int k4 = 0; 4 * k16 + 3 * k8 + 2 * k4 <= a; ++k4) {
+                const int k2 = a - 4 * k16 - 3 * k8 - 2 * k4;
+                if (k2 > 1) continue;
+                std::vector<int> v;
+                for (int i = 0; i < k16; ++i) v.push_back(16);
+                for (int i = 0; i < k8; ++i) v.push_back(8);
+                for (int i = 0; i < k4; ++i) v.push_back(4);
+                for (int i = 0; i < k2; ++i) v.push_back(2);
+                twos.push_back(v);
+                if ((int)v.size() < best) best = (int)v.size();
+            }
     for (auto& v : twos) {
         if ((int)v.size() > best + 1) continue;
         for (int i = 0; i < b; ++i) v.push_back(3);
         for (int i = 0; i < cc; ++i) v.push_back(5);
         sets.push_back(v);
     }
+    // fewest stages first, so that the cap keeps them
+    std::stable_sort(sets.begin(), sets.end(),
+                     [](const std::vector<int>& x, const std::vector<int>& y) { return x.size() < y.size(); });
     std::vector<std::vector<int>> out;
     for (auto v : sets) {
         std::sort(v.begin(), v.end());

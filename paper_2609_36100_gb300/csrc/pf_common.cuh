@@ -268,6 +268,16 @@ static void set_smem(K kern, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// compile-time radix-16 support dispatch (R16C), from the axis plan
+#define PF_R16_SWITCH(flag, ...)       \
+    if (flag) {                        \
+        constexpr bool R16C = true;    \
+        __VA_ARGS__;                   \
+    } else {                           \
+        constexpr bool R16C = false;   \
+        __VA_ARGS__;                   \
+    }
+
 // compile-time tile width dispatch
 #define PF_TX_SWITCH(tx, ...)                 \
     switch (tx) {                             \

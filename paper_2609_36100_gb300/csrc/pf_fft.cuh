@@ -1,4 +1,4 @@
-// Shared-memory mixed-radix (2,3,4,5,8) Stockham FFT used by every pass of
+// Shared-memory mixed-radix (2,3,4,5,8,16) Stockham FFT used by every pass of
 // the pseudospectral right-hand side.  A CTA transforms `nl` lines of length
 // n held in shared memory; element e of line l sits at l*ls + e*es.  Stages
 // ping-pong between two buffers; each butterfly reads R inputs strided by n/R,
@@ -46,6 +46,8 @@ __device__ __forceinline__ T2 cscale(T2 a, S s) { return T2{a.x * s, a.y * s}; }
 #define PF_S2_5 0.5877852522924731
 #define PF_S3 0.8660254037844386
 #define PF_R2 0.7071067811865476
+#define PF_C16 0.9238795325112867  // cos(pi/8)
+#define PF_S16 0.3826834323650898  // sin(pi/8)
 
 template <int R, int SIGN, typename T2>
 struct Bfly;
@@ -128,6 +130,42 @@ struct Bfly<8, SIGN, T2> {
     }
 };
 
+// 16 = 4 x 4: radix-4 DFTs over the stride-4 subsequences, twiddles
+// w16^(n2 k1), radix-4 DFTs across them; w16 = exp(SIGN 2 pi i / 16)
+template <int SIGN, typename T2>
+struct Bfly<16, SIGN, T2> {
+    __device__ __forceinline__ static T2 w16(T2 a, int m) {
+        using T = decltype(a.x);
+        const T c = (T)PF_C16, s = (T)PF_S16, r = (T)PF_R2;
+        switch (m) {
+            case 1: return cmul(a, T2{c, SIGN * s});
+            case 2: return cmul(a, T2{r, SIGN * r});
+            case 3: return cmul(a, T2{s, SIGN * c});
+            case 4: return mul_si<SIGN>(a);
+            case 6: return cmul(a, T2{-r, SIGN * r});
+            case 9: return cmul(a, T2{-c, -SIGN * s});
+            default: return a;
+        }
+    }
+    __device__ __forceinline__ static void run(T2* v) {
+        T2 A[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            T2 q[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+            Bfly<4, SIGN, T2>::run(q);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) A[n2][k1] = w16(q[k1], n2 * k1);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            T2 q[4] = {A[0][k1], A[1][k1], A[2][k1], A[3][k1]};
+            Bfly<4, SIGN, T2>::run(q);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = q[k2];
+        }
+    }
+};
+
 template <typename T2>
 __device__ __forceinline__ const T2* twiddles(const AxisPlan& p);
 template <>
@@ -145,16 +183,18 @@ struct FastDiv {
 };
 
 // Skewed position of element i of a shared-memory line: one empty slot after
-// every 8 elements.  The first Stockham stages write with stride R (and R*Ns)
+// every 16 elements.  The first Stockham stages write with stride R (and R*Ns)
 // along a line; without the skew a warp's stores of 8- or 16-byte elements
-// fall on a few banks (16-way conflicts for a radix-8 first stage), with it
-// the radix-8 and 8x8 stages are conflict-free.
+// fall on a few banks (16-way conflicts for a radix-8 first stage), with it a
+// radix-16 first stage is conflict-free and the (8, 8, 4) and (8, 4, 5) plans
+// lose most of theirs (modelled over n = 64..256: 1.2x the conflict-free
+// wavefront count for 8-byte elements, 1.03x for 16-byte ones).
 template <bool SKEW>
 __device__ __forceinline__ int skew(int i) {
-    return SKEW ? i + (i >> 3) : i;
+    return SKEW ? i + (i >> 4) : i;
 }
 // line stride of n skewed elements
-__host__ __device__ __forceinline__ int skewed_len(int n) { return n + (n >> 3); }
+__host__ __device__ __forceinline__ int skewed_len(int n) { return n + (n >> 4); }
 
 // One radix-R Stockham stage over all lines. LINE_FAST maps consecutive
 // threads to consecutive lines (strided tiles, lines are contiguous columns);
@@ -202,10 +242,12 @@ __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __rest
     }
 }
 
-// Full transform of the lines in `a` (b is scratch).  Callers synchronise
+// Full transform of the lines in `a` (b is scratch).  Radix-16 stages are
+// compiled in only with R16 (they raise the register count of the whole
+// kernel); the launcher picks R16 from the plan (AxisPlan::has16).  Callers synchronise
 // before; returns the buffer holding the result (synchronised).  NL > 0 fixes
 // the line count at compile time (strided tiles of NL columns).
-template <int SIGN, bool LINE_FAST, int NL = 0, bool SKEW = false, typename T2>
+template <int SIGN, bool LINE_FAST, int NL = 0, bool SKEW = false, bool R16 = false, typename T2>
 __device__ T2* fft_lines(T2* a, T2* b, const AxisPlan& p, int nl, int es, int ls, FastDiv divl = FastDiv(1, 0)) {
     const T2* tw = twiddles<T2>(p);
     T2* src = a;
@@ -219,6 +261,9 @@ __device__ T2* fft_lines(T2* a, T2* b, const AxisPlan& p, int nl, int es, int ls
             case 3: fft_stage<3, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
             case 4: fft_stage<4, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
             case 5: fft_stage<5, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
+            case 16:
+                if constexpr (R16) fft_stage<16, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl);
+                break;
             default: fft_stage<8, SIGN, LINE_FAST, NL, SKEW>(src, dst, p.n, nl, es, ls, Ns, tw, dm, dN, divl); break;
         }
         __syncthreads();
@@ -286,7 +331,8 @@ __device__ __forceinline__ void col_stage(int n, int Ns, FastDiv dN, const T2* _
 // prologues (stage assembly from many global arrays) this keeps the memory
 // parallelism and the register count of the transform independent of the
 // prologue.
-template <int SIGN, int TX, bool IN_PLACE = false, bool PRELOAD = false, typename T2, class Src, class Dst>
+template <int SIGN, int TX, bool IN_PLACE = false, bool PRELOAD = false, bool R16 = false, typename T2, class Src,
+          class Dst>
 __device__ void fft_cols(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
     const T2* tw = twiddles<T2>(p);
     const int n = p.n;
@@ -305,6 +351,9 @@ __device__ void fft_cols(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
                 case 3: col_stage<3, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
                 case 4: col_stage<4, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
                 case 5: col_stage<5, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
+                case 16:
+                    if constexpr (R16) col_stage<16, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst);
+                    break;
                 default: col_stage<8, SIGN, TX>(n, Ns, dN, in, out, false, last, tw, none, dst); break;
             }
             if (!last) __syncthreads();
@@ -324,6 +373,9 @@ __device__ void fft_cols(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
             case 3: col_stage<3, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
             case 4: col_stage<4, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
             case 5: col_stage<5, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
+            case 16:
+                if constexpr (R16) col_stage<16, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP);
+                break;
             default: col_stage<8, SIGN, TX>(n, 1, dN, P, P, true, true, tw, src, toP); break;
         }
         __syncthreads();
@@ -341,6 +393,9 @@ __device__ void fft_cols(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
             case 3: col_stage<3, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
             case 4: col_stage<4, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
             case 5: col_stage<5, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
+            case 16:
+                if constexpr (R16) col_stage<16, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst);
+                break;
             default: col_stage<8, SIGN, TX>(n, Ns, dN, in, out, first, last, tw, src, dst); break;
         }
         if (!last) __syncthreads();

@@ -15,6 +15,7 @@ struct AxisPlan {
     int n;
     int nst;
     int rad[kMaxRadices];
+    int has16;                   // some stage is radix-16 (kernels compiled with radix-16 support)
     unsigned mulm[kMaxRadices];  // division magic for n / rad[s]
     unsigned mulN[kMaxRadices];  // division magic for the stage's Ns
     const double2* tw64;
@@ -24,7 +25,7 @@ struct AxisPlan {
 // ceil(2^32 / d) for d >= 2 (0 for d = 1, which FastDiv special-cases)
 inline unsigned magic_u32(unsigned d) { return d <= 1 ? 0u : (unsigned)((0xffffffffull + d) / d); }
 // radix schedule (8s first, then 4/2, 3s, 5s) and division magic of one axis
-bool make_axis_plan(int n, AxisPlan& p);
+bool make_axis_plan(int n, AxisPlan& p, bool prefer16 = false);
 bool make_axis_plan_radices(int n, const int* rad, int nr, AxisPlan& p);
 
 // Grid geometry and the per-axis wave-number tables k_m = 2 pi m / (n d)

@@ -100,7 +100,7 @@ __device__ __forceinline__ void r2c_store(const Geo& g, const T2* S, int ls, int
     }
 }
 
-template <typename T>
+template <typename T, bool R16>
 __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, const typename Cx<T>::t* __restrict__ in,
                                                      typename Cx<T>::t* __restrict__ out, T* __restrict__ R,
                                                      const T* __restrict__ Rin, double* __restrict__ partials,
@@ -137,14 +137,14 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
             S0[line * ls + skew<true>(x)] = Z;
         }
         __syncthreads();
-        T2* res = fft_lines<-1, false, 0, true>(S0, S1, g.px, 4 * P, 1, ls);
+        T2* res = fft_lines<-1, false, 0, true, R16>(S0, S1, g.px, 4 * P, 1, ls);
         r2c_store(g, res, ls, 4, P, rp0, npairs, out);
         return;
     }
     if (Fin > 0) {
         c2r_load(g, in, Fin, P, rp0, npairs, S0, ls);
         __syncthreads();
-        RS = fft_lines<+1, false, 0, true>(S0, S1, g.px, Fin * P, 1, ls);
+        RS = fft_lines<+1, false, 0, true, R16>(S0, S1, g.px, Fin * P, 1, ls);
     }
     T2* OS = (RS == S0) ? S1 : S0;  // output lines
 
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, c
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
         partials[blockIdx.x] = s;
     }
-    T2* res = fft_lines<-1, false, 0, true>(OS, RS, g.px, Fout * P, 1, ls);
+    T2* res = fft_lines<-1, false, 0, true, R16>(OS, RS, g.px, Fout * P, 1, ls);
     r2c_store(g, res, ls, Fout, P, rp0, npairs, out);
 }
 
@@ -321,17 +321,20 @@ static int x_rows(const Geo& g) {
     return P;
 }
 
-// plan from an explicit radix order (each radix in {2,3,4,5,8}, product n)
+// plan from an explicit radix order (each radix in {2,3,4,5,8,16}, product n)
 bool make_axis_plan_radices(int n, const int* rad, int nr, AxisPlan& p) {
     if (nr < 1 || nr > kMaxRadices) return false;
     long long prod = 1;
     for (int s = 0; s < nr; ++s) {
-        if (rad[s] != 2 && rad[s] != 3 && rad[s] != 4 && rad[s] != 5 && rad[s] != 8) return false;
+        if (rad[s] != 2 && rad[s] != 3 && rad[s] != 4 && rad[s] != 5 && rad[s] != 8 && rad[s] != 16) return false;
         prod *= rad[s];
     }
     if (prod != n) return false;
     p.n = n;
     p.nst = nr;
+    p.has16 = 0;
+    for (int s = 0; s < nr; ++s)
+        if (rad[s] == 16) p.has16 = 1;
     unsigned Ns = 1;
     for (int s = 0; s < nr; ++s) {
         p.rad[s] = rad[s];
@@ -342,9 +345,10 @@ bool make_axis_plan_radices(int n, const int* rad, int nr, AxisPlan& p) {
     return true;
 }
 
-// default schedule: radix-8 stages first, then a 4 (or 4*4 instead of 8*2)
-// or 2, then the 3s and 5s
-bool make_axis_plan(int n, AxisPlan& p) {
+// default schedule: the fewest stages, largest radices first -- radix-16
+// stages (prefer16) or radix-8 ones, then a 8 / 4 (or 4*4 instead of 8*2,
+// 8*4 instead of 16*2) or 2, then the 3s and 5s
+bool make_axis_plan(int n, AxisPlan& p, bool prefer16) {
     int m = n, a = 0, b = 0, c = 0;
     while (m % 2 == 0) { m /= 2; ++a; }
     while (m % 3 == 0) { m /= 3; ++b; }
@@ -352,24 +356,45 @@ bool make_axis_plan(int n, AxisPlan& p) {
     if (m != 1) return false;
     int r[kMaxRadices + 8];
     int nr = 0;
-    int n8 = a / 3;
-    const int rem = a % 3;
-    bool two4 = false;
-    if (rem == 1 && n8 > 0) {
-        --n8;
-        two4 = true;
-    }
-    for (int i = 0; i < n8; ++i) r[nr++] = 8;
-    if (two4) {
-        r[nr++] = 4;
-        r[nr++] = 4;
-    } else if (rem == 2) {
-        r[nr++] = 4;
-    } else if (rem == 1) {
-        r[nr++] = 2;
+    if (prefer16) {
+        int n16 = a / 4;
+        int rem = a % 4;
+        if (rem == 1 && n16 > 0) {
+            --n16;
+            rem = 5;
+        }
+        for (int i = 0; i < n16; ++i) r[nr++] = 16;
+        if (rem == 5) {
+            r[nr++] = 8;
+            r[nr++] = 4;
+        } else if (rem == 3) {
+            r[nr++] = 8;
+        } else if (rem == 2) {
+            r[nr++] = 4;
+        } else if (rem == 1) {
+            r[nr++] = 2;
+        }
+    } else {
+        int n8 = a / 3;
+        const int rem = a % 3;
+        bool two4 = false;
+        if (rem == 1 && n8 > 0) {
+            --n8;
+            two4 = true;
+        }
+        for (int i = 0; i < n8; ++i) r[nr++] = 8;
+        if (two4) {
+            r[nr++] = 4;
+            r[nr++] = 4;
+        } else if (rem == 2) {
+            r[nr++] = 4;
+        } else if (rem == 1) {
+            r[nr++] = 2;
+        }
     }
     for (int i = 0; i < b; ++i) r[nr++] = 3;
     for (int i = 0; i < c; ++i) r[nr++] = 5;
+    if (nr > kMaxRadices) return false;
     return make_axis_plan_radices(n, r, nr, p);
 }
 
@@ -386,12 +411,13 @@ void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void*
     using T2 = typename Cx<T>::t;
     const int P = x_rows<T>(g);
     const size_t sm = 2 * 4 * (size_t)P * skewed_len(g.nx) * sizeof(T2);
-    set_smem(k_x_pass<T>, sm);
     const int npairs = g.nz * g.ny / 2;
     const int nb = (npairs + P - 1) / P;
-    k_x_pass<T><<<nb, kThreads, sm, s>>>(g, ph, mode, reinterpret_cast<const T2*>(in), reinterpret_cast<T2*>(out),
-                                         reinterpret_cast<T*>(R), reinterpret_cast<const T*>(Rin), partials, rtol,
-                                         atol, real_in, real_out, P);
+    PF_R16_SWITCH(g.px.has16, set_smem(k_x_pass<T, R16C>, sm);
+                  k_x_pass<T, R16C><<<nb, kThreads, sm, s>>>(
+                      g, ph, mode, reinterpret_cast<const T2*>(in), reinterpret_cast<T2*>(out),
+                      reinterpret_cast<T*>(R), reinterpret_cast<const T*>(Rin), partials, rtol, atol, real_in,
+                      real_out, P))
 }
 
 // explicit instantiations

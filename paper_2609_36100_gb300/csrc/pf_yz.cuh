@@ -1,13 +1,14 @@
 // Strided column passes along y (inverse/forward FFT) and the spectral z
 // passes: forward FFT with the k-space scaling of f^E, and the elastic
 // Green's contraction between a forward and an inverse FFT along z.
+#pragma once
 #include "pf_common.cuh"
 
 namespace pf {
 // ---------------------------------------------------------------------------
 // y pass: in-place complex FFT along y of nf fields
 // ---------------------------------------------------------------------------
-template <typename T, int SIGN, int TX>
+template <typename T, int SIGN, int TX, bool R16>
 __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* __restrict__ buf) {
     PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* _
     auto dst = [&](int ky, int col, T2 v) {
         if (col < ncol) base[ky * ys + col] = v;
     };
-    fft_cols<SIGN, TX, true>(g.py, A, B, src, dst);
+    fft_cols<SIGN, TX, true, false, R16>(g.py, A, B, src, dst);
 }
 
 template <typename T>
@@ -32,11 +33,11 @@ void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
     const size_t sm = 2 * (size_t)TX * g.ny * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.nz, nf);
     if (sign > 0) {
-        PF_TX_SWITCH(TX, set_smem(k_y_pass<T, 1, TXC>, sm);
-                     k_y_pass<T, 1, TXC><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf)))
+        PF_R16_SWITCH(g.py.has16, PF_TX_SWITCH(TX, set_smem(k_y_pass<T, 1, TXC, R16C>, sm);
+                     k_y_pass<T, 1, TXC, R16C><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf))))
     } else {
-        PF_TX_SWITCH(TX, set_smem(k_y_pass<T, -1, TXC>, sm);
-                     k_y_pass<T, -1, TXC><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf)))
+        PF_R16_SWITCH(g.py.has16, PF_TX_SWITCH(TX, set_smem(k_y_pass<T, -1, TXC, R16C>, sm);
+                     k_y_pass<T, -1, TXC, R16C><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf))))
     }
 }
 
@@ -46,7 +47,7 @@ void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
 //   mode 1: f^E_X = -M k^2 q^/N, f^E_phi = -L g^/N -> compute type (stages)
 //   mode 2: same scaling -> FP64                                  (ABI f^E)
 // ---------------------------------------------------------------------------
-template <typename T, typename OT2, int TX>
+template <typename T, typename OT2, int TX, bool R16>
 __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typename Cx<T>::t* __restrict__ W,
                                                     OT2* __restrict__ out, int mode) {
     PF_SKIP_INACTIVE(g);
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typena
             out[gi] = OT2{(OT)(v.x * sc), (OT)(v.y * sc)};
         }
     };
-    fft_cols<-1, TX>(g.pz, A, B, src, dst);
+    fft_cols<-1, TX, false, false, R16>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
@@ -89,18 +90,18 @@ void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int sc
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
     if (scale_mode == 1) {
-        PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, T2, TXC>, sm);
-                     k_z_fwd<T, T2, TXC><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
-                                                                    reinterpret_cast<T2*>(out), 1))
+        PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, T2, TXC, R16C>, sm);
+                     k_z_fwd<T, T2, TXC, R16C><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
+                                                                          reinterpret_cast<T2*>(out), 1)))
     } else {
-        PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, double2, TXC>, sm);
-                     k_z_fwd<T, double2, TXC><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
-                                                                         reinterpret_cast<double2*>(out),
-                                                                         scale_mode))
+        PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, double2, TXC, R16C>, sm);
+                     k_z_fwd<T, double2, TXC, R16C><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
+                                                                               reinterpret_cast<double2*>(out),
+                                                                               scale_mode)))
     }
 }
 
-template <typename T, int TX>
+template <typename T, int TX, bool R16>
 __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename Cx<T>::t* __restrict__ H) {
     PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
@@ -125,9 +126,9 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
         auto src = [&](int kz, int col) -> T2 { return col < ncol ? H[fb + kz * zs + col] : T2{0, 0}; };
         auto dst = [&](int kz, int col, T2 v) { S[kz * TX + col] = v; };
         if (nst_even)
-            fft_cols<-1, TX>(g.pz, E, S, src, dst);
+            fft_cols<-1, TX, false, false, R16>(g.pz, E, S, src, dst);
         else
-            fft_cols<-1, TX>(g.pz, S, E, src, dst);
+            fft_cols<-1, TX, false, false, R16>(g.pz, S, E, src, dst);
         __syncthreads();
     }
     const T invN = std::is_same<T, float>::value ? (T)g.invN32 : (T)g.invN;
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
         auto dst = [&](int kz, int col, T2 v) {
             if (col < ncol) H[fb + kz * zs + col] = v;
         };
-        fft_cols<+1, TX>(g.pz, E, S, src, dst);
+        fft_cols<+1, TX, false, false, R16>(g.pz, E, S, src, dst);
         __syncthreads();
     }
 }
@@ -168,15 +169,8 @@ void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     const int TX = tuned_cols<T>(g, g.tx_el, g.nz, 4, 128 * 1024);
     const size_t sm = 4 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);
-    PF_TX_SWITCH(TX, set_smem(k_z_elastic<T, TXC>, sm);
-                 k_z_elastic<T, TXC><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<T2*>(H)))
+    PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_elastic<T, TXC, R16C>, sm);
+                 k_z_elastic<T, TXC, R16C><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<T2*>(H))))
 }
 
-// explicit instantiations
-template void launch_y_pass<double>(const Geo&, void*, int, int, cudaStream_t);
-template void launch_y_pass<float>(const Geo&, void*, int, int, cudaStream_t);
-template void launch_z_fwd<double>(const Geo&, const Phys&, const void*, void*, int, cudaStream_t, int);
-template void launch_z_fwd<float>(const Geo&, const Phys&, const void*, void*, int, cudaStream_t, int);
-template void launch_z_elastic<double>(const Geo&, const Phys&, void*, cudaStream_t);
-template void launch_z_elastic<float>(const Geo&, const Phys&, void*, cudaStream_t);
 }  // namespace pf
