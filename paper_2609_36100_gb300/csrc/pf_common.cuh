@@ -147,11 +147,30 @@ __device__ __forceinline__ DF df_two_sum(float a, float b) {
     return DF{h, __fadd_rn(__fsub_rn(a, __fsub_rn(h, bb)), __fsub_rn(b, bb))};
 }
 
-// FP64 -> double-float (one FP64 subtraction); double-float -> FP64 (one FP64
-// addition)
+// FP32 value of an FP64 one truncated to 24 significant bits, from its bit
+// fields (below the FP32 normal range: signed zero; above it: infinity; NaN
+// stays NaN)
+__device__ __forceinline__ float f32_trunc_bits(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned sign = hi & 0x80000000u;
+    const int fe = (int)((hi >> 20) & 0x7ffu) - 896;
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) {
+        const bool nan = fe == 2047 - 896 && ((hi & 0xfffffu) | lo) != 0u;
+        return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
+    }
+    return __uint_as_float(sign | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// FP64 -> double-float: h = d truncated to 24 significant bits (exact in both
+// types), l = d - h (one exact FP64 subtraction) truncated to FP32; h + l
+// carries at least 47 significant bits.  Bit operations only, apart from the
+// subtraction.  Double-float -> FP64: one FP64 addition.
 __device__ __forceinline__ DF df_from_d(double d) {
-    const float h = d2f_bits(d);
-    return DF{h, d2f_bits(d - f2d_bits(h))};
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const int fe = (int)((hi >> 20) & 0x7ffu) - 896;
+    const double hd = fe > 0 ? __hiloint2double((int)hi, (int)(lo & 0xe0000000u)) : 0.0;
+    return DF{f32_trunc_bits(hd), f32_trunc_bits(d - hd)};
 }
 __device__ __forceinline__ double df_to_d(DF a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 
@@ -197,8 +216,8 @@ struct DFAcc {
         df_acc(yh, yl, ch, cl, zy.h, zy.l);
     }
     __device__ __forceinline__ void add(float ch, float cl, float2 f) {
-        df_acc(xh, xl, ch, cl, f.x, 0.f);
-        df_acc(yh, yl, ch, cl, f.y, 0.f);
+        ds_add_prod(xh, xl, ch, cl, f.x);
+        ds_add_prod(yh, yl, ch, cl, f.y);
     }
     __device__ __forceinline__ DF x() const { return df_two_sum(xh, xl); }
     __device__ __forceinline__ DF y() const { return df_two_sum(yh, yl); }

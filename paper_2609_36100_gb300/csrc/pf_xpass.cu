@@ -59,7 +59,7 @@ __device__ __forceinline__ void c2r_load(const Geo& g, const T2* __restrict__ in
     // unrolled so that several iterations' loads are in flight together
 #pragma unroll 4
     for (int e = threadIdx.x; e < P * F * nx; e += blockDim.x) {
-        const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = line / F, f = line - rp * F;
+        const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = F == 4 ? line >> 2 : line / 3, f = line - rp * F;
         T2 Z = T2{0, 0};
         if (rp0 + rp < npairs) {
             const long long row = 2LL * (rp0 + rp);
@@ -86,7 +86,7 @@ __device__ __forceinline__ void r2c_store(const Geo& g, const T2* S, int ls, int
     const int nx = g.nx, nxh = g.nxh;
     const FastDiv dnh((unsigned)nxh, g.mul_nxh);
     for (int e = threadIdx.x; e < P * F * nxh; e += blockDim.x) {
-        const int line = (int)dnh.div((unsigned)e), k = e - line * nxh, rp = line / F, f = line - rp * F;
+        const int line = (int)dnh.div((unsigned)e), k = e - line * nxh, rp = F == 4 ? line >> 2 : line / 3, f = line - rp * F;
         if (rp0 + rp >= npairs) continue;
         const T2 Zk = S[line * ls + skew<true>(k)];
         const T2 Zm = S[line * ls + skew<true>(k == 0 ? 0 : nx - k)];
