@@ -101,7 +101,7 @@ __device__ __forceinline__ void r2c_store(const Geo& g, const T2* S, int ls, int
 }
 
 template <typename T, bool R16>
-__global__ void __launch_bounds__(kThreads) k_x_pass(Geo g, Phys ph, int mode, const typename Cx<T>::t* __restrict__ in,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo g, Phys ph, int mode, const typename Cx<T>::t* __restrict__ in,
                                                      typename Cx<T>::t* __restrict__ out, T* __restrict__ R,
                                                      const T* __restrict__ Rin, double* __restrict__ partials,
                                                      double rtol, double atol, const double* __restrict__ real_in,
