@@ -30,7 +30,7 @@ namespace pf {
 // The assembly is the first FFT stage's load: each element is formed once.
 // ---------------------------------------------------------------------------
 template <typename T, int TX, bool R16>
-__global__ void __launch_bounds__(kThreads) k_z_stage(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st,
                                                       double2* __restrict__ zout,
                                                       typename Cx<T>::t* __restrict__ W) {
     PF_SKIP_INACTIVE(g);
@@ -106,7 +106,7 @@ void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageT
 //   LTE = sum_i (dt (b-bt)^I_i) lambda z_i + (dt (b-bt)^E_i) f^E_i
 // ---------------------------------------------------------------------------
 template <typename T, int TX, bool R16>
-__global__ void __launch_bounds__(kThreads) k_z_final(Geo g, Phys ph, const double2* __restrict__ y, StageTerms bt,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_final(Geo g, Phys ph, const double2* __restrict__ y, StageTerms bt,
                                                       StageTerms dt, int want_lte, double2* __restrict__ ynew,
                                                       typename Cx<T>::t* __restrict__ W) {
     PF_SKIP_INACTIVE(g);
