@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 path")
     ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble measurement (0: skip)")
-    ap.add_argument("--ensemble-t", type=float, default=3.0, help="simulated seconds of the ensemble measurement")
+    ap.add_argument("--ensemble-t", type=float, default=5.0, help="simulated seconds of the ensemble measurement")
     ap.add_argument("--surrogate", type=int, default=16, help="training trajectories of the surrogate measurement (0: skip)")
     return ap.parse_args()
 
@@ -147,12 +147,13 @@ def run_ours(args, rank, world, dist):
         sim.set_state(y0)
         tuning = sim.autotune(reps=2)  # launch schedule picked by the autotuner
         sim.set_time(0.0, 1.0)
+        # clocks sampled over the warm-up and timed attempts (identical work)
+        clk = Clocks(local) if (profile and rank == 0) else None
         sim.advance_attempts(W)
         st0 = sim.stats()
         if profile:
             sim.profile(True)
         barrier()
-        clk = Clocks(local) if (profile and rank == 0) else None
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         w0 = time.perf_counter()
@@ -252,29 +253,37 @@ def run_ours(args, rank, world, dist):
 
 
 def run_ensemble(K, t_final, rank=0, world=1):
-    """Uneven-grid ensemble (members 0..K-1 of the seeded recipe: sides from
-    {64,96,120,128,160}, 4-24 nuclei, T0 +/- 20 K), FP32-bulk ARK4 adaptive at
-    rtol 1e-4: all members one after another with pf_advance, then the same
-    states advanced together with pf_batch_advance."""
+    """Ensembles advanced to t_final (ARK4 adaptive, rtol 1e-4, atol 1e-8):
+    every member one after another with pf_advance, then the same states
+    together with pf_batch_advance (one launch of the device-looped graph).
+
+    - "uneven": members 0..K-1 of the seeded uneven-grid recipe (sides from
+      {64,96,120,128,160}, 4-24 nuclei, T0 +/- 20 K), FP32-bulk, and the plain
+      FP64 path advanced member by member as the comparison point;
+    - "small": K members of 32^3 and 48^3 (4 nuclei each), FP32-bulk, where a
+      single member's kernels no longer fill the GPU."""
     import torch
 
     import paper_2609_36100_gb300 as pfg
     import synth
     from paper_2609_36100_gb300.dist import max_over_ranks, shard, sum_over_ranks
 
-    # members shard across ranks (no collective on the data path)
-    mem = [synth.ensemble_member(i) for i in shard(K, rank, world)]
+    p = synth.load_params()
+    ids = shard(K, rank, world)  # members shard across ranks (no collective on the data path)
+    recipes = {
+        "uneven": [synth.ensemble_member(i) for i in ids],
+        "small": [(synth.ic_spheres((32, 48)[i % 2], 4, 3.0, 5.0, 300 + i, p), p) for i in ids],
+    }
     stream = torch.cuda.current_stream()
-
+    dev = "cuda"
     tuned = {}
 
-    def timed(fn):
+    def timed(mem, prec, fn):
         sims = []
-        for y0, p in mem:
-            s = pfg.Simulation(y0.shape[1:], p, "ark4", "fp32bulk")
+        for y0, q in mem:
+            s = pfg.Simulation(y0.shape[1:], q, "ark4", prec)
             s.set_state(y0)
-            # one autotuned schedule per distinct grid size
-            key = y0.shape[1:]
+            key = (y0.shape[1:], prec)  # one autotuned schedule per grid size
             if key not in tuned:
                 tuned[key] = s.autotune(reps=1)["cfg"]
             s.set_tuning(tuned[key])
@@ -290,23 +299,23 @@ def run_ensemble(K, t_final, rank=0, world=1):
         st = [s.stats() for s in sims]
         for s in sims:
             s.close()
-        return e0.elapsed_time(e1), st
+        ms = max_over_ranks(e0.elapsed_time(e1), dev)
+        ps = sum_over_ranks(sum(x["point_stages"] for x in st), dev)
+        return {"ms": ms, "gpt_stage_s": ps / (ms / 1e3) / 1e9, "sim_s_per_wall_s": K * t_final / (ms / 1e3)}
 
-    ms_seq, st_seq = timed(lambda sims: [s.advance(t_final, 1e-4, 1e-8) for s in sims])
-    ms_bat, st_bat = timed(lambda sims: pfg.batch_advance(sims, t_final, 1e-4, 1e-8))
-    dev = "cuda"
-    ms_seq = max_over_ranks(ms_seq, dev)
-    ms_bat = max_over_ranks(ms_bat, dev)
-    ps_seq = sum_over_ranks(sum(x["point_stages"] for x in st_seq), dev)
-    ps_bat = sum_over_ranks(sum(x["point_stages"] for x in st_bat), dev)
-    sides = sorted({int(y0.shape[1]) for y0, _ in mem})
-    return {"members": K, "ranks": world, "sides_rank0": sides,
-            "points": int(sum_over_ranks(sum(y0[0].size for y0, _ in mem), dev)), "t_final": t_final,
-            "sequential": {"ms": ms_seq, "gpt_stage_s": ps_seq / (ms_seq / 1e3) / 1e9,
-                           "sim_s_per_wall_s": K * t_final / (ms_seq / 1e3)},
-            "batched": {"ms": ms_bat, "gpt_stage_s": ps_bat / (ms_bat / 1e3) / 1e9,
-                        "sim_s_per_wall_s": K * t_final / (ms_bat / 1e3)},
-            "gain_batched_vs_sequential": ms_seq / ms_bat}
+    out = {"members": K, "ranks": world, "t_final": t_final}
+    for name, mem in recipes.items():
+        r = {"sides_rank0": sorted({int(y0.shape[1]) for y0, _ in mem}),
+             "points": int(sum_over_ranks(sum(y0[0].size for y0, _ in mem), dev))}
+        r["sequential"] = timed(mem, "fp32bulk", lambda sims: [s.advance(t_final, 1e-4, 1e-8) for s in sims])
+        r["batched"] = timed(mem, "fp32bulk", lambda sims: pfg.batch_advance(sims, t_final, 1e-4, 1e-8))
+        r["batched"]["rounds"], r["batched"]["device_looped"] = pfg.batch_last()
+        r["gain_batched_vs_sequential"] = r["sequential"]["ms"] / r["batched"]["ms"]
+        if name == "uneven":
+            r["fp64_sequential"] = timed(mem, "fp64", lambda sims: [s.advance(t_final, 1e-4, 1e-8) for s in sims])
+            r["gain_batched_fp32bulk_vs_fp64"] = r["fp64_sequential"]["ms"] / r["batched"]["ms"]
+        out[name] = r
+    return out
 
 
 def run_surrogate(ntraj, n=64, dt=1.0, nsnap=25, epochs=3):

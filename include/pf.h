@@ -146,10 +146,28 @@ int pf_advance(pf_ctx* ctx, double t_final, double rtol, double atol, pf_stats* 
 int pf_advance_attempts(pf_ctx* ctx, double t_final, double rtol, double atol, int max_attempts, pf_stats* out);
 
 /* Advance n independent contexts (same stream, same method and precision,
- * any grid sizes) to t_final, each with its own step size and controller,
- * the stages of all members issued together per pass.  `out` has n entries or
- * is NULL. */
+ * any grid sizes) to t_final, each with its own step size and controller.
+ * One round = one step attempt of every live member (stage sequence,
+ * completion, WRMS norm, accept/reject, next step size -- all on the device),
+ * captured once per call into a CUDA graph.  Members run as independent
+ * branches of that graph, so small grids share the GPU.  The rounds run from
+ * a single launch of a device-looped graph (a conditional WHILE node over the
+ * rounds, a conditional IF node per member that skips finished members) and
+ * the host waits once; where the driver lacks conditional nodes, or in
+ * PF_BATCH_POLLED mode, the round graph is relaunched under a host poll.  At
+ * most 2^20 rounds (PF_ESTEPFAIL beyond).  `out` has n entries or is NULL. */
 int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, double atol, pf_stats* out);
+
+/* Driver of pf_batch_advance for this process: PF_BATCH_AUTO (device-looped
+ * graph where available) or PF_BATCH_POLLED.  Returns the previous mode, or
+ * PF_EINVAL for an unknown one.  Not thread-safe against concurrent
+ * pf_batch_advance calls. */
+#define PF_BATCH_AUTO 0
+#define PF_BATCH_POLLED 1
+int pf_batch_mode(int mode);
+/* Rounds run by the last pf_batch_advance call of this process and whether
+ * they ran device-looped (1) or host-polled (0); NULL pointers allowed. */
+int pf_batch_last(long long* rounds, int* looped);
 
 /* Total free energy F = int (f_b + f_el + f_ch) dV of the current state
  * (Sec. 4.1), FP64. */

@@ -70,6 +70,8 @@ SIGNATURES = {
     "pf_advance_attempts": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(PFStats)]),
     "pf_batch_advance": (C.c_int, [C.POINTER(_P), C.c_int, C.c_double, C.c_double, C.c_double,
                                    C.POINTER(PFStats)]),
+    "pf_batch_mode": (C.c_int, [C.c_int]),
+    "pf_batch_last": (C.c_int, [C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "pf_free_energy": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "pf_get_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pf_set_time": (C.c_int, [_P, C.c_double, C.c_double]),
@@ -362,14 +364,27 @@ class Simulation:
         return st.as_dict()
 
 
-def batch_advance(sims, t_final, rtol=1e-4, atol=1e-8):
-    """Advance several simulations (same method and precision) to t_final."""
+def batch_advance(sims, t_final, rtol=1e-4, atol=1e-8, polled=False):
+    """Advance several simulations (same method and precision) to t_final;
+    `polled` forces the host-polled round driver instead of the device-looped
+    graph."""
     n = len(sims)
     arr = (C.c_void_p * n)(*[s.ctx.value for s in sims])
     st = (PFStats * n)()
-    rc = lib().pf_batch_advance(arr, n, float(t_final), float(rtol), float(atol), st)
+    prev = lib().pf_batch_mode(1 if polled else 0)
+    try:
+        rc = lib().pf_batch_advance(arr, n, float(t_final), float(rtol), float(atol), st)
+    finally:
+        lib().pf_batch_mode(prev)
     _check(rc, sims[0].ctx if rc != PF_OK else None)
     return [s.as_dict() for s in st]
+
+
+def batch_last():
+    """(rounds, device_looped) of the last batch_advance call."""
+    r, lp = C.c_longlong(), C.c_int()
+    lib().pf_batch_last(C.byref(r), C.byref(lp))
+    return r.value, bool(lp.value)
 
 
 class FNO:

@@ -948,6 +948,23 @@ int pf_advance_attempts(pf_ctx* c, double t_final, double rtol, double atol, int
     return rc;
 }
 
+static int g_batch_mode = PF_BATCH_AUTO;
+static long long g_batch_rounds = 0;
+static int g_batch_looped = 0;
+
+int pf_batch_mode(int mode) {
+    if (mode != PF_BATCH_AUTO && mode != PF_BATCH_POLLED) return fail(nullptr, PF_EINVAL, "pf_batch_mode: unknown mode");
+    const int prev = g_batch_mode;
+    g_batch_mode = mode;
+    return prev;
+}
+
+int pf_batch_last(long long* rounds, int* looped) {
+    if (rounds) *rounds = g_batch_rounds;
+    if (looped) *looped = g_batch_looped;
+    return PF_OK;
+}
+
 int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, double atol, pf_stats* out) {
     if (!ctxs || n <= 0) return fail(nullptr, PF_EINVAL, "pf_batch_advance: empty batch");
     if (!(rtol >= 0) || !(atol > 0)) return fail(nullptr, PF_EINVAL, "pf_batch_advance: need rtol >= 0, atol > 0");
@@ -1054,7 +1071,78 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
         c->prof_on = prof;
         if (!rc && e != cudaSuccess) rc = fail(c0, PF_ECUDA, "batch capture: %s", cudaGetErrorString(e));
     }
-    if (!rc) {
+    // One graph launch advances the whole ensemble: a WHILE node (some member
+    // live, round cap 2^20) around one round in which a gate kernel opens each
+    // member's IF node only while that member is live, so members that are
+    // done launch nothing, and the host waits once.  Where conditional nodes
+    // are unavailable, one plain graph holding every member's round is
+    // relaunched with a host poll of the live flags after every two rounds.
+    struct LoopState {
+        unsigned long long rounds;
+        int capped;
+    };
+    const unsigned long long kRoundCap = 1ull << 20;
+    LoopState* d_loop = nullptr;
+    cudaGraphConditionalHandle* d_hif = nullptr;
+    bool looped = false;
+    if (!rc && g_batch_mode == PF_BATCH_AUTO) {
+        cudaError_t e = cudaMalloc((void**)&d_loop, sizeof(LoopState));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&d_hif, sizeof(cudaGraphConditionalHandle) * n);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_loop, 0, sizeof(LoopState), s);
+        std::vector<cudaGraphConditionalHandle> hif(n);
+        cudaGraphConditionalHandle hw{};
+        cudaGraph_t top = nullptr;
+        if (e == cudaSuccess) e = cudaGraphCreate(&top, 0);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, top, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams wp{};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = hw;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wnode{};
+        if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp);
+        cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+        for (int m = 0; m < n && e == cudaSuccess; ++m) e = cudaGraphConditionalHandleCreate(&hif[m], body, 0, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d_hif, hif.data(), sizeof(cudaGraphConditionalHandle) * n, cudaMemcpyHostToDevice);
+        cudaGraphNode_t gate{};
+        if (e == cudaSuccess) e = add_batch_gate_node(&gate, body, d_ctl, d_hif, n);
+        std::vector<cudaGraphNode_t> ifn(n);
+        for (int m = 0; m < n && e == cudaSuccess; ++m) {
+            cudaGraphNodeParams ip{};
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = hif[m];
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            e = cudaGraphAddNode(&ifn[m], body, &gate, nullptr, 1, &ip);
+            cudaGraphNode_t child{};
+            if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, ip.conditional.phGraph_out[0], nullptr, 0, graphs[m]);
+        }
+        cudaGraphNode_t more{};
+        if (e == cudaSuccess)
+            e = add_batch_more_node(&more, body, ifn.data(), ifn.size(), d_ctl, n, hw, &d_loop->rounds, kRoundCap,
+                                    &d_loop->capped);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, top, 0);
+        if (e == cudaSuccess) {
+            looped = true;
+            batch = top;
+        } else {
+            cudaGetLastError();
+            if (top) cudaGraphDestroy(top);
+            exec = nullptr;
+        }
+    }
+    long long rounds = 0;
+    if (!rc && looped) {
+        LoopState hl{};
+        cudaError_t e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_ctl, d_ctl, sizeof(MemberCtl) * n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hl, d_loop, sizeof hl, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = fail(c0, PF_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+        rounds = (long long)hl.rounds;
+        if (!rc && hl.capped) rc = fail(c0, PF_ESTEPFAIL, "pf_batch_advance: no end after %llu rounds", hl.rounds);
+    } else if (!rc) {
         cudaError_t e = cudaGraphCreate(&batch, 0);
         for (int m = 0; m < n && e == cudaSuccess; ++m) {
             cudaGraphNode_t node;
@@ -1062,27 +1150,28 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, batch, 0);
         if (e != cudaSuccess) rc = fail(c0, PF_ECUDA, "batch graph: %s", cudaGetErrorString(e));
-    }
-    // one graph launch advances every member by one attempt; poll for the end
-    long long rounds = 0;
-    while (!rc) {
-        cudaError_t e = cudaGraphLaunch(exec, s);
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
-        rounds += 2;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_ctl, d_ctl, sizeof(MemberCtl) * n, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            rc = fail(c0, PF_ECUDA, "batch round: %s", cudaGetErrorString(e));
-            break;
+        while (!rc) {
+            e = cudaGraphLaunch(exec, s);
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+            rounds += 2;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_ctl, d_ctl, sizeof(MemberCtl) * n, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                rc = fail(c0, PF_ECUDA, "batch round: %s", cudaGetErrorString(e));
+                break;
+            }
+            int live = 0;
+            for (int m = 0; m < n; ++m) live += h_ctl[m].active;
+            if (!live) break;
+            if (rounds > (long long)kRoundCap) {
+                rc = fail(c0, PF_ESTEPFAIL, "pf_batch_advance: no end after %lld rounds", rounds);
+                break;
+            }
         }
-        int live = 0;
-        for (int m = 0; m < n; ++m) live += h_ctl[m].active;
-        if (!live) break;
-        if (rounds > 10000000) {
-            rc = fail(c0, PF_ESTEPFAIL, "pf_batch_advance: no progress");
-            break;
-        }
     }
+    g_batch_rounds = rounds;
+    g_batch_looped = looped ? 1 : 0;
     const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (int m = 0; m < n && h_ctl; ++m) {
         pf_ctx* c = ctxs[m];
@@ -1113,6 +1202,8 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
     if (fork) cudaEventDestroy(fork);
     cudaFree(d_ctl);
     cudaFree(d_coef);
+    cudaFree(d_loop);
+    cudaFree(d_hif);
     if (h_ctl) cudaFreeHost(h_ctl);
     return rc;
 }

@@ -175,6 +175,12 @@ void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamd
 void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef, cudaStream_t s);
 void launch_batch_ctl(const BatchConst& bc, MemberCtl* ctl, const double* wrms_sum, double scale, cudaStream_t s);
 void launch_batch_accept(const Geo& g, const MemberCtl* ctl, const double2* ynew, double2* y, cudaStream_t s);
+// kernel nodes of the device-looped ensemble graph
+cudaError_t add_batch_gate_node(cudaGraphNode_t* node, cudaGraph_t graph, const MemberCtl* ctl,
+                                const cudaGraphConditionalHandle* hif, int n);
+cudaError_t add_batch_more_node(cudaGraphNode_t* node, cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
+                                const MemberCtl* ctl, int n, cudaGraphConditionalHandle hwhile,
+                                unsigned long long* rounds, unsigned long long cap, int* capped);
 void launch_reduce(const double* partials, int n, double scale, double* out, cudaStream_t s);
 void launch_energy_k(const Geo& g, const Phys& ph, const double2* y, const double2* hk, double* partials,
                      cudaStream_t s);

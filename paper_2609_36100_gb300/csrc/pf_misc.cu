@@ -192,6 +192,53 @@ __global__ void k_batch_accept(Geo g, const MemberCtl* __restrict__ ctl, const d
         y[i] = ynew[i];
 }
 
+// Device-looped ensemble graph (a WHILE node around one round of every
+// member, each member's round under an IF node).  The gate opens a member's
+// IF node only while it is live; the loop condition is "some member live",
+// with a round cap so that the loop always ends.  One thread each: calls
+// that set one conditional handle must not race.
+__global__ void k_batch_gate(const MemberCtl* __restrict__ ctl, const cudaGraphConditionalHandle* __restrict__ hif,
+                             int n) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int m = 0; m < n; ++m) cudaGraphSetConditional(hif[m], ctl[m].active ? 1u : 0u);
+}
+
+__global__ void k_batch_more(const MemberCtl* __restrict__ ctl, int n, cudaGraphConditionalHandle hwhile,
+                             unsigned long long* rounds, unsigned long long cap, int* capped) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int live = 0;
+    for (int m = 0; m < n; ++m) live |= ctl[m].active;
+    const unsigned long long r = ++*rounds;
+    if (live && r >= cap) {
+        *capped = 1;
+        live = 0;
+    }
+    cudaGraphSetConditional(hwhile, live ? 1u : 0u);
+}
+
+cudaError_t add_batch_gate_node(cudaGraphNode_t* node, cudaGraph_t graph, const MemberCtl* ctl,
+                                const cudaGraphConditionalHandle* hif, int n) {
+    cudaKernelNodeParams kp{};
+    void* args[] = {(void*)&ctl, (void*)&hif, (void*)&n};
+    kp.func = (void*)k_batch_gate;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(node, graph, nullptr, 0, &kp);
+}
+
+cudaError_t add_batch_more_node(cudaGraphNode_t* node, cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
+                                const MemberCtl* ctl, int n, cudaGraphConditionalHandle hwhile,
+                                unsigned long long* rounds, unsigned long long cap, int* capped) {
+    cudaKernelNodeParams kp{};
+    void* args[] = {(void*)&ctl, (void*)&n, (void*)&hwhile, (void*)&rounds, (void*)&cap, (void*)&capped};
+    kp.func = (void*)k_batch_more;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(node, graph, deps, ndeps, &kp);
+}
+
 void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef, cudaStream_t s) {
     k_batch_prep<<<1, 32, 0, s>>>(bc, ctl, coef);
 }

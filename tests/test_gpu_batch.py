@@ -1,7 +1,8 @@
 """Ensemble batching (pf_batch_advance): members of uneven grids and
-temperatures advanced together by one captured graph per round must give what
-each member's own pf_advance gives (same attempt counts, same states to
-rounding), and an FP64 member must still match the oracle."""
+temperatures advanced together (one device-looped graph launch, or the
+host-polled round graph) must give what each member's own pf_advance gives
+(same attempt counts, same states to rounding), and an FP64 member must
+still match the oracle."""
 import numpy as np
 import pytest
 
@@ -113,3 +114,32 @@ def test_batch_rejects_mixed_methods(pfg, params):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32bulk"])
+def test_batch_device_looped_equals_polled(pfg, params, prec):
+    """The device-looped driver runs the same rounds as the host-polled one
+    and gives bitwise the same states; members that finish early skip their
+    rounds (attempt counts per member unchanged)."""
+    ms = members(params)
+    out = {}
+    for polled in (False, True):
+        sims = [pfg.Simulation(shape, p, "ark4", prec) for shape, p, _ in ms]
+        try:
+            for s, (_, _, y0) in zip(sims, ms):
+                s.set_state(y0)
+            stats = pfg.batch_advance(sims, 4.0, 1e-4, 1e-8, polled=polled)
+            rounds, looped = pfg.batch_last()
+            out[polled] = ([s.state_hat().cpu().numpy() for s in sims], stats, rounds, looped)
+        finally:
+            for s in sims:
+                s.close()
+    states_l, stats_l, rounds_l, looped_l = out[False]
+    states_p, stats_p, rounds_p, looped_p = out[True]
+    assert looped_l and not looped_p
+    attempts = [st["steps_accepted"] + st["steps_rejected"] for st in stats_l]
+    assert rounds_l == max(attempts)          # the loop ends with the last live member
+    assert rounds_p >= rounds_l               # the polled driver checks every two rounds
+    for a, b, sa, sb in zip(states_l, states_p, stats_l, stats_p):
+        assert np.array_equal(a, b)
+        assert sa["steps_accepted"] == sb["steps_accepted"] and sa["steps_rejected"] == sb["steps_rejected"]
