@@ -1048,12 +1048,14 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
     const cudaStream_t s_user = s;
     if (cap) s = cap;
     // capture one round of each member: prep, stages, completion, norm,
-    // controller, accepted-state copy
+    // controller (an accepted attempt flips which state buffer holds y)
     for (int m = 0; m < n && !rc; ++m) {
         pf_ctx* c = ctxs[m];
         const bool prof = c->prof_on;
         c->prof_on = false;
         c->g.active = &d_ctl[m].active;
+        c->g.ypar = &d_ctl[m].ypar;
+        c->g.yother = c->ynew;
         c->stream = cap;
         StageCoefDev* coef = d_coef + (size_t)m * ncoef;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
@@ -1062,11 +1064,12 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
             int r2 = c->fp32 ? enqueue_step<float>(c, 1.0, tb.embedded, coef)
                              : enqueue_step<double>(c, 1.0, tb.embedded, coef);
             launch_batch_ctl(bc, d_ctl + m, c->d_scalar, 1.0, s);
-            launch_batch_accept(c->g, d_ctl + m, c->ynew, c->y, s);
             e = cudaStreamEndCapture(s, &graphs[m]);
             if (r2) rc = r2;
         }
         c->g.active = nullptr;
+        c->g.ypar = nullptr;
+        c->g.yother = nullptr;
         c->stream = s_user;
         c->prof_on = prof;
         if (!rc && e != cudaSuccess) rc = fail(c0, PF_ECUDA, "batch capture: %s", cudaGetErrorString(e));
@@ -1177,6 +1180,7 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
         pf_ctx* c = ctxs[m];
         const MemberCtl& h = h_ctl[m];
         if (rounds > 0) {
+            if (h.ypar) std::swap(c->y, c->ynew);  // the state ended in the y_new buffer
             c->t = h.t;
             if (tb.embedded) c->h = h.h;
             c->e_prev = h.e_prev;

@@ -52,6 +52,9 @@ __device__ __forceinline__ float qgl_of(const StageTerms& st) { return st.dc ? s
 // batch members that reached t_final (or failed) skip all work
 #define PF_SKIP_INACTIVE(g) \
     if ((g).active && *(g).active == 0) return
+// a batch member's state alternates between its two state buffers (an
+// accepted attempt flips the parity instead of copying y_new over y)
+__device__ __forceinline__ bool y_swapped(const Geo& g) { return g.ypar && *g.ypar; }
 
 template <typename T2>
 __device__ __forceinline__ double2 load_f(const void* p, long long i) {

@@ -47,6 +47,8 @@ struct Geo {
     AxisPlan px, py, pz;
     unsigned mul_nx, mul_nxh;  // division magic for nx and nx/2+1
     const int* active;         // batch member flag: kernels return at once when *active == 0
+    const int* ypar;           // batch member: when *ypar != 0 the state lives in yother (the context's
+    double2* yother;           // y_new buffer) and y_new goes to the context's y buffer
     int tx_y, tx_z, tx_el;  // tuned tile widths (kx columns) of the strided passes, 0 = heuristic
     int rp;                  // tuned row pairs per CTA in the x passes, 0 = heuristic
 };
@@ -124,6 +126,7 @@ struct StageTerms {
 struct MemberCtl {
     double t, h, dt, e_prev, e_last;
     int after_reject, nrej, active, accepted_now, status;
+    int ypar;  // which of the two state buffers holds y (flips on every accepted attempt)
     long long n_acc, n_rej, n_rhs;
 };
 
@@ -174,7 +177,6 @@ void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamd
 // batch round: coefficients from the member's step, controller, accepted-state copy
 void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef, cudaStream_t s);
 void launch_batch_ctl(const BatchConst& bc, MemberCtl* ctl, const double* wrms_sum, double scale, cudaStream_t s);
-void launch_batch_accept(const Geo& g, const MemberCtl* ctl, const double2* ynew, double2* y, cudaStream_t s);
 // kernel nodes of the device-looped ensemble graph
 cudaError_t add_batch_gate_node(cudaGraphNode_t* node, cudaGraph_t graph, const MemberCtl* ctl,
                                 const cudaGraphConditionalHandle* hif, int n);

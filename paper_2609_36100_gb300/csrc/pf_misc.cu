@@ -10,6 +10,7 @@ namespace pf {
 __global__ void k_stage_pointwise(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st, int fe32,
                                   double2* __restrict__ zout) {
     PF_SKIP_INACTIVE(g);
+    if (y_swapped(g)) y = g.yother;
     const long long total = 4LL * g.NK;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
          gi += (long long)gridDim.x * blockDim.x) {
@@ -41,6 +42,7 @@ __global__ void k_stage_pointwise(Geo g, Phys ph, const double2* __restrict__ y,
 // transform (stages whose f^E no later stage or completion reads)
 __global__ void k_stage_pointwise_df(Geo g, const double2* __restrict__ y, StageTerms st, float4* __restrict__ zout) {
     PF_SKIP_INACTIVE(g);
+    if (y_swapped(g)) y = g.yother;
     const long long total = 4LL * g.NK;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
          gi += (long long)gridDim.x * blockDim.x)
@@ -157,6 +159,7 @@ __global__ void k_batch_ctl(BatchConst bc, MemberCtl* __restrict__ ctl, const do
         m.n_acc += 1;
         m.nrej = 0;
         m.accepted_now = 1;
+        m.ypar ^= 1;
         if (bc.embedded) {
             const double ee = e < 1e-10 ? 1e-10 : e;
             double eta = bc.safety * pow(ee, -bc.k1 / bc.q) * pow(m.e_prev, bc.k2 / bc.q);
@@ -182,15 +185,6 @@ __global__ void k_batch_ctl(BatchConst bc, MemberCtl* __restrict__ ctl, const do
     if (!(m.t < bc.t_final * (1 - 1e-14))) m.active = 0;
 }
 
-// y <- y_new for an accepted attempt
-__global__ void k_batch_accept(Geo g, const MemberCtl* __restrict__ ctl, const double2* __restrict__ ynew,
-                               double2* __restrict__ y) {
-    if (!ctl->accepted_now) return;
-    const long long total = 4LL * g.NK;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x)
-        y[i] = ynew[i];
-}
 
 // Device-looped ensemble graph (a WHILE node around one round of every
 // member, each member's round under an IF node).  The gate opens a member's
@@ -244,9 +238,6 @@ void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef,
 }
 void launch_batch_ctl(const BatchConst& bc, MemberCtl* ctl, const double* wrms_sum, double scale, cudaStream_t s) {
     k_batch_ctl<<<1, 32, 0, s>>>(bc, ctl, wrms_sum, scale);
-}
-void launch_batch_accept(const Geo& g, const MemberCtl* ctl, const double2* ynew, double2* y, cudaStream_t s) {
-    k_batch_accept<<<152 * 4, 256, 0, s>>>(g, ctl, ynew, y);
 }
 
 // deterministic single-CTA reduction: out = sum(partials) * scale (FP64)

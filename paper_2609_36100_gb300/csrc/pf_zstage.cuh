@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Ge
                                                       double2* __restrict__ zout,
                                                       typename Cx<T>::t* __restrict__ W) {
     PF_SKIP_INACTIVE(g);
+    if (y_swapped(g)) y = g.yother;
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
@@ -110,6 +111,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_final(Ge
                                                       StageTerms dt, int want_lte, double2* __restrict__ ynew,
                                                       typename Cx<T>::t* __restrict__ W) {
     PF_SKIP_INACTIVE(g);
+    if (y_swapped(g)) {
+        double2* other = const_cast<double2*>(y);
+        y = ynew;
+        ynew = other;
+    }
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
