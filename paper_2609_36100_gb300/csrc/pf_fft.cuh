@@ -242,6 +242,84 @@ __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time plans for contiguous (skewed) lines: the length N, the radix
+// order and each stage's sub-transform size NS are constants, so the line /
+// butterfly split is a constant division and, wherever the skew allows, every
+// shared-memory offset of a butterfly is an immediate from one per-thread
+// base address (the generic stage spends about as many integer instructions
+// on addressing as floating-point ones on the butterfly).
+// ---------------------------------------------------------------------------
+template <int... Rs>
+struct Radices {};
+
+template <int R, int SIGN, int N, int NS, typename T2>
+__device__ __forceinline__ void fft_stage_fixed(const T2* __restrict__ src, T2* __restrict__ dst, int nl, int ls,
+                                                const T2* __restrict__ tw) {
+    constexpr int M = N / R;           // butterflies per line
+    constexpr int TWS = N / (NS * R);  // twiddle table stride of this stage
+    static_assert(M * R == N, "radix does not divide the length");
+    const int total = nl * M;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int line = idx / M, j = idx - line * M;
+        const T2* s = src + line * ls;
+        T2 v[R];
+        if constexpr (M % 16 == 0) {
+            // skew(j + t M) = skew(j) + t (M + M/16)
+            const T2* sj = s + skew<true>(j);
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = sj[t * (M + M / 16)];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = s[skew<true>(j + t * M)];
+        }
+        const int jq = j / NS, k = j - jq * NS;
+        if constexpr (NS > 1) {
+            const int st = k * TWS;
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                const T2 w = __ldg(tw + t * st);
+                v[t] = SIGN < 0 ? cmul(v[t], w) : cmulc(v[t], w);
+            }
+        }
+        Bfly<R, SIGN, T2>::run(v);
+        T2* d = dst + line * ls;
+        const int a = jq * NS * R;  // output block start; outputs at a + k + t NS
+        if constexpr ((NS * R) % 16 == 0 && NS % 16 == 0) {
+            T2* dk = d + skew<true>(a) + skew<true>(k);
+#pragma unroll
+            for (int t = 0; t < R; ++t) dk[t * (NS + NS / 16)] = v[t];
+        } else if constexpr ((NS * R) % 16 == 0 && 16 % NS == 0) {
+            // k + t NS never crosses a 16-block boundary except at multiples of 16
+            T2* dk = d + skew<true>(a) + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t) dk[t * NS + ((t * NS) >> 4)] = v[t];
+        } else if constexpr (NS == 1 && 16 % R == 0) {
+            // a = j R and a + t stay inside one 16-block
+            T2* dk = d + skew<true>(a);
+#pragma unroll
+            for (int t = 0; t < R; ++t) dk[t] = v[t];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) d[skew<true>(a + k + t * NS)] = v[t];
+        }
+    }
+}
+
+template <int SIGN, int N, int NS, typename T2>
+__device__ __forceinline__ T2* fft_fixed_run(T2* src, T2*, int, int, const T2*, Radices<>) {
+    return src;
+}
+
+// Full transform of nl skewed lines with a compile-time plan; returns the
+// buffer holding the result (synchronised).
+template <int SIGN, int N, int NS, typename T2, int R, int... Rest>
+__device__ __forceinline__ T2* fft_fixed_run(T2* src, T2* dst, int nl, int ls, const T2* tw, Radices<R, Rest...>) {
+    fft_stage_fixed<R, SIGN, N, NS>(src, dst, nl, ls, tw);
+    __syncthreads();
+    return fft_fixed_run<SIGN, N, NS * R>(dst, src, nl, ls, tw, Radices<Rest...>{});
+}
+
 // Full transform of the lines in `a` (b is scratch).  Radix-16 stages are
 // compiled in only with R16 (they raise the register count of the whole
 // kernel); the launcher picks R16 from the plan (AxisPlan::has16).  Callers synchronise

@@ -1,6 +1,7 @@
 // x passes: packed real transforms along the contiguous axis with the
 // real-space physics of the right-hand side, the WRMS error norm and the
 // real-space free energy fused in.
+#pragma once
 #include "pf_common.cuh"
 
 namespace pf {
@@ -50,22 +51,101 @@ struct Pt {
 template <typename T>
 __device__ __forceinline__ T hfun(T f) { return f * f * f * ((T)6 * f * f - (T)15 * f + (T)10); }
 
+// x-axis plans compiled with a constant length and radix order (PID > 0);
+// any other plan runs the generic kernel (PID 0).  The list holds the default
+// plans of the grid sizes of the workloads (FP32 plans prefer radix 16, FP64
+// plans radix 8).
+template <int PID>
+struct XPlan {
+    static constexpr int N = 0;
+    using Rad = Radices<>;
+};
+#define PF_XPLAN(PID_, N_, ...)                 \
+    template <>                                 \
+    struct XPlan<PID_> {                        \
+        static constexpr int N = N_;            \
+        using Rad = Radices<__VA_ARGS__>;       \
+    };
+PF_XPLAN(1, 256, 16, 16)
+PF_XPLAN(2, 256, 8, 8, 4)
+PF_XPLAN(3, 128, 16, 8)
+PF_XPLAN(4, 128, 8, 4, 4)
+PF_XPLAN(5, 64, 16, 4)
+PF_XPLAN(6, 64, 8, 8)
+PF_XPLAN(7, 160, 8, 4, 5)
+PF_XPLAN(8, 96, 8, 4, 3)
+PF_XPLAN(9, 120, 8, 3, 5)
+PF_XPLAN(10, 192, 16, 4, 3)
+PF_XPLAN(11, 640, 16, 8, 5)
+#undef PF_XPLAN
+constexpr int kXPlans = 11;
+
+template <int... Rs>
+inline bool plan_is(const AxisPlan& p, int n, Radices<Rs...>) {
+    const int r[] = {Rs...};
+    if (p.n != n || p.nst != (int)sizeof...(Rs)) return false;
+    for (int s = 0; s < p.nst; ++s)
+        if (p.rad[s] != r[s]) return false;
+    return true;
+}
+
+template <int PID = 1>
+inline int xplan_id(const AxisPlan& p) {
+    if constexpr (PID > kXPlans) {
+        return 0;
+    } else {
+        if (plan_is(p, XPlan<PID>::N, typename XPlan<PID>::Rad{})) return PID;
+        return xplan_id<PID + 1>(p);
+    }
+}
+
+// line length nx and half-spectrum length nx/2+1 along x, compile-time when
+// NX > 0, and the divisions by them
+template <int NX>
+struct XLen {
+    int n, h;
+    unsigned mn, mh;
+    __device__ __forceinline__ explicit XLen(const Geo& g)
+        : n(NX > 0 ? NX : g.nx), h(NX > 0 ? NX / 2 + 1 : g.nxh), mn(g.mul_nx), mh(g.mul_nxh) {}
+    __device__ __forceinline__ int divn(int e) const {
+        if constexpr (NX > 0)
+            return e / NX;
+        else
+            return (int)FastDiv((unsigned)n, mn).div((unsigned)e);
+    }
+    __device__ __forceinline__ int divh(int e) const {
+        if constexpr (NX > 0)
+            return e / (NX / 2 + 1);
+        else
+            return (int)FastDiv((unsigned)h, mh).div((unsigned)e);
+    }
+};
+
+// transform of nl skewed x lines: compile-time plan, or the generic stages
+template <int SIGN, int PID, bool R16, typename T2>
+__device__ __forceinline__ T2* x_fft(T2* a, T2* b, const AxisPlan& p, int nl, int ls) {
+    if constexpr (PID > 0)
+        return fft_fixed_run<SIGN, XPlan<PID>::N, 1>(a, b, nl, ls, twiddles<T2>(p), typename XPlan<PID>::Rad{});
+    else
+        return fft_lines<SIGN, false, 0, true, R16>(a, b, p, nl, 1, ls);
+}
+
 // load F packed lines (C2R input) of row pairs [rp0, rp0+P) into S
-template <typename T2>
+template <int NX, typename T2>
 __device__ __forceinline__ void c2r_load(const Geo& g, const T2* __restrict__ in, int F, int P, int rp0, int npairs,
                                          T2* S, int ls) {
-    const int nx = g.nx, nh = nx / 2;
-    const FastDiv dnx((unsigned)nx, g.mul_nx);
+    const XLen<NX> L(g);
+    const int nx = L.n, nh = nx / 2, nxh = L.h;
     // unrolled so that several iterations' loads are in flight together
 #pragma unroll 4
     for (int e = threadIdx.x; e < P * F * nx; e += blockDim.x) {
-        const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = F == 4 ? line >> 2 : line / 3, f = line - rp * F;
+        const int line = L.divn(e), x = e - line * nx, rp = F == 4 ? line >> 2 : line / 3, f = line - rp * F;
         T2 Z = T2{0, 0};
         if (rp0 + rp < npairs) {
             const long long row = 2LL * (rp0 + rp);
             const int k = x <= nh ? x : nx - x;
-            const T2* base = in + (long long)f * g.NK + row * g.nxh + k;
-            T2 a = base[0], b = base[g.nxh];
+            const T2* base = in + (long long)f * g.NK + row * nxh + k;
+            T2 a = base[0], b = base[nxh];
             if (k == 0 || k == nh) {
                 a.y = 0;
                 b.y = 0;
@@ -79,14 +159,14 @@ __device__ __forceinline__ void c2r_load(const Geo& g, const T2* __restrict__ in
     }
 }
 
-template <typename T2>
+template <int NX, typename T2>
 __device__ __forceinline__ void r2c_store(const Geo& g, const T2* S, int ls, int F, int P, int rp0, int npairs,
                                           T2* __restrict__ out) {
     using T = decltype(T2{}.x);
-    const int nx = g.nx, nxh = g.nxh;
-    const FastDiv dnh((unsigned)nxh, g.mul_nxh);
+    const XLen<NX> L(g);
+    const int nx = L.n, nxh = L.h;
     for (int e = threadIdx.x; e < P * F * nxh; e += blockDim.x) {
-        const int line = (int)dnh.div((unsigned)e), k = e - line * nxh, rp = F == 4 ? line >> 2 : line / 3, f = line - rp * F;
+        const int line = L.divh(e), k = e - line * nxh, rp = F == 4 ? line >> 2 : line / 3, f = line - rp * F;
         if (rp0 + rp >= npairs) continue;
         const T2 Zk = S[line * ls + skew<true>(k)];
         const T2 Zm = S[line * ls + skew<true>(k == 0 ? 0 : nx - k)];
@@ -100,7 +180,7 @@ __device__ __forceinline__ void r2c_store(const Geo& g, const T2* S, int ls, int
     }
 }
 
-template <typename T, bool R16>
+template <typename T, bool R16, int PID>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo g, Phys ph, int mode, const typename Cx<T>::t* __restrict__ in,
                                                      typename Cx<T>::t* __restrict__ out, T* __restrict__ R,
                                                      const T* __restrict__ Rin, double* __restrict__ partials,
@@ -109,9 +189,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
     PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int nx = g.nx;
+    constexpr int NX = XPlan<PID>::N;
+    const XLen<NX> L(g);
+    const int nx = L.n;
     const int ls = skewed_len(nx);
-    const FastDiv dnx((unsigned)nx, g.mul_nx);
     const PhysT<T>& pt = phys_t<T>(ph);
     const int npairs = g.nz * g.ny / 2;
     const int rp0 = blockIdx.x * P;
@@ -127,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
     if (mode == XM_R2C_REAL) {
 #pragma unroll 4
         for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
-            const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = line >> 2, f = line & 3;
+            const int line = L.divn(e), x = e - line * nx, rp = line >> 2, f = line & 3;
             T2 Z = T2{0, 0};
             if (rp0 + rp < npairs) {
                 const long long row = 2LL * (rp0 + rp);
@@ -137,20 +218,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
             S0[line * ls + skew<true>(x)] = Z;
         }
         __syncthreads();
-        T2* res = fft_lines<-1, false, 0, true, R16>(S0, S1, g.px, 4 * P, 1, ls);
-        r2c_store(g, res, ls, 4, P, rp0, npairs, out);
+        T2* res = x_fft<-1, PID, R16>(S0, S1, g.px, 4 * P, ls);
+        r2c_store<NX>(g, res, ls, 4, P, rp0, npairs, out);
         return;
     }
     if (Fin > 0) {
-        c2r_load(g, in, Fin, P, rp0, npairs, S0, ls);
+        c2r_load<NX>(g, in, Fin, P, rp0, npairs, S0, ls);
         __syncthreads();
-        RS = fft_lines<+1, false, 0, true, R16>(S0, S1, g.px, Fin * P, 1, ls);
+        RS = x_fft<+1, PID, R16>(S0, S1, g.px, Fin * P, ls);
     }
     T2* OS = (RS == S0) ? S1 : S0;  // output lines
 
     if (mode == XM_C2R_REAL) {
         for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
-            const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = line >> 2, f = line & 3;
+            const int line = L.divn(e), x = e - line * nx, rp = line >> 2, f = line & 3;
             if (rp0 + rp >= npairs) continue;
             const long long row = 2LL * (rp0 + rp);
             const T2 z = RS[line * ls + skew<true>(x)];
@@ -164,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
     if (mode == XM_WRMS) {
         double acc = 0.0;
         for (int e = threadIdx.x; e < P * 4 * nx; e += blockDim.x) {
-            const int line = (int)dnx.div((unsigned)e), x = e - line * nx, rp = line >> 2, f = line & 3;
+            const int line = L.divn(e), x = e - line * nx, rp = line >> 2, f = line & 3;
             if (rp0 + rp >= npairs) continue;
             const long long row = 2LL * (rp0 + rp);
             const T2 z = RS[line * ls + skew<true>(x)];
@@ -199,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
     const bool full_rhs = (mode == XM_PHYS2) || (mode == XM_PHYS1 && !ph.elastic);
 #pragma unroll 2
     for (int e = threadIdx.x; e < P * nx; e += blockDim.x) {
-        const int rp = (int)dnx.div((unsigned)e), x = e - rp * nx;
+        const int rp = L.divn(e), x = e - rp * nx;
         if (rp0 + rp >= npairs) continue;
         const long long row = 2LL * (rp0 + rp);
         T Xr[2], pr[2][3], er[2][3];
@@ -299,8 +380,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
         partials[blockIdx.x] = s;
     }
-    T2* res = fft_lines<-1, false, 0, true, R16>(OS, RS, g.px, Fout * P, 1, ls);
-    r2c_store(g, res, ls, Fout, P, rp0, npairs, out);
+    T2* res = x_fft<-1, PID, R16>(OS, RS, g.px, Fout * P, ls);
+    r2c_store<NX>(g, res, ls, Fout, P, rp0, npairs, out);
 }
 
 template <typename T>
@@ -321,89 +402,6 @@ static int x_rows(const Geo& g) {
     return P;
 }
 
-// plan from an explicit radix order (each radix in {2,3,4,5,8,16}, product n)
-bool make_axis_plan_radices(int n, const int* rad, int nr, AxisPlan& p) {
-    if (nr < 1 || nr > kMaxRadices) return false;
-    long long prod = 1;
-    for (int s = 0; s < nr; ++s) {
-        if (rad[s] != 2 && rad[s] != 3 && rad[s] != 4 && rad[s] != 5 && rad[s] != 8 && rad[s] != 16) return false;
-        prod *= rad[s];
-    }
-    if (prod != n) return false;
-    p.n = n;
-    p.nst = nr;
-    p.has16 = 0;
-    for (int s = 0; s < nr; ++s)
-        if (rad[s] == 16) p.has16 = 1;
-    unsigned Ns = 1;
-    for (int s = 0; s < nr; ++s) {
-        p.rad[s] = rad[s];
-        p.mulm[s] = magic_u32((unsigned)(n / rad[s]));
-        p.mulN[s] = magic_u32(Ns);
-        Ns *= (unsigned)rad[s];
-    }
-    return true;
-}
-
-// default schedule: the fewest stages, largest radices first -- radix-16
-// stages (prefer16) or radix-8 ones, then a 8 / 4 (or 4*4 instead of 8*2,
-// 8*4 instead of 16*2) or 2, then the 3s and 5s
-bool make_axis_plan(int n, AxisPlan& p, bool prefer16) {
-    int m = n, a = 0, b = 0, c = 0;
-    while (m % 2 == 0) { m /= 2; ++a; }
-    while (m % 3 == 0) { m /= 3; ++b; }
-    while (m % 5 == 0) { m /= 5; ++c; }
-    if (m != 1) return false;
-    int r[kMaxRadices + 8];
-    int nr = 0;
-    if (prefer16) {
-        int n16 = a / 4;
-        int rem = a % 4;
-        if (rem == 1 && n16 > 0) {
-            --n16;
-            rem = 5;
-        }
-        for (int i = 0; i < n16; ++i) r[nr++] = 16;
-        if (rem == 5) {
-            r[nr++] = 8;
-            r[nr++] = 4;
-        } else if (rem == 3) {
-            r[nr++] = 8;
-        } else if (rem == 2) {
-            r[nr++] = 4;
-        } else if (rem == 1) {
-            r[nr++] = 2;
-        }
-    } else {
-        int n8 = a / 3;
-        const int rem = a % 3;
-        bool two4 = false;
-        if (rem == 1 && n8 > 0) {
-            --n8;
-            two4 = true;
-        }
-        for (int i = 0; i < n8; ++i) r[nr++] = 8;
-        if (two4) {
-            r[nr++] = 4;
-            r[nr++] = 4;
-        } else if (rem == 2) {
-            r[nr++] = 4;
-        } else if (rem == 1) {
-            r[nr++] = 2;
-        }
-    }
-    for (int i = 0; i < b; ++i) r[nr++] = 3;
-    for (int i = 0; i < c; ++i) r[nr++] = 5;
-    if (nr > kMaxRadices) return false;
-    return make_axis_plan_radices(n, r, nr, p);
-}
-
-int x_pass_blocks(const Geo& g, int f64) {
-    const int P = f64 ? x_rows<double>(g) : x_rows<float>(g);
-    const int npairs = g.nz * g.ny / 2;
-    return (npairs + P - 1) / P;
-}
-
 template <typename T>
 void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
                    double* partials, double rtol, double atol, const double* real_in, double* real_out,
@@ -413,16 +411,27 @@ void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void*
     const size_t sm = 2 * 4 * (size_t)P * skewed_len(g.nx) * sizeof(T2);
     const int npairs = g.nz * g.ny / 2;
     const int nb = (npairs + P - 1) / P;
-    PF_R16_SWITCH(g.px.has16, set_smem(k_x_pass<T, R16C>, sm);
-                  k_x_pass<T, R16C><<<nb, kThreads, sm, s>>>(
-                      g, ph, mode, reinterpret_cast<const T2*>(in), reinterpret_cast<T2*>(out),
-                      reinterpret_cast<T*>(R), reinterpret_cast<const T*>(Rin), partials, rtol, atol, real_in,
-                      real_out, P))
+#define PF_XLAUNCH(R16_, PID_)                                                                                       \
+    set_smem(k_x_pass<T, R16_, PID_>, sm);                                                                         \
+    k_x_pass<T, R16_, PID_><<<nb, kThreads, sm, s>>>(g, ph, mode, reinterpret_cast<const T2*>(in),                 \
+                                                     reinterpret_cast<T2*>(out), reinterpret_cast<T*>(R),          \
+                                                     reinterpret_cast<const T*>(Rin), partials, rtol, atol, real_in, \
+                                                     real_out, P)
+    switch (xplan_id(g.px)) {
+        case 1: PF_XLAUNCH(false, 1); break;
+        case 2: PF_XLAUNCH(false, 2); break;
+        case 3: PF_XLAUNCH(false, 3); break;
+        case 4: PF_XLAUNCH(false, 4); break;
+        case 5: PF_XLAUNCH(false, 5); break;
+        case 6: PF_XLAUNCH(false, 6); break;
+        case 7: PF_XLAUNCH(false, 7); break;
+        case 8: PF_XLAUNCH(false, 8); break;
+        case 9: PF_XLAUNCH(false, 9); break;
+        case 10: PF_XLAUNCH(false, 10); break;
+        case 11: PF_XLAUNCH(false, 11); break;
+        default: PF_R16_SWITCH(g.px.has16, PF_XLAUNCH(R16C, 0)); break;
+    }
+#undef PF_XLAUNCH
 }
 
-// explicit instantiations
-template void launch_x_pass<double>(const Geo&, const Phys&, int, const void*, void*, void*, const void*, double*,
-                                    double, double, const double*, double*, cudaStream_t);
-template void launch_x_pass<float>(const Geo&, const Phys&, int, const void*, void*, void*, const void*, double*,
-                                   double, double, const double*, double*, cudaStream_t);
 }  // namespace pf
