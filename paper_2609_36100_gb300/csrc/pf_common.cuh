@@ -300,6 +300,83 @@ static void set_smem(K kern, size_t bytes) {
         __VA_ARGS__;                   \
     }
 
+// Launch dispatch of a column pass over the tile width (TXC), the radix-16
+// flag (R16C) and the compiled plan (PIDC): FP32 kernels with tile widths 8
+// or 16 run the compile-time plan when the axis plan is one of the compiled
+// ones, everything else the generic stages.
+#define PF_PID_CASE(K_, tx, ...)            \
+    case K_: {                              \
+        constexpr int PIDC = K_;            \
+        constexpr bool R16C = false;        \
+        if ((tx) == 16) {                   \
+            constexpr int TXC = 16;         \
+            __VA_ARGS__;                    \
+        } else {                            \
+            constexpr int TXC = 8;          \
+            __VA_ARGS__;                    \
+        }                                   \
+    } break;
+#define PF_COL_SWITCH(T_, plan, tx, ...)                                                          \
+    do {                                                                                          \
+        int pid_ = 0;                                                                             \
+        if (sizeof(T_) == 4 && ((tx) == 8 || (tx) == 16)) pid_ = fixed_plan_id(plan);              \
+        if constexpr (sizeof(T_) == 4) {                                                          \
+            switch (pid_) {                                                                       \
+                PF_PID_CASE(1, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(2, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(3, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(4, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(5, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(6, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(7, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(8, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(9, tx, __VA_ARGS__)                                                   \
+                PF_PID_CASE(10, tx, __VA_ARGS__)                                                  \
+                PF_PID_CASE(11, tx, __VA_ARGS__)                                                  \
+                default: break;                                                                   \
+            }                                                                                     \
+        }                                                                                         \
+        if (pid_ == 0) {                                                                          \
+            constexpr int PIDC = 0;                                                               \
+            PF_R16_SWITCH((plan).has16, PF_TX_SWITCH(tx, __VA_ARGS__));                            \
+        }                                                                                         \
+    } while (0)
+
+// as PF_COL_SWITCH, with compiled plans for tile width 8 only (passes whose
+// wider tiles do not fit shared memory)
+#define PF_PID_CASE8(K_, ...)               \
+    case K_: {                              \
+        constexpr int PIDC = K_;            \
+        constexpr bool R16C = false;        \
+        constexpr int TXC = 8;              \
+        __VA_ARGS__;                        \
+    } break;
+#define PF_COL_SWITCH8(T_, plan, tx, ...)                                                         \
+    do {                                                                                          \
+        int pid_ = 0;                                                                             \
+        if (sizeof(T_) == 4 && (tx) == 8) pid_ = fixed_plan_id(plan);                             \
+        if constexpr (sizeof(T_) == 4) {                                                          \
+            switch (pid_) {                                                                       \
+                PF_PID_CASE8(1, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(2, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(3, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(4, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(5, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(6, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(7, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(8, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(9, __VA_ARGS__)                                                      \
+                PF_PID_CASE8(10, __VA_ARGS__)                                                     \
+                PF_PID_CASE8(11, __VA_ARGS__)                                                     \
+                default: break;                                                                   \
+            }                                                                                     \
+        }                                                                                         \
+        if (pid_ == 0) {                                                                          \
+            constexpr int PIDC = 0;                                                               \
+            PF_R16_SWITCH((plan).has16, PF_TX_SWITCH(tx, __VA_ARGS__));                            \
+        }                                                                                         \
+    } while (0)
+
 // compile-time tile width dispatch
 #define PF_TX_SWITCH(tx, ...)                 \
     switch (tx) {                             \

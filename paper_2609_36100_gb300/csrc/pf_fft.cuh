@@ -483,4 +483,152 @@ __device__ void fft_cols(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Plans compiled with a constant length and radix order (PID > 0), shared by
+// the line (x) and column (y, z) transforms; any other plan runs the generic
+// stages (PID 0).  The list holds the default plans of the grid sizes of the
+// workloads (FP32 plans prefer radix 16, FP64 plans radix 8).
+// ---------------------------------------------------------------------------
+template <int PID>
+struct FixedPlan {
+    static constexpr int N = 0;
+    using Rad = Radices<>;
+};
+#define PF_FIXED_PLAN(PID_, N_, ...)      \
+    template <>                           \
+    struct FixedPlan<PID_> {              \
+        static constexpr int N = N_;      \
+        using Rad = Radices<__VA_ARGS__>; \
+    };
+PF_FIXED_PLAN(1, 256, 16, 16)
+PF_FIXED_PLAN(2, 256, 8, 8, 4)
+PF_FIXED_PLAN(3, 128, 16, 8)
+PF_FIXED_PLAN(4, 128, 8, 4, 4)
+PF_FIXED_PLAN(5, 64, 16, 4)
+PF_FIXED_PLAN(6, 64, 8, 8)
+PF_FIXED_PLAN(7, 160, 8, 4, 5)
+PF_FIXED_PLAN(8, 96, 8, 4, 3)
+PF_FIXED_PLAN(9, 120, 8, 3, 5)
+PF_FIXED_PLAN(10, 192, 16, 4, 3)
+PF_FIXED_PLAN(11, 640, 16, 8, 5)
+#undef PF_FIXED_PLAN
+constexpr int kFixedPlans = 11;
+
+template <int... Rs>
+inline bool plan_is(const AxisPlan& p, int n, Radices<Rs...>) {
+    const int r[] = {Rs...};
+    if (p.n != n || p.nst != (int)sizeof...(Rs)) return false;
+    for (int s = 0; s < p.nst; ++s)
+        if (p.rad[s] != r[s]) return false;
+    return true;
+}
+
+// PID of a plan (0: not compiled)
+template <int PID = 1>
+inline int fixed_plan_id(const AxisPlan& p) {
+    if constexpr (PID > kFixedPlans) {
+        return 0;
+    } else {
+        if (plan_is(p, FixedPlan<PID>::N, typename FixedPlan<PID>::Rad{})) return PID;
+        return fixed_plan_id<PID + 1>(p);
+    }
+}
+
+// Column stage with compile-time length, radix and sub-transform size: the
+// same data movement as col_stage, with constant strides.
+template <int R, int SIGN, int TX, int N, int NS, bool FIRST, bool LAST, typename T2, class Src, class Dst>
+__device__ __forceinline__ void col_stage_fixed(const T2* __restrict__ in, T2* __restrict__ out,
+                                                const T2* __restrict__ tw, Src& src, Dst& dst) {
+    constexpr int M = N / R;
+    constexpr int TWS = N / (NS * R);
+    static_assert(M * R == N, "radix does not divide the length");
+    for (int idx = threadIdx.x; idx < TX * M; idx += blockDim.x) {
+        const int col = idx & (TX - 1);
+        const int j = idx / TX;
+        T2 v[R];
+        if constexpr (FIRST) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = src(j + t * M, col);
+        } else {
+            const T2* p = in + j * TX + col;
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = p[t * M * TX];
+        }
+        const int jq = j / NS, k = j - jq * NS;
+        if constexpr (NS > 1) {
+            const int st = k * TWS;
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                const T2 w = __ldg(tw + t * st);
+                v[t] = SIGN < 0 ? cmul(v[t], w) : cmulc(v[t], w);
+            }
+        }
+        Bfly<R, SIGN, T2>::run(v);
+        const int base = jq * NS * R + k;
+        if constexpr (LAST) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) dst(base + t * NS, col, v[t]);
+        } else {
+            T2* p = out + base * TX + col;
+#pragma unroll
+            for (int t = 0; t < R; ++t) p[t * NS * TX] = v[t];
+        }
+    }
+}
+
+template <int SIGN, int TX, int N, int NS, bool FIRST, typename T2, class Src, class Dst>
+__device__ __forceinline__ void cols_fixed_run(const T2*, T2*, T2*, const T2*, Src&, Dst&, Radices<>) {}
+
+// stages in order: stage 0 reads src (FIRST) or `in`, writes `out`; the
+// middle stages ping-pong between out and other; the last hands results to dst
+template <int SIGN, int TX, int N, int NS, bool FIRST, typename T2, class Src, class Dst, int R, int... Rest>
+__device__ __forceinline__ void cols_fixed_run(const T2* in, T2* out, T2* other, const T2* tw, Src& src, Dst& dst,
+                                               Radices<R, Rest...>) {
+    constexpr bool LAST = sizeof...(Rest) == 0;
+    col_stage_fixed<R, SIGN, TX, N, NS, FIRST, LAST>(in, out, tw, src, dst);
+    if constexpr (!LAST) {
+        __syncthreads();
+        cols_fixed_run<SIGN, TX, N, NS * R, false>(out, other, out, tw, src, dst, Radices<Rest...>{});
+    }
+}
+
+template <class Rad>
+struct RadInfo;
+template <int R, int... Rs>
+struct RadInfo<Radices<R, Rs...>> {
+    static constexpr int count = 1 + (int)sizeof...(Rs);
+    static constexpr int first = R;
+};
+
+// fft_cols with the compile-time plan PID (same contract)
+template <int SIGN, int TX, bool IN_PLACE, bool PRELOAD, int PID, typename T2, class Src, class Dst>
+__device__ void fft_cols_fixed(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
+    constexpr int N = FixedPlan<PID>::N;
+    using Rad = typename FixedPlan<PID>::Rad;
+    const T2* tw = twiddles<T2>(p);
+    if constexpr (PRELOAD) {
+        for (int e = threadIdx.x; e < TX * N; e += blockDim.x) P[e] = src(e / TX, e & (TX - 1));
+        __syncthreads();
+        auto none = [](int, int) -> T2 { return T2{}; };
+        cols_fixed_run<SIGN, TX, N, 1, false>(P, Q, P, tw, none, dst, Rad{});
+    } else if constexpr (IN_PLACE && RadInfo<Rad>::count == 1) {
+        auto toP = [&](int pos, int col, T2 v) { P[pos * TX + col] = v; };
+        col_stage_fixed<RadInfo<Rad>::first, SIGN, TX, N, 1, true, true>(P, P, tw, src, toP);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TX * N; e += blockDim.x) dst(e / TX, e & (TX - 1), P[e]);
+    } else {
+        cols_fixed_run<SIGN, TX, N, 1, true>(static_cast<const T2*>(nullptr), P, Q, tw, src, dst, Rad{});
+    }
+}
+
+// column transform with the compile-time plan PID, or the generic stages
+template <int SIGN, int TX, bool IN_PLACE, bool PRELOAD, bool R16, int PID, typename T2, class Src, class Dst>
+__device__ __forceinline__ void cols_fft(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
+    if constexpr (PID > 0)
+        fft_cols_fixed<SIGN, TX, IN_PLACE, PRELOAD, PID>(p, P, Q, src, dst);
+    else
+        fft_cols<SIGN, TX, IN_PLACE, PRELOAD, R16>(p, P, Q, src, dst);
+}
+
 }  // namespace pf

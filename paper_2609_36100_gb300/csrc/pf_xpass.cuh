@@ -51,54 +51,6 @@ struct Pt {
 template <typename T>
 __device__ __forceinline__ T hfun(T f) { return f * f * f * ((T)6 * f * f - (T)15 * f + (T)10); }
 
-// x-axis plans compiled with a constant length and radix order (PID > 0);
-// any other plan runs the generic kernel (PID 0).  The list holds the default
-// plans of the grid sizes of the workloads (FP32 plans prefer radix 16, FP64
-// plans radix 8).
-template <int PID>
-struct XPlan {
-    static constexpr int N = 0;
-    using Rad = Radices<>;
-};
-#define PF_XPLAN(PID_, N_, ...)                 \
-    template <>                                 \
-    struct XPlan<PID_> {                        \
-        static constexpr int N = N_;            \
-        using Rad = Radices<__VA_ARGS__>;       \
-    };
-PF_XPLAN(1, 256, 16, 16)
-PF_XPLAN(2, 256, 8, 8, 4)
-PF_XPLAN(3, 128, 16, 8)
-PF_XPLAN(4, 128, 8, 4, 4)
-PF_XPLAN(5, 64, 16, 4)
-PF_XPLAN(6, 64, 8, 8)
-PF_XPLAN(7, 160, 8, 4, 5)
-PF_XPLAN(8, 96, 8, 4, 3)
-PF_XPLAN(9, 120, 8, 3, 5)
-PF_XPLAN(10, 192, 16, 4, 3)
-PF_XPLAN(11, 640, 16, 8, 5)
-#undef PF_XPLAN
-constexpr int kXPlans = 11;
-
-template <int... Rs>
-inline bool plan_is(const AxisPlan& p, int n, Radices<Rs...>) {
-    const int r[] = {Rs...};
-    if (p.n != n || p.nst != (int)sizeof...(Rs)) return false;
-    for (int s = 0; s < p.nst; ++s)
-        if (p.rad[s] != r[s]) return false;
-    return true;
-}
-
-template <int PID = 1>
-inline int xplan_id(const AxisPlan& p) {
-    if constexpr (PID > kXPlans) {
-        return 0;
-    } else {
-        if (plan_is(p, XPlan<PID>::N, typename XPlan<PID>::Rad{})) return PID;
-        return xplan_id<PID + 1>(p);
-    }
-}
-
 // line length nx and half-spectrum length nx/2+1 along x, compile-time when
 // NX > 0, and the divisions by them
 template <int NX>
@@ -125,7 +77,7 @@ struct XLen {
 template <int SIGN, int PID, bool R16, typename T2>
 __device__ __forceinline__ T2* x_fft(T2* a, T2* b, const AxisPlan& p, int nl, int ls) {
     if constexpr (PID > 0)
-        return fft_fixed_run<SIGN, XPlan<PID>::N, 1>(a, b, nl, ls, twiddles<T2>(p), typename XPlan<PID>::Rad{});
+        return fft_fixed_run<SIGN, FixedPlan<PID>::N, 1>(a, b, nl, ls, twiddles<T2>(p), typename FixedPlan<PID>::Rad{});
     else
         return fft_lines<SIGN, false, 0, true, R16>(a, b, p, nl, 1, ls);
 }
@@ -189,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
     PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int NX = XPlan<PID>::N;
+    constexpr int NX = FixedPlan<PID>::N;
     const XLen<NX> L(g);
     const int nx = L.n;
     const int ls = skewed_len(nx);
@@ -417,7 +369,7 @@ void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void*
                                                      reinterpret_cast<T2*>(out), reinterpret_cast<T*>(R),          \
                                                      reinterpret_cast<const T*>(Rin), partials, rtol, atol, real_in, \
                                                      real_out, P)
-    switch (xplan_id(g.px)) {
+    switch (fixed_plan_id(g.px)) {
         case 1: PF_XLAUNCH(false, 1); break;
         case 2: PF_XLAUNCH(false, 2); break;
         case 3: PF_XLAUNCH(false, 3); break;

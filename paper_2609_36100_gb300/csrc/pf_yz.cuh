@@ -8,7 +8,7 @@ namespace pf {
 // ---------------------------------------------------------------------------
 // y pass: in-place complex FFT along y of nf fields
 // ---------------------------------------------------------------------------
-template <typename T, int SIGN, int TX, bool R16>
+template <typename T, int SIGN, int TX, bool R16, int PID>
 __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* __restrict__ buf) {
     PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* _
     auto dst = [&](int ky, int col, T2 v) {
         if (col < ncol) base[ky * ys + col] = v;
     };
-    fft_cols<SIGN, TX, true, false, R16>(g.py, A, B, src, dst);
+    cols_fft<SIGN, TX, true, false, R16, PID>(g.py, A, B, src, dst);
 }
 
 template <typename T>
@@ -33,11 +33,11 @@ void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
     const size_t sm = 2 * (size_t)TX * g.ny * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.nz, nf);
     if (sign > 0) {
-        PF_R16_SWITCH(g.py.has16, PF_TX_SWITCH(TX, set_smem(k_y_pass<T, 1, TXC, R16C>, sm);
-                     k_y_pass<T, 1, TXC, R16C><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf))))
+        PF_COL_SWITCH(T, g.py, TX, set_smem(k_y_pass<T, 1, TXC, R16C, PIDC>, sm);
+                      k_y_pass<T, 1, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf)));
     } else {
-        PF_R16_SWITCH(g.py.has16, PF_TX_SWITCH(TX, set_smem(k_y_pass<T, -1, TXC, R16C>, sm);
-                     k_y_pass<T, -1, TXC, R16C><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf))))
+        PF_COL_SWITCH(T, g.py, TX, set_smem(k_y_pass<T, -1, TXC, R16C, PIDC>, sm);
+                      k_y_pass<T, -1, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf)));
     }
 }
 
@@ -47,7 +47,7 @@ void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
 //   mode 1: f^E_X = -M k^2 q^/N, f^E_phi = -L g^/N -> compute type (stages)
 //   mode 2: same scaling -> FP64                                  (ABI f^E)
 // ---------------------------------------------------------------------------
-template <typename T, typename OT2, int TX, bool R16>
+template <typename T, typename OT2, int TX, bool R16, int PID>
 __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typename Cx<T>::t* __restrict__ W,
                                                     OT2* __restrict__ out, int mode) {
     PF_SKIP_INACTIVE(g);
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typena
             out[gi] = OT2{(OT)(v.x * sc), (OT)(v.y * sc)};
         }
     };
-    fft_cols<-1, TX, false, false, R16>(g.pz, A, B, src, dst);
+    cols_fft<-1, TX, false, false, R16, PID>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
@@ -90,18 +90,18 @@ void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int sc
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
     if (scale_mode == 1) {
-        PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, T2, TXC, R16C>, sm);
-                     k_z_fwd<T, T2, TXC, R16C><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
-                                                                          reinterpret_cast<T2*>(out), 1)))
+        PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_fwd<T, T2, TXC, R16C, PIDC>, sm);
+                      k_z_fwd<T, T2, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(
+                          g, ph, reinterpret_cast<const T2*>(W), reinterpret_cast<T2*>(out), 1));
     } else {
-        PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, double2, TXC, R16C>, sm);
-                     k_z_fwd<T, double2, TXC, R16C><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<const T2*>(W),
-                                                                               reinterpret_cast<double2*>(out),
-                                                                               scale_mode)))
+        constexpr int PIDC = 0;  // FP64 output (state in, ABI f^E): generic stages
+        PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_fwd<T, double2, TXC, R16C, PIDC>, sm);
+                     k_z_fwd<T, double2, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(
+                         g, ph, reinterpret_cast<const T2*>(W), reinterpret_cast<double2*>(out), scale_mode)))
     }
 }
 
-template <typename T, int TX, bool R16>
+template <typename T, int TX, bool R16, int PID>
 __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename Cx<T>::t* __restrict__ H) {
     PF_SKIP_INACTIVE(g);
     using T2 = typename Cx<T>::t;
@@ -116,19 +116,23 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
     const int ncol = min(TX, g.nxh - kx0);
     const long long rowoff = (long long)ky * g.nxh + kx0;
     const long long zs = (long long)g.ny * g.nxh;
-    const bool nst_even = (g.pz.nst % 2) == 0;
+    bool nst_even;
+    if constexpr (PID > 0)
+        nst_even = RadInfo<typename FixedPlan<PID>::Rad>::count % 2 == 0;
+    else
+        nst_even = (g.pz.nst % 2) == 0;
     // forward transforms: global -> field slot (middle stages ping-pong with E
     // so that the last stage reads E and writes the slot)
-#pragma unroll
+#pragma unroll 1
     for (int f = 0; f < 3; ++f) {
         T2* S = slot[f];
         const long long fb = (long long)f * g.NK + rowoff;
         auto src = [&](int kz, int col) -> T2 { return col < ncol ? H[fb + kz * zs + col] : T2{0, 0}; };
         auto dst = [&](int kz, int col, T2 v) { S[kz * TX + col] = v; };
         if (nst_even)
-            fft_cols<-1, TX, false, false, R16>(g.pz, E, S, src, dst);
+            cols_fft<-1, TX, false, false, R16, PID>(g.pz, E, S, src, dst);
         else
-            fft_cols<-1, TX, false, false, R16>(g.pz, S, E, src, dst);
+            cols_fft<-1, TX, false, false, R16, PID>(g.pz, S, E, src, dst);
         __syncthreads();
     }
     const T invN = std::is_same<T, float>::value ? (T)g.invN32 : (T)g.invN;
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
     __syncthreads();
     // inverse transforms: field slot -> global (stage 0 reads the slot and
     // writes E)
-#pragma unroll
+#pragma unroll 1
     for (int f = 0; f < 3; ++f) {
         T2* S = slot[f];
         const long long fb = (long long)f * g.NK + rowoff;
@@ -158,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
         auto dst = [&](int kz, int col, T2 v) {
             if (col < ncol) H[fb + kz * zs + col] = v;
         };
-        fft_cols<+1, TX, false, false, R16>(g.pz, E, S, src, dst);
+        cols_fft<+1, TX, false, false, R16, PID>(g.pz, E, S, src, dst);
         __syncthreads();
     }
 }
@@ -169,8 +173,8 @@ void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     const int TX = tuned_cols<T>(g, g.tx_el, g.nz, 4, 128 * 1024);
     const size_t sm = 4 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);
-    PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_elastic<T, TXC, R16C>, sm);
-                 k_z_elastic<T, TXC, R16C><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<T2*>(H))))
+    PF_COL_SWITCH8(T, g.pz, TX, set_smem(k_z_elastic<T, TXC, R16C, PIDC>, sm);
+                  k_z_elastic<T, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(g, ph, reinterpret_cast<T2*>(H)));
 }
 
 }  // namespace pf

@@ -27,9 +27,10 @@ namespace pf {
 // z pass: stage assembly + implicit solve + inverse FFT along z
 //   r = y + sum_j (dt A^I_ij) lambda z_j + (dt A^E_ij) f^E_j
 //   z_i = r / (1 - dt A^I_ii lambda)
-// The assembly is the first FFT stage's load: each element is formed once.
+// The tile is assembled in shared memory before the transform (every load of
+// an element issued together); each element is formed once.
 // ---------------------------------------------------------------------------
-template <typename T, int TX, bool R16>
+template <typename T, int TX, bool R16, int PID>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st,
                                                       double2* __restrict__ zout,
                                                       typename Cx<T>::t* __restrict__ W) {
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Ge
     auto dst = [&](int kz, int col, T2 v) {
         if (col < ncol) W[base + kz * zs + col] = v;
     };
-    fft_cols<+1, TX, false, true, R16>(g.pz, A, B, src, dst);
+    cols_fft<+1, TX, false, true, R16, PID>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
@@ -97,8 +98,9 @@ void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageT
     const int TX = tuned_cols<T>(g, g.tx_z, g.nz, 2, 128 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
-    PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_stage<T, TXC, R16C>, sm);
-                 k_z_stage<T, TXC, R16C><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout, reinterpret_cast<T2*>(W))))
+    PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_stage<T, TXC, R16C, PIDC>, sm);
+                  k_z_stage<T, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout,
+                                                                        reinterpret_cast<T2*>(W)));
 }
 
 // ---------------------------------------------------------------------------
@@ -106,7 +108,7 @@ void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageT
 //   y_n = y + sum_i (dt b^I_i) lambda z_i + (dt b^E_i) f^E_i
 //   LTE = sum_i (dt (b-bt)^I_i) lambda z_i + (dt (b-bt)^E_i) f^E_i
 // ---------------------------------------------------------------------------
-template <typename T, int TX, bool R16>
+template <typename T, int TX, bool R16, int PID>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_final(Geo g, Phys ph, const double2* __restrict__ y, StageTerms bt,
                                                       StageTerms dt, int want_lte, double2* __restrict__ ynew,
                                                       typename Cx<T>::t* __restrict__ W) {
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_final(Ge
     auto dst = [&](int kz, int col, T2 v) {
         if (col < ncol) W[base + kz * zs + col] = v;
     };
-    fft_cols<+1, TX, false, true, R16>(g.pz, A, B, combine, dst);
+    cols_fft<+1, TX, false, true, R16, PID>(g.pz, A, B, combine, dst);
 }
 
 template <typename T>
@@ -181,9 +183,9 @@ void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageT
     const int TX = tuned_cols<T>(g, g.tx_z, g.nz, 2, 128 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
-    PF_R16_SWITCH(g.pz.has16, PF_TX_SWITCH(TX, set_smem(k_z_final<T, TXC, R16C>, sm);
-                 k_z_final<T, TXC, R16C><<<grid, kThreads, sm, s>>>(g, ph, y, bterm, dterm, want_lte, ynew,
-                                                                    reinterpret_cast<T2*>(W))))
+    PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_final<T, TXC, R16C, PIDC>, sm);
+                  k_z_final<T, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(g, ph, y, bterm, dterm, want_lte, ynew,
+                                                                        reinterpret_cast<T2*>(W)));
 }
 
 }  // namespace pf
