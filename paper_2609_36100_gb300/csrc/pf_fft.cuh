@@ -403,18 +403,21 @@ __device__ __forceinline__ void col_stage(int n, int Ns, FastDiv dN, const T2* _
 }
 
 //
-// PRELOAD: every element is first formed by src into P by a plain loop over
-// the tile (one src inlined, its loads all independent and in flight
-// together), and the stages then run from shared memory.  For heavy
+// PRELOAD > 0: every element is first formed by src into P by a plain loop
+// over the tile, unrolled PRELOAD times (one src inlined, its loads all
+// independent and in flight together), and the stages then run from shared
+// memory.  For heavy
 // prologues (stage assembly from many global arrays) this keeps the memory
 // parallelism and the register count of the transform independent of the
 // prologue.
-template <int SIGN, int TX, bool IN_PLACE = false, bool PRELOAD = false, bool R16 = false, typename T2, class Src,
+template <int SIGN, int TX, bool IN_PLACE = false, int PRELOAD = 0, bool R16 = false, typename T2, class Src,
           class Dst>
 __device__ void fft_cols(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
     const T2* tw = twiddles<T2>(p);
     const int n = p.n;
-    if constexpr (PRELOAD) {
+    if constexpr (PRELOAD > 0) {
+        // unrolled PRELOAD times: the loads of several elements are in flight together
+#pragma unroll PRELOAD
         for (int e = threadIdx.x; e < TX * n; e += blockDim.x) P[e] = src(e / TX, e & (TX - 1));
         __syncthreads();
         auto none = [](int, int) -> T2 { return T2{}; };
@@ -602,12 +605,14 @@ struct RadInfo<Radices<R, Rs...>> {
 };
 
 // fft_cols with the compile-time plan PID (same contract)
-template <int SIGN, int TX, bool IN_PLACE, bool PRELOAD, int PID, typename T2, class Src, class Dst>
+template <int SIGN, int TX, bool IN_PLACE, int PRELOAD, int PID, typename T2, class Src, class Dst>
 __device__ void fft_cols_fixed(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
     constexpr int N = FixedPlan<PID>::N;
     using Rad = typename FixedPlan<PID>::Rad;
     const T2* tw = twiddles<T2>(p);
-    if constexpr (PRELOAD) {
+    if constexpr (PRELOAD > 0) {
+        // unrolled PRELOAD times: the loads of several elements are in flight together
+#pragma unroll PRELOAD
         for (int e = threadIdx.x; e < TX * N; e += blockDim.x) P[e] = src(e / TX, e & (TX - 1));
         __syncthreads();
         auto none = [](int, int) -> T2 { return T2{}; };
@@ -623,7 +628,7 @@ __device__ void fft_cols_fixed(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst
 }
 
 // column transform with the compile-time plan PID, or the generic stages
-template <int SIGN, int TX, bool IN_PLACE, bool PRELOAD, bool R16, int PID, typename T2, class Src, class Dst>
+template <int SIGN, int TX, bool IN_PLACE, int PRELOAD, bool R16, int PID, typename T2, class Src, class Dst>
 __device__ __forceinline__ void cols_fft(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
     if constexpr (PID > 0)
         fft_cols_fixed<SIGN, TX, IN_PLACE, PRELOAD, PID>(p, P, Q, src, dst);

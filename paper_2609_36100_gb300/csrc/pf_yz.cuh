@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* _
     auto dst = [&](int ky, int col, T2 v) {
         if (col < ncol) base[ky * ys + col] = v;
     };
-    cols_fft<SIGN, TX, true, false, R16, PID>(g.py, A, B, src, dst);
+    cols_fft<SIGN, TX, true, 0, R16, PID>(g.py, A, B, src, dst);
 }
 
 template <typename T>
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typena
             out[gi] = OT2{(OT)(v.x * sc), (OT)(v.y * sc)};
         }
     };
-    cols_fft<-1, TX, false, false, R16, PID>(g.pz, A, B, src, dst);
+    cols_fft<-1, TX, false, 0, R16, PID>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
@@ -130,9 +130,9 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
         auto src = [&](int kz, int col) -> T2 { return col < ncol ? H[fb + kz * zs + col] : T2{0, 0}; };
         auto dst = [&](int kz, int col, T2 v) { S[kz * TX + col] = v; };
         if (nst_even)
-            cols_fft<-1, TX, false, false, R16, PID>(g.pz, E, S, src, dst);
+            cols_fft<-1, TX, false, 0, R16, PID>(g.pz, E, S, src, dst);
         else
-            cols_fft<-1, TX, false, false, R16, PID>(g.pz, S, E, src, dst);
+            cols_fft<-1, TX, false, 0, R16, PID>(g.pz, S, E, src, dst);
         __syncthreads();
     }
     const T invN = std::is_same<T, float>::value ? (T)g.invN32 : (T)g.invN;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
         auto dst = [&](int kz, int col, T2 v) {
             if (col < ncol) H[fb + kz * zs + col] = v;
         };
-        cols_fft<+1, TX, false, false, R16, PID>(g.pz, E, S, src, dst);
+        cols_fft<+1, TX, false, 0, R16, PID>(g.pz, E, S, src, dst);
         __syncthreads();
     }
 }

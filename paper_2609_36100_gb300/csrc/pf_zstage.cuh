@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Ge
     auto dst = [&](int kz, int col, T2 v) {
         if (col < ncol) W[base + kz * zs + col] = v;
     };
-    cols_fft<+1, TX, false, true, R16, PID>(g.pz, A, B, src, dst);
+    cols_fft<+1, TX, false, 1, R16, PID>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_final(Ge
     auto dst = [&](int kz, int col, T2 v) {
         if (col < ncol) W[base + kz * zs + col] = v;
     };
-    cols_fft<+1, TX, false, true, R16, PID>(g.pz, A, B, combine, dst);
+    cols_fft<+1, TX, false, 1, R16, PID>(g.pz, A, B, combine, dst);
 }
 
 template <typename T>
