@@ -80,3 +80,51 @@ def test_radix_orders_match_oracle(pfg, params, prec, orders, tol):
         den = np.linalg.norm(ref[f]) or np.linalg.norm(ref)
         err = np.linalg.norm(got[f] - ref[f]) / den
         assert err <= tol, (f, err)
+
+
+@pytest.mark.parametrize("tx", [8, 16])
+def test_compiled_plans_match_oracle(pfg, params, tx):
+    """The kernels compiled for fixed lengths and radix orders (the FP32-bulk
+    defaults of the workload sizes: z 96 = 8*4*3, y 64 = 16*4, x 128 = 16*8,
+    and 256 = 16*16 along z in the second grid) against the oracle, for both
+    tile widths that have compiled variants."""
+    import oracle
+    for shape in [(96, 64, 128), (256, 16, 32)]:
+        nz, ny, nx = shape
+        rng = np.random.default_rng(7)
+        nuc = synth.draw_nuclei(shape, 6, rng, lambda r, v: (3.5, 3.5, 3.5))
+        y0 = synth.nuclei_ic(shape, params, nuc, x_inside=params["B_v"])
+        m = oracle.Model(shape, params)
+        ref, _, _ = oracle.ark_step(m, m.to_k(y0), 0.5, oracle.ark436l2sa())
+        with pfg.Simulation(shape, params, "ark4", "fp32bulk") as s:
+            cfg = s.tuning()
+            cfg[0], cfg[1], cfg[2] = tx, tx, 8  # z, y and elastic tile widths
+            s.set_tuning(cfg)
+            s.set_state(y0)
+            s.step(0.5)
+            got = s.state_hat().cpu().numpy()
+        for f in range(4):
+            den = np.linalg.norm(ref[f]) or np.linalg.norm(ref)
+            err = np.linalg.norm(got[f] - ref[f]) / den
+            assert err <= 1e-5, (shape, f, err)
+
+
+def test_compiled_x_plans_fp64_match_oracle(pfg, params):
+    """FP64 x passes with the compiled radix-8 plans (256 = 8*8*4, 128 =
+    8*4*4, 160 = 8*4*5) against the oracle at the FP64 bar."""
+    import oracle
+    for nx in (256, 128, 160):
+        shape = (12, 16, nx)
+        rng = np.random.default_rng(nx)
+        nuc = synth.draw_nuclei(shape, 3, rng, lambda r, v: (3.0, 3.0, 3.0))
+        y0 = synth.nuclei_ic(shape, params, nuc, x_inside=params["B_v"])
+        m = oracle.Model(shape, params)
+        ref, _, _ = oracle.ark_step(m, m.to_k(y0), 0.5, oracle.ark436l2sa())
+        with pfg.Simulation(shape, params, "ark4", "fp64") as s:
+            s.set_state(y0)
+            s.step(0.5)
+            got = s.state_hat().cpu().numpy()
+        for f in range(4):
+            den = np.linalg.norm(ref[f]) or np.linalg.norm(ref)
+            err = np.linalg.norm(got[f] - ref[f]) / den
+            assert err <= 1e-11, (shape, f, err)
