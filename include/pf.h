@@ -204,11 +204,12 @@ int pf_profile_enable(pf_ctx* ctx, int on);
 int pf_profile_read(pf_ctx* ctx, double* ms, double* bytes, long long* launches);
 const char* pf_kernel_name(int kind);
 
-/* Launch schedule of a context: tuned tile widths of the z / y / elastic
- * passes, rows per CTA of the x passes (0 = built-in heuristic), and the
- * radix order of each axis (count + up to 10 radices in {2,3,4,5,8,16}, for x,
- * y, z).  PF_TUNE_LEN ints. */
-#define PF_TUNE_LEN 37
+/* Launch schedule of a context: tuned tile widths of the z stage-assembly
+ * and completion / y / elastic passes, rows per CTA of the x passes (0 =
+ * built-in heuristic), the radix order of each axis (count + up to 10 radices
+ * in {2,3,4,5,8,16}, for x, y, z: ints 4-36), and the tile width of the
+ * forward z pass (int 37).  PF_TUNE_LEN ints. */
+#define PF_TUNE_LEN 38
 int pf_get_tuning(pf_ctx* ctx, int* cfg, int n);
 int pf_set_tuning(pf_ctx* ctx, const int* cfg, int n);
 /* Autotuner: times `reps` step attempts per candidate schedule on the

@@ -102,7 +102,7 @@ SIGNATURES = {
                                     C.POINTER(C.c_double)]),
 }
 NKERNELS = 10
-TUNE_LEN = 37
+TUNE_LEN = 38
 _DPTR_ARGS = {"pf_method_tableau"}
 
 _lib = None

@@ -1280,6 +1280,7 @@ int pf_get_tuning(pf_ctx* c, int* cfg, int n) {
     cfg[1] = c->g.tx_y;
     cfg[2] = c->g.tx_el;
     cfg[3] = c->g.rp;
+    cfg[37] = c->g.tx_zf;
     plan_to_cfg(c->g.px, cfg + 4);
     plan_to_cfg(c->g.py, cfg + 4 + 11);
     plan_to_cfg(c->g.pz, cfg + 4 + 22);
@@ -1293,6 +1294,7 @@ int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
     g.tx_y = cfg[1];
     g.tx_el = cfg[2];
     g.rp = cfg[3];
+    g.tx_zf = cfg[37];
     AxisPlan* pl[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
@@ -1395,7 +1397,7 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
         pf_set_tuning(c, best, PF_TUNE_LEN);
     };
     for (int sweep = 0; sweep < 2; ++sweep) {
-        for (int slot = 0; slot < 4; ++slot) {
+        for (int slot : {0, 1, 2, 3, 37}) {
             const int cands[5] = {1, 2, 4, 8, 16};
             for (int v : cands) {
                 std::memcpy(cfg, best, sizeof cfg);

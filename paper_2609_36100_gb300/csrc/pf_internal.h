@@ -51,6 +51,7 @@ struct Geo {
     double2* yother;           // y_new buffer) and y_new goes to the context's y buffer
     int tx_y, tx_z, tx_el;  // tuned tile widths (kx columns) of the strided passes, 0 = heuristic
     int rp;                  // tuned row pairs per CTA in the x passes, 0 = heuristic
+    int tx_zf;               // tuned tile width of the forward z pass, 0 = heuristic
 };
 
 // Model constants of the real-space and elastic terms in one compute type,

@@ -30,7 +30,10 @@ template <typename T>
 void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
     const int TX = tuned_cols<T>(g, g.tx_y, g.ny, 2, 128 * 1024);
-    const size_t sm = 2 * (size_t)TX * g.ny * sizeof(T2);
+    // a transform of at most two stages never touches its second buffer
+    // (stage 0 reads global, the last stage writes global): half the shared
+    // memory, more CTAs per SM
+    const size_t sm = (g.py.nst <= 2 ? 1 : 2) * (size_t)TX * g.ny * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.nz, nf);
     if (sign > 0) {
         PF_COL_SWITCH(T, g.py, TX, set_smem(k_y_pass<T, 1, TXC, R16C, PIDC>, sm);
@@ -86,8 +89,8 @@ __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typena
 template <typename T>
 void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int scale_mode, cudaStream_t s, int nf) {
     using T2 = typename Cx<T>::t;
-    const int TX = tuned_cols<T>(g, g.tx_z, g.nz, 2, 128 * 1024);
-    const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
+    const int TX = tuned_cols<T>(g, g.tx_zf, g.nz, 2, 128 * 1024);
+    const size_t sm = (g.pz.nst <= 2 ? 1 : 2) * (size_t)TX * g.nz * sizeof(T2);  // as in the y pass
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
     if (scale_mode == 1) {
         PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_fwd<T, T2, TXC, R16C, PIDC>, sm);

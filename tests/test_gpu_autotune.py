@@ -98,7 +98,7 @@ def test_compiled_plans_match_oracle(pfg, params, tx):
         ref, _, _ = oracle.ark_step(m, m.to_k(y0), 0.5, oracle.ark436l2sa())
         with pfg.Simulation(shape, params, "ark4", "fp32bulk") as s:
             cfg = s.tuning()
-            cfg[0], cfg[1], cfg[2] = tx, tx, 8  # z, y and elastic tile widths
+            cfg[0], cfg[1], cfg[2], cfg[37] = tx, tx, 8, tx  # z, y, elastic and forward-z tile widths
             s.set_tuning(cfg)
             s.set_state(y0)
             s.step(0.5)
