@@ -1110,14 +1110,20 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
             e = cudaMemcpy(d_hif, hif.data(), sizeof(cudaGraphConditionalHandle) * n, cudaMemcpyHostToDevice);
         cudaGraphNode_t gate{};
         if (e == cudaSuccess) e = add_batch_gate_node(&gate, body, d_ctl, d_hif, n);
+        // members large enough to fill the GPU alone run one after another;
+        // smaller ones run as independent branches beside them
+        const long long kFillsGpu = 1LL << 21;  // grid points (128^3)
         std::vector<cudaGraphNode_t> ifn(n);
+        cudaGraphNode_t prev_large = gate;
         for (int m = 0; m < n && e == cudaSuccess; ++m) {
             cudaGraphNodeParams ip{};
             ip.type = cudaGraphNodeTypeConditional;
             ip.conditional.handle = hif[m];
             ip.conditional.type = cudaGraphCondTypeIf;
             ip.conditional.size = 1;
-            e = cudaGraphAddNode(&ifn[m], body, &gate, nullptr, 1, &ip);
+            const bool large = ctxs[m]->g.N >= kFillsGpu;
+            e = cudaGraphAddNode(&ifn[m], body, large ? &prev_large : &gate, nullptr, 1, &ip);
+            if (large) prev_large = ifn[m];
             cudaGraphNode_t child{};
             if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, ip.conditional.phGraph_out[0], nullptr, 0, graphs[m]);
         }
