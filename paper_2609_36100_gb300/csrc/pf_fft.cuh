@@ -253,6 +253,36 @@ __device__ __forceinline__ void fft_stage(const T2* __restrict__ src, T2* __rest
 template <int... Rs>
 struct Radices {};
 
+// v[t] *= w^t (SIGN < 0) or conj(w)^t, w = tw[st], t = 1..R-1.  FP32 radix-8
+// and radix-16 stages load w, w^2, w^4 (and w^8) from the table and form the
+// other powers by at most three complex products (a few ulp, against the
+// ulp-level rounding of the table itself), trading up to 11 dependent L1
+// loads per butterfly for FMAs; FP64 stages (whose FMA pipe is the narrow
+// one) load every power.
+template <int R, int SIGN, typename T2>
+__device__ __forceinline__ void apply_twiddles(T2* v, const T2* __restrict__ tw, int st) {
+    T2 w[R];
+    if constexpr (sizeof(T2) == 8 && (R == 8 || R == 16)) {
+        w[1] = __ldg(tw + st);
+        w[2] = __ldg(tw + 2 * st);
+        w[4] = __ldg(tw + 4 * st);
+        w[3] = cmul(w[2], w[1]);
+        w[5] = cmul(w[4], w[1]);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+        if constexpr (R == 16) {
+            w[8] = __ldg(tw + 8 * st);
+#pragma unroll
+            for (int t = 9; t < 16; ++t) w[t] = cmul(w[8], w[t - 8]);
+        }
+    } else {
+#pragma unroll
+        for (int t = 1; t < R; ++t) w[t] = __ldg(tw + t * st);
+    }
+#pragma unroll
+    for (int t = 1; t < R; ++t) v[t] = SIGN < 0 ? cmul(v[t], w[t]) : cmulc(v[t], w[t]);
+}
+
 template <int R, int SIGN, int N, int NS, typename T2>
 __device__ __forceinline__ void fft_stage_fixed(const T2* __restrict__ src, T2* __restrict__ dst, int nl, int ls,
                                                 const T2* __restrict__ tw) {
@@ -275,12 +305,7 @@ __device__ __forceinline__ void fft_stage_fixed(const T2* __restrict__ src, T2* 
         }
         const int jq = j / NS, k = j - jq * NS;
         if constexpr (NS > 1) {
-            const int st = k * TWS;
-#pragma unroll
-            for (int t = 1; t < R; ++t) {
-                const T2 w = __ldg(tw + t * st);
-                v[t] = SIGN < 0 ? cmul(v[t], w) : cmulc(v[t], w);
-            }
+            apply_twiddles<R, SIGN>(v, tw, k * TWS);
         }
         Bfly<R, SIGN, T2>::run(v);
         T2* d = dst + line * ls;
@@ -560,12 +585,7 @@ __device__ __forceinline__ void col_stage_fixed(const T2* __restrict__ in, T2* _
         }
         const int jq = j / NS, k = j - jq * NS;
         if constexpr (NS > 1) {
-            const int st = k * TWS;
-#pragma unroll
-            for (int t = 1; t < R; ++t) {
-                const T2 w = __ldg(tw + t * st);
-                v[t] = SIGN < 0 ? cmul(v[t], w) : cmulc(v[t], w);
-            }
+            apply_twiddles<R, SIGN>(v, tw, k * TWS);
         }
         Bfly<R, SIGN, T2>::run(v);
         const int base = jq * NS * R + k;
