@@ -412,6 +412,7 @@ static void set_smem(K kern, size_t bytes) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ DF df_one_minus(DF c, DF lam) { return df_add(DF{1.f, 0.f}, df_mul(DF{-c.h, -c.l}, lam)); }
 
+template <int MAXT = kMaxStages>  // at most MAXT earlier-stage terms (compile-time bound: fewer registers)
 __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms& st, const double2* __restrict__ y,
                                                  long long gi, float4* __restrict__ zout) {
     // every load first (independent, all in flight together), then the sums
@@ -421,10 +422,10 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
     const float2 lt = need_lam ? __ldg(g.lamdf + gi) : make_float2(0.f, 0.f);
     const float2 qt = load_q ? __ldg(reinterpret_cast<const float2*>(st.qin) + gi) : make_float2(1.f, 0.f);
     const unsigned mz = st.mI & ~st.mY;
-    float4 zv[kMaxStages];
-    float2 fv[kMaxStages];
+    float4 zv[MAXT > 0 ? MAXT : 1];
+    float2 fv[MAXT > 0 ? MAXT : 1];
 #pragma unroll
-    for (int j = 0; j < kMaxStages; ++j) {
+    for (int j = 0; j < MAXT; ++j) {
         zv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         fv[j] = make_float2(0.f, 0.f);
         if (j < st.n) {
@@ -435,7 +436,7 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
     const DF yx = df_from_d(yv.x), yy = df_from_d(yv.y);
     DFAcc I, E;
 #pragma unroll
-    for (int j = 0; j < kMaxStages; ++j) {
+    for (int j = 0; j < MAXT; ++j) {
         if (j < st.n) {
             if ((st.mI >> j) & 1u) {
                 const float ch = cIh_of(st, j), cl = cIl_of(st, j);

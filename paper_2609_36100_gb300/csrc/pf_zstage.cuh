@@ -30,7 +30,7 @@ namespace pf {
 // The tile is assembled in shared memory before the transform (every load of
 // an element issued together); each element is formed once.
 // ---------------------------------------------------------------------------
-template <typename T, int TX, bool R16, int PID>
+template <typename T, int TX, bool R16, int PID, int MAXT>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Geo g, Phys ph, const double2* __restrict__ y, StageTerms st,
                                                       double2* __restrict__ zout,
                                                       typename Cx<T>::t* __restrict__ W) {
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Ge
         if (col >= ncol) return T2{0, 0};
         const long long gi = base + kz * zs + col;
         if constexpr (sizeof(T) == 4) {
-            return stage_value_df(g, st, y, gi, reinterpret_cast<float4*>(zout));
+            return stage_value_df<MAXT>(g, st, y, gi, reinterpret_cast<float4*>(zout));
         } else {
         // every load first (independent, all in flight together), then the sums
         const double2 yv = __ldg(y + gi);
@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Ge
     auto dst = [&](int kz, int col, T2 v) {
         if (col < ncol) W[base + kz * zs + col] = v;
     };
-    cols_fft<+1, TX, false, 1, R16, PID>(g.pz, A, B, src, dst);
+    // few terms: few registers per element, so several elements' loads go out together
+    cols_fft<+1, TX, false, (MAXT == 0 ? 4 : (MAXT <= 2 ? 2 : 1)), R16, PID>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
@@ -98,9 +99,24 @@ void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageT
     const int TX = tuned_cols<T>(g, g.tx_z, g.nz, 2, 128 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
-    PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_stage<T, TXC, R16C, PIDC>, sm);
-                  k_z_stage<T, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout,
-                                                                        reinterpret_cast<T2*>(W)));
+    // FP32-bulk stages with no or few earlier terms run kernels compiled for
+    // that bound (the first stages of a step)
+    auto go = [&](auto bound) {
+        constexpr int MT = decltype(bound)::value;
+        PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_stage<T, TXC, R16C, PIDC, MT>, sm);
+                      k_z_stage<T, TXC, R16C, PIDC, MT><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout,
+                                                                                 reinterpret_cast<T2*>(W)));
+    };
+    if constexpr (sizeof(T) == 4) {
+        if (st.n == 0)
+            go(std::integral_constant<int, 0>{});
+        else if (st.n <= 2)
+            go(std::integral_constant<int, 2>{});
+        else
+            go(std::integral_constant<int, kMaxStages>{});
+    } else {
+        go(std::integral_constant<int, kMaxStages>{});
+    }
 }
 
 // ---------------------------------------------------------------------------
