@@ -82,6 +82,49 @@ __device__ __forceinline__ T2* x_fft(T2* a, T2* b, const AxisPlan& p, int nl, in
         return fft_lines<SIGN, false, 0, true, R16>(a, b, p, nl, 1, ls);
 }
 
+// asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes; the data
+// never passes through registers, so a thread can have any number in flight
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// load F packed lines (C2R input) of row pairs [rp0, rp0+P) into S: the raw
+// half-spectrum rows are first copied asynchronously into `raw` (all of a
+// tile's loads in flight together), then packed from shared memory
+template <int NX, typename T2>
+__device__ __forceinline__ void c2r_load_async(const Geo& g, const T2* __restrict__ in, int F, int P, int rp0,
+                                               int npairs, T2* S, int ls, T2* raw) {
+    const XLen<NX> L(g);
+    const int nx = L.n, nh = nx / 2, nxh = L.h;
+    for (int e = threadIdx.x; e < P * F * 2 * nxh; e += blockDim.x) {
+        const int r = L.divh(e), k = e - r * nxh;  // raw row r = (rp F + f) 2 + (0: row y, 1: row y+1)
+        const int pf = r >> 1, rp = F == 4 ? pf >> 2 : pf / 3, f = pf - rp * F;
+        if (rp0 + rp < npairs)
+            cp_async<sizeof(T2)>(raw + e, in + (long long)f * g.NK + (2LL * (rp0 + rp) + (r & 1)) * nxh + k);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int e = threadIdx.x; e < P * F * nx; e += blockDim.x) {
+        const int line = L.divn(e), x = e - line * nx, rp = F == 4 ? line >> 2 : line / 3;
+        T2 Z = T2{0, 0};
+        if (rp0 + rp < npairs) {
+            const int k = x <= nh ? x : nx - x;
+            T2 a = raw[(2 * line) * nxh + k], b = raw[(2 * line + 1) * nxh + k];
+            if (k == 0 || k == nh) {
+                a.y = 0;
+                b.y = 0;
+            }
+            Z = x <= nh ? T2{a.x - b.y, a.y + b.x} : T2{a.x + b.y, b.x - a.y};
+        }
+        S[line * ls + skew<true>(x)] = Z;
+    }
+}
+
 // load F packed lines (C2R input) of row pairs [rp0, rp0+P) into S
 template <int NX, typename T2>
 __device__ __forceinline__ void c2r_load(const Geo& g, const T2* __restrict__ in, int F, int P, int rp0, int npairs,
@@ -175,7 +218,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
         return;
     }
     if (Fin > 0) {
-        c2r_load<NX>(g, in, Fin, P, rp0, npairs, S0, ls);
+        // the raw rows of the F fields fit in the second buffer (F (nx + 2) <= 4 ls) for every nx >= 32
+        if ((long long)Fin * 2 * L.h <= 4LL * ls)
+            c2r_load_async<NX>(g, in, Fin, P, rp0, npairs, S0, ls, S1);
+        else
+            c2r_load<NX>(g, in, Fin, P, rp0, npairs, S0, ls);
         __syncthreads();
         RS = x_fft<+1, PID, R16>(S0, S1, g.px, Fin * P, ls);
     }
