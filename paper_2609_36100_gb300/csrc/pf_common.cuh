@@ -300,6 +300,17 @@ static void set_smem(K kern, size_t bytes) {
         __VA_ARGS__;                   \
     }
 
+// asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes; the data
+// never passes through registers, so a thread can have any number in flight
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Launch dispatch of a column pass over the tile width (TXC), the radix-16
 // flag (R16C) and the compiled plan (PIDC): FP32 kernels with tile widths 8
 // or 16 run the compile-time plan when the axis plan is one of the compiled

@@ -82,17 +82,6 @@ __device__ __forceinline__ T2* x_fft(T2* a, T2* b, const AxisPlan& p, int nl, in
         return fft_lines<SIGN, false, 0, true, R16>(a, b, p, nl, 1, ls);
 }
 
-// asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes; the data
-// never passes through registers, so a thread can have any number in flight
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem), "n"(BYTES));
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 // load F packed lines (C2R input) of row pairs [rp0, rp0+P) into S: the raw
 // half-spectrum rows are first copied asynchronously into `raw` (all of a
 // tile's loads in flight together), then packed from shared memory
