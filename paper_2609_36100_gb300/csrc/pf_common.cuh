@@ -483,7 +483,7 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
 // FP32-bulk step completion (double-float):
 //   y_n = y + [lambda sum_j (dt b^I_j) z_j + sum_j (dt b^E_j) f^E_j]
 // with the bracket rounded to FP64 once and added to the FP64 state; returns
-// fl32 of the local error estimate (the same sums with dt (b - bt)).
+// the local error estimate (the same sums with dt (b - bt)) in FP32.
 __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms& bt, const StageTerms& dt,
                                                  int want_lte, const double2* __restrict__ y, long long gi,
                                                  double2* __restrict__ ynew) {
@@ -508,7 +508,10 @@ __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms&
         yx = df_from_d(yv.x);
         yy = df_from_d(yv.y);
     }
-    DFAcc Ib, Eb, Id, Ed;
+    // y_n in double-float; the local error estimate (an estimate, transformed
+    // and normed in FP32 next) in plain FP32 from the leading words
+    DFAcc Ib, Eb;
+    float dIx = 0.f, dIy = 0.f, dEx = 0.f, dEy = 0.f;
 #pragma unroll
     for (int j = 0; j < kMaxStages; ++j) {
         if (j < bt.n) {
@@ -521,17 +524,22 @@ __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms&
                     zy = DF{zv[j].y, zv[j].w};
                 }
                 if (bI) Ib.add(cIh_of(bt, j), cIl_of(bt, j), zx, zy);
-                if (lI) Id.add(cIh_of(dt, j), cIl_of(dt, j), zx, zy);
+                if (lI) {
+                    dIx = __fmaf_rn(cIh_of(dt, j), zx.h, dIx);
+                    dIy = __fmaf_rn(cIh_of(dt, j), zy.h, dIy);
+                }
             }
             if (bE) Eb.add(cEh_of(bt, j), cEl_of(bt, j), fv[j]);
-            if (lE) Ed.add(cEh_of(dt, j), cEl_of(dt, j), fv[j]);
+            if (lE) {
+                dEx = __fmaf_rn(cEh_of(dt, j), fv[j].x, dEx);
+                dEy = __fmaf_rn(cEh_of(dt, j), fv[j].y, dEy);
+            }
         }
     }
     const DF lam{lt.x, lt.y};
     const DF dx = df_add(df_mul(lam, Ib.x()), Eb.x()), dy = df_add(df_mul(lam, Ib.y()), Eb.y());
     ynew[gi] = make_double2(yv.x + df_to_d(dx), yv.y + df_to_d(dy));
-    const DF lx = df_add(df_mul(lam, Id.x()), Ed.x()), ly = df_add(df_mul(lam, Id.y()), Ed.y());
-    return make_float2(lx.h, ly.h);
+    return make_float2(__fmaf_rn(lam.h, dIx, dEx), __fmaf_rn(lam.h, dIy, dEy));
 }
 
 // ---------------------------------------------------------------------------
