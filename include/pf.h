@@ -185,7 +185,7 @@ int pf_get_attempts(pf_ctx* ctx, double* buf, int max_attempts);
 /* Kernel profiler: CUDA events around every launch of the step driver on the
  * context's stream, with the algorithmic bytes of each launch (each field read
  * or written once per pass as the method requires).  Kernel kinds: */
-#define PF_K_Z_STAGE 0    /* stage assembly + implicit solve + inverse z FFT   */
+#define PF_K_Z_STAGE 0    /* stage assembly + implicit solve (+ inverse z FFT in FP64) */
 #define PF_K_Y 1          /* y FFT (either direction)                           */
 #define PF_K_X_PHYS1 2    /* C2R x + real-space physics (h or full RHS) + R2C  */
 #define PF_K_X_PHYS2 3    /* C2R x of e_v + KKS/barrier RHS + R2C              */
@@ -195,7 +195,8 @@ int pf_get_attempts(pf_ctx* ctx, double* buf, int max_attempts);
 #define PF_K_X_WRMS 7     /* C2R x of the error + WRMS partial sums             */
 #define PF_K_REDUCE 8     /* deterministic WRMS reduction                       */
 #define PF_K_POINTWISE 9  /* stage assembly without a RHS evaluation            */
-#define PF_NKERNELS 10
+#define PF_K_Z_IFFT 10    /* inverse z FFT of an assembled stage (FP32-bulk)    */
+#define PF_NKERNELS 11
 /* Turn the profiler on/off (clears pending records). */
 int pf_profile_enable(pf_ctx* ctx, int on);
 /* Synchronise and return, per kind, the summed event time (ms), algorithmic

@@ -101,7 +101,7 @@ SIGNATURES = {
     "pf_surrogate_step": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int),
                                     C.POINTER(C.c_double)]),
 }
-NKERNELS = 10
+NKERNELS = 11
 TUNE_LEN = 38
 _DPTR_ARGS = {"pf_method_tableau"}
 

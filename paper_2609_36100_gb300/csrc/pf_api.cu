@@ -420,7 +420,18 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef 
             continue;
         }
         void* Ri = (i == 0) ? c->R1 : c->R;
-        {
+        if constexpr (sizeof(T) == 4) {
+            // FP32-bulk: streaming double-float assembly, then the inverse z
+            // transform as a plain in-place pass
+            {
+                ProfScope p(c, PF_K_Z_STAGE, 4 * NK * (16.0 + terms + (zout ? 16.0 : 0.0) + cb));
+                launch_stage_assemble(g, c->y, st, zout, c->W, s);
+            }
+            {
+                ProfScope p(c, PF_K_Z_IFFT, 4 * NK * 2 * cb);
+                launch_z_pass<T>(g, c->W, 4, +1, s);
+            }
+        } else {
             ProfScope p(c, PF_K_Z_STAGE, 4 * NK * (16.0 + terms + (zout ? 16.0 : 0.0) + cb));
             launch_z_stage<T>(g, ph, c->y, st, zout, c->W, s);
         }
@@ -559,7 +570,12 @@ int rhs_explicit_t(pf_ctx* c, const double2* yh, double2* out) {
     const Phys& ph = c->ph;
     cudaStream_t s = c->stream;
     StageTerms none{};
-    launch_z_stage<T>(g, ph, yh, none, nullptr, c->W, s);
+    if constexpr (sizeof(T) == 4) {
+        launch_stage_assemble(g, yh, none, nullptr, c->W, s);
+        launch_z_pass<T>(g, c->W, 4, +1, s);
+    } else {
+        launch_z_stage<T>(g, ph, yh, none, nullptr, c->W, s);
+    }
     launch_y_pass<T>(g, c->W, 4, +1, s);
     if (ph.elastic) {
         launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->H, c->R, nullptr, nullptr, 0, 0, nullptr, nullptr, s);
@@ -1430,7 +1446,7 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
 static const char* kKernelNames[PF_NKERNELS] = {"z_stage_solve_ifft", "y_fft", "x_c2r_physics1_r2c",
                                                  "x_c2r_physics2_r2c", "z_elastic_contraction", "z_fft_scale_fE",
                                                  "z_step_completion_lte", "x_c2r_wrms", "wrms_reduce",
-                                                 "stage_pointwise"};
+                                                 "stage_pointwise", "z_ifft"};
 
 const char* pf_kernel_name(int kind) { return (kind >= 0 && kind < PF_NKERNELS) ? kKernelNames[kind] : "?"; }
 

@@ -175,6 +175,13 @@ void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, cons
                             double2* zout, cudaStream_t s);
 void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s);
 void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamdf, cudaStream_t s);
+// FP32-bulk stage assembly as a streaming pass (double-float z_i out, FP32
+// transform input W out); the inverse z transform follows as launch_z_pass
+void launch_stage_assemble(const Geo& g, const double2* y, const StageTerms& st, double2* zout, void* W,
+                           cudaStream_t s);
+// in-place FFT along z of nf fields (sign +1 inverse)
+template <typename T>
+void launch_z_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s);
 // batch round: coefficients from the member's step, controller, accepted-state copy
 void launch_batch_prep(const BatchConst& bc, MemberCtl* ctl, StageCoefDev* coef, cudaStream_t s);
 void launch_batch_ctl(const BatchConst& bc, MemberCtl* ctl, const double* wrms_sum, double scale, cudaStream_t s);

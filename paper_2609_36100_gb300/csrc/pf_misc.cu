@@ -49,6 +49,60 @@ __global__ void k_stage_pointwise_df(Geo g, const double2* __restrict__ y, Stage
         stage_value_df(g, st, y, gi, zout);
 }
 
+// FP32-bulk stage assembly, streaming: each element's loads all issued
+// together (U elements per iteration for stages with few earlier terms), the
+// double-float stage value z_i and its FP32 rounding (the input of the inverse
+// z transform) written back.  Every array is read or written once.
+template <int MAXT, int U>
+__global__ void __launch_bounds__(256) k_stage_assemble_df(Geo g, const double2* __restrict__ y, StageTerms st,
+                                                           float4* __restrict__ zout, float2* __restrict__ W) {
+    PF_SKIP_INACTIVE(g);
+    if (y_swapped(g)) y = g.yother;
+    const long long total = 4LL * g.NK;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total; gi += stride * U) {
+        float2 r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (gi + u * stride < total) r[u] = stage_value_df<MAXT>(g, st, y, gi + u * stride, zout);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (gi + u * stride < total) W[gi + u * stride] = r[u];
+    }
+}
+
+// one wave of CTAs: every CTA resident at once, the grid-stride loop
+// spreading the elements evenly (no partial last wave)
+template <typename K>
+static int resident_blocks(K kern, int threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    return (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+}
+
+template <int MAXT, int U>
+static void assemble(const Geo& g, const double2* y, const StageTerms& st, float4* z, float2* w, cudaStream_t s) {
+    static int blocks = 0;  // per process: one device type
+    if (blocks == 0) blocks = resident_blocks(k_stage_assemble_df<MAXT, U>, 256);
+    k_stage_assemble_df<MAXT, U><<<blocks, 256, 0, s>>>(g, y, st, z, w);
+}
+
+void launch_stage_assemble(const Geo& g, const double2* y, const StageTerms& st, double2* zout, void* W,
+                           cudaStream_t s) {
+    float4* z = reinterpret_cast<float4*>(zout);
+    float2* w = reinterpret_cast<float2*>(W);
+    if (st.n == 0)
+        assemble<0, 4>(g, y, st, z, w, s);
+    else if (st.n <= 2)
+        assemble<2, 2>(g, y, st, z, w, s);
+    else if (st.n <= 5)
+        assemble<5, 1>(g, y, st, z, w, s);
+    else
+        assemble<kMaxStages, 1>(g, y, st, z, w, s);
+}
+
 void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, int fe_is_f32,
                             double2* zout, cudaStream_t s) {
     if (fe_is_f32)

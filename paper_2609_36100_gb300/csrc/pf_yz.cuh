@@ -45,6 +45,43 @@ void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// z pass: in-place FFT along z of nf fields (the inverse transform of an
+// assembled FP32-bulk stage)
+// ---------------------------------------------------------------------------
+template <typename T, int SIGN, int TX, bool R16, int PID>
+__global__ void __launch_bounds__(kThreads) k_z_pass(Geo g, typename Cx<T>::t* __restrict__ buf) {
+    PF_SKIP_INACTIVE(g);
+    using T2 = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* A = reinterpret_cast<T2*>(smraw);
+    T2* B = A + TX * g.nz;
+    const int f = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    const int ncol = min(TX, g.nxh - kx0);
+    T2* base = buf + (long long)f * g.NK + (long long)ky * g.nxh + kx0;
+    const long long zs = (long long)g.ny * g.nxh;
+    auto src = [&](int kz, int col) -> T2 { return col < ncol ? base[kz * zs + col] : T2{0, 0}; };
+    auto dst = [&](int kz, int col, T2 v) {
+        if (col < ncol) base[kz * zs + col] = v;
+    };
+    cols_fft<SIGN, TX, true, 0, R16, PID>(g.pz, A, B, src, dst);
+}
+
+template <typename T>
+void launch_z_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    const int TX = tuned_cols<T>(g, g.tx_zf, g.nz, 2, 128 * 1024);
+    const size_t sm = (g.pz.nst <= 2 ? 1 : 2) * (size_t)TX * g.nz * sizeof(T2);  // as in the y pass
+    dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
+    if (sign > 0) {
+        PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_pass<T, 1, TXC, R16C, PIDC>, sm);
+                      k_z_pass<T, 1, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf)));
+    } else {
+        PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_pass<T, -1, TXC, R16C, PIDC>, sm);
+                      k_z_pass<T, -1, TXC, R16C, PIDC><<<grid, kThreads, sm, s>>>(g, reinterpret_cast<T2*>(buf)));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // z pass, forward: FFT along z then k-space scaling (the last stage's store)
 //   mode 0: y^ = W / N  -> FP64                                  (set_state)
 //   mode 1: f^E_X = -M k^2 q^/N, f^E_phi = -L g^/N -> compute type (stages)

@@ -5,4 +5,5 @@
 namespace pf {
 template void launch_z_fwd<double>(const Geo&, const Phys&, const void*, void*, int, cudaStream_t, int);
 template void launch_z_fwd<float>(const Geo&, const Phys&, const void*, void*, int, cudaStream_t, int);
+template void launch_z_pass<float>(const Geo&, void*, int, int, cudaStream_t);
 }  // namespace pf

@@ -99,24 +99,10 @@ void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageT
     const int TX = tuned_cols<T>(g, g.tx_z, g.nz, 2, 128 * 1024);
     const size_t sm = 2 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 4);
-    // FP32-bulk stages with no or few earlier terms run kernels compiled for
-    // that bound (the first stages of a step)
-    auto go = [&](auto bound) {
-        constexpr int MT = decltype(bound)::value;
-        PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_stage<T, TXC, R16C, PIDC, MT>, sm);
-                      k_z_stage<T, TXC, R16C, PIDC, MT><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout,
-                                                                                 reinterpret_cast<T2*>(W)));
-    };
-    if constexpr (sizeof(T) == 4) {
-        if (st.n == 0)
-            go(std::integral_constant<int, 0>{});
-        else if (st.n <= 2)
-            go(std::integral_constant<int, 2>{});
-        else
-            go(std::integral_constant<int, kMaxStages>{});
-    } else {
-        go(std::integral_constant<int, kMaxStages>{});
-    }
+    constexpr int MT = kMaxStages;
+    PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_stage<T, TXC, R16C, PIDC, MT>, sm);
+                  k_z_stage<T, TXC, R16C, PIDC, MT><<<grid, kThreads, sm, s>>>(g, ph, y, st, zout,
+                                                                             reinterpret_cast<T2*>(W)));
 }
 
 // ---------------------------------------------------------------------------
