@@ -261,26 +261,34 @@ struct Radices {};
 // one) load every power.
 template <int R, int SIGN, typename T2>
 __device__ __forceinline__ void apply_twiddles(T2* v, const T2* __restrict__ tw, int st) {
-    T2 w[R];
+    auto mul = [](T2& x, T2 w) { x = SIGN < 0 ? cmul(x, w) : cmulc(x, w); };
     if constexpr (sizeof(T2) == 8 && (R == 8 || R == 16)) {
-        w[1] = __ldg(tw + st);
-        w[2] = __ldg(tw + 2 * st);
-        w[4] = __ldg(tw + 4 * st);
-        w[3] = cmul(w[2], w[1]);
-        w[5] = cmul(w[4], w[1]);
-        w[6] = cmul(w[4], w[2]);
-        w[7] = cmul(w[4], w[3]);
+        // each power applied as soon as it is formed (few live registers)
+        const T2 w1 = __ldg(tw + st), w2 = __ldg(tw + 2 * st), w4 = __ldg(tw + 4 * st);
+        mul(v[1], w1);
+        mul(v[2], w2);
+        const T2 w3 = cmul(w2, w1);
+        mul(v[3], w3);
+        mul(v[4], w4);
+        mul(v[5], cmul(w4, w1));
+        mul(v[6], cmul(w4, w2));
+        mul(v[7], cmul(w4, w3));
         if constexpr (R == 16) {
-            w[8] = __ldg(tw + 8 * st);
-#pragma unroll
-            for (int t = 9; t < 16; ++t) w[t] = cmul(w[8], w[t - 8]);
+            const T2 w8 = __ldg(tw + 8 * st);
+            mul(v[8], w8);
+            mul(v[9], cmul(w8, w1));
+            mul(v[10], cmul(w8, w2));
+            mul(v[11], cmul(w8, w3));
+            const T2 w12 = cmul(w8, w4);
+            mul(v[12], w12);
+            mul(v[13], cmul(w12, w1));
+            mul(v[14], cmul(w12, w2));
+            mul(v[15], cmul(w12, w3));
         }
     } else {
 #pragma unroll
-        for (int t = 1; t < R; ++t) w[t] = __ldg(tw + t * st);
+        for (int t = 1; t < R; ++t) mul(v[t], __ldg(tw + t * st));
     }
-#pragma unroll
-    for (int t = 1; t < R; ++t) v[t] = SIGN < 0 ? cmul(v[t], w[t]) : cmulc(v[t], w[t]);
 }
 
 template <int R, int SIGN, int N, int NS, typename T2>
