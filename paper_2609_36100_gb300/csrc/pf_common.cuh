@@ -150,19 +150,21 @@ __device__ __forceinline__ DF df_two_sum(float a, float b) {
     return DF{h, __fadd_rn(__fsub_rn(a, __fsub_rn(h, bb)), __fsub_rn(b, bb))};
 }
 
-// FP32 value of an FP64 one truncated to 24 significant bits, from its bit
-// fields (below the FP32 normal range: signed zero; above it: infinity; NaN
-// stays NaN)
-__device__ __forceinline__ float f32_trunc_bits(double d) {
-    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+// FP32 value of an FP64 one, given as its two 32-bit words, truncated to 24
+// significant bits (below the FP32 normal range: signed zero; above it:
+// infinity; NaN stays NaN).  In range the exponent field is rebiased in place
+// and one funnel shift brings exponent and leading mantissa bits together.
+__device__ __forceinline__ float f32_trunc_hilo(unsigned hi, unsigned lo) {
     const unsigned sign = hi & 0x80000000u;
-    const int fe = (int)((hi >> 20) & 0x7ffu) - 896;
-    if (fe <= 0) return __uint_as_float(sign);
-    if (fe >= 255) {
-        const bool nan = fe == 2047 - 896 && ((hi & 0xfffffu) | lo) != 0u;
-        return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
-    }
-    return __uint_as_float(sign | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    const unsigned ef = (hi >> 20) & 0x7ffu;  // FP64 biased exponent; FP32 normal range: 897..1150
+    unsigned r = __funnelshift_l(lo, hi - (896u << 20), 3) | sign;
+    if (ef - 897u >= 254u)
+        r = ef <= 896u ? sign
+                       : sign | 0x7f800000u | (ef == 2047u && ((hi & 0xfffffu) | lo) != 0u ? 0x400000u : 0u);
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ float f32_trunc_bits(double d) {
+    return f32_trunc_hilo((unsigned)__double2hiint(d), (unsigned)__double2loint(d));
 }
 
 // FP64 -> double-float: h = d truncated to 24 significant bits (exact in both
@@ -171,9 +173,10 @@ __device__ __forceinline__ float f32_trunc_bits(double d) {
 // subtraction.  Double-float -> FP64: one FP64 addition.
 __device__ __forceinline__ DF df_from_d(double d) {
     const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-    const int fe = (int)((hi >> 20) & 0x7ffu) - 896;
-    const double hd = fe > 0 ? __hiloint2double((int)hi, (int)(lo & 0xe0000000u)) : 0.0;
-    return DF{f32_trunc_bits(hd), f32_trunc_bits(d - hd)};
+    const bool normal = ((hi >> 20) & 0x7ffu) > 896u;  // |d| at or above the FP32 normal range
+    const unsigned lh = lo & 0xe0000000u;
+    const double hd = normal ? __hiloint2double((int)hi, (int)lh) : 0.0;
+    return DF{normal ? f32_trunc_hilo(hi, lh) : 0.0f, f32_trunc_bits(d - hd)};
 }
 __device__ __forceinline__ double df_to_d(DF a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 
@@ -423,9 +426,28 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ DF df_one_minus(DF c, DF lam) { return df_add(DF{1.f, 0.f}, df_mul(DF{-c.h, -c.l}, lam)); }
 
-template <int MAXT = kMaxStages>  // at most MAXT earlier-stage terms (compile-time bound: fewer registers)
+// where the stage coefficients of a FP32-bulk combination live: DC = 0 in the
+// kernel parameters (direct operands, no loads), DC = 1 behind st.dc (device
+// copies written by the batch round kernels), DC = -1 decided per call
+template <int DC>
+struct CoefSrc {
+    const StageTerms& st;
+    __device__ __forceinline__ bool dev() const { return DC < 0 ? st.dc != nullptr : DC > 0; }
+    __device__ __forceinline__ float Ih(int j) const { return dev() ? st.dc->cIh[j] : st.cIh[j]; }
+    __device__ __forceinline__ float Il(int j) const { return dev() ? st.dc->cIl[j] : st.cIl[j]; }
+    __device__ __forceinline__ float Eh(int j) const { return dev() ? st.dc->cEh[j] : st.cEh[j]; }
+    __device__ __forceinline__ float El(int j) const { return dev() ? st.dc->cEl[j] : st.cEl[j]; }
+    __device__ __forceinline__ DF gamma() const { return dev() ? DF{st.dc->gh, st.dc->gl} : DF{st.gh, st.gl}; }
+    __device__ __forceinline__ DF qgamma() const { return dev() ? DF{st.dc->qgh, st.dc->qgl} : DF{st.qgh, st.qgl}; }
+};
+
+// at most MAXT earlier-stage terms (compile-time bound: fewer registers);
+// Idx: element index type (unsigned where 4 NK < 2^32: one-instruction
+// address arithmetic)
+template <int MAXT = kMaxStages, int DC = -1, typename Idx = long long>
 __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms& st, const double2* __restrict__ y,
-                                                 long long gi, float4* __restrict__ zout) {
+                                                 Idx gi, float4* __restrict__ zout) {
+    const CoefSrc<DC> cs{st};
     // every load first (independent, all in flight together), then the sums
     const bool need_lam = st.mI != 0u || st.qout || st.has_gamma;
     const bool load_q = st.has_gamma && st.qin;
@@ -450,13 +472,13 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
     for (int j = 0; j < MAXT; ++j) {
         if (j < st.n) {
             if ((st.mI >> j) & 1u) {
-                const float ch = cIh_of(st, j), cl = cIl_of(st, j);
+                const float ch = cs.Ih(j), cl = cs.Il(j);
                 if ((st.mY >> j) & 1u)
                     I.add(ch, cl, yx, yy);
                 else
                     I.add(ch, cl, DF{zv[j].x, zv[j].z}, DF{zv[j].y, zv[j].w});
             }
-            if ((st.mE >> j) & 1u) E.add(cEh_of(st, j), cEl_of(st, j), fv[j]);
+            if ((st.mE >> j) & 1u) E.add(cs.Eh(j), cs.El(j), fv[j]);
         }
     }
     DF rx = df_add(yx, E.x()), ry = df_add(yy, E.y());
@@ -467,11 +489,11 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
             ry = df_add(ry, df_mul(lam, I.y()));
         }
         if (st.qout) {
-            const DF q = df_rcp(df_one_minus(DF{qgh_of(st), qgl_of(st)}, lam));
+            const DF q = df_rcp(df_one_minus(cs.qgamma(), lam));
             reinterpret_cast<float2*>(st.qout)[gi] = make_float2(q.h, q.l);
         }
         if (st.has_gamma) {
-            const DF q = load_q ? DF{qt.x, qt.y} : df_rcp(df_one_minus(DF{gh_of(st), gl_of(st)}, lam));
+            const DF q = load_q ? DF{qt.x, qt.y} : df_rcp(df_one_minus(cs.gamma(), lam));
             rx = df_mul(rx, q);
             ry = df_mul(ry, q);
         }

@@ -52,19 +52,21 @@ __global__ void k_stage_pointwise_df(Geo g, const double2* __restrict__ y, Stage
 // FP32-bulk stage assembly, streaming: each element's loads all issued
 // together (U elements per iteration for stages with few earlier terms), the
 // double-float stage value z_i and its FP32 rounding (the input of the inverse
-// z transform) written back.  Every array is read or written once.
-template <int MAXT, int U>
+// z transform) written back.  Every array is read or written once.  DC: where
+// the coefficients live (0: kernel parameters, 1: the batch's device copy);
+// Idx: element index type.
+template <int MAXT, int U, int DC, typename Idx>
 __global__ void __launch_bounds__(256) k_stage_assemble_df(Geo g, const double2* __restrict__ y, StageTerms st,
                                                            float4* __restrict__ zout, float2* __restrict__ W) {
     PF_SKIP_INACTIVE(g);
     if (y_swapped(g)) y = g.yother;
-    const long long total = 4LL * g.NK;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total; gi += stride * U) {
+    const Idx total = (Idx)(4LL * g.NK);
+    const Idx stride = (Idx)gridDim.x * blockDim.x;
+    for (Idx gi = (Idx)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += stride * U) {
         float2 r[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (gi + u * stride < total) r[u] = stage_value_df<MAXT>(g, st, y, gi + u * stride, zout);
+            if (gi + u * stride < total) r[u] = stage_value_df<MAXT, DC, Idx>(g, st, y, gi + u * stride, zout);
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (gi + u * stride < total) W[gi + u * stride] = r[u];
@@ -82,11 +84,29 @@ static int resident_blocks(K kern, int threads) {
     return (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
 }
 
+template <int MAXT, int U, int DC, typename Idx>
+static void assemble_k(const Geo& g, const double2* y, const StageTerms& st, float4* z, float2* w, cudaStream_t s) {
+    static int blocks = 0;  // per process: one device type
+    if (blocks == 0) blocks = resident_blocks(k_stage_assemble_df<MAXT, U, DC, Idx>, 256);
+    k_stage_assemble_df<MAXT, U, DC, Idx><<<blocks, 256, 0, s>>>(g, y, st, z, w);
+}
+
 template <int MAXT, int U>
 static void assemble(const Geo& g, const double2* y, const StageTerms& st, float4* z, float2* w, cudaStream_t s) {
-    static int blocks = 0;  // per process: one device type
-    if (blocks == 0) blocks = resident_blocks(k_stage_assemble_df<MAXT, U>, 256);
-    k_stage_assemble_df<MAXT, U><<<blocks, 256, 0, s>>>(g, y, st, z, w);
+    // 32-bit indices while every index the loop forms (below 4 NK plus U
+    // grid strides of at most a few million) stays below 2^32
+    const bool idx32 = 4LL * g.NK <= (1LL << 32) - (1LL << 26);
+    if (st.dc) {
+        if (idx32)
+            assemble_k<MAXT, U, 1, unsigned>(g, y, st, z, w, s);
+        else
+            assemble_k<MAXT, U, 1, long long>(g, y, st, z, w, s);
+    } else {
+        if (idx32)
+            assemble_k<MAXT, U, 0, unsigned>(g, y, st, z, w, s);
+        else
+            assemble_k<MAXT, U, 0, long long>(g, y, st, z, w, s);
+    }
 }
 
 void launch_stage_assemble(const Geo& g, const double2* y, const StageTerms& st, double2* zout, void* W,
