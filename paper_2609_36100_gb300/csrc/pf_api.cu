@@ -500,7 +500,18 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef 
         const bool fEn = bt.cE[j] != 0.0 || (lte && dtm.cE[j] != 0.0);
         fterms += (zI && !(c->alias_y[j]) ? 16.0 : 0.0) + (fEn ? (c->fp32 ? 8.0 : 16.0) : 0.0);
     }
-    {
+    if constexpr (sizeof(T) == 4) {
+        // FP32-bulk: streaming completion, then the error's inverse z
+        // transform as a plain in-place pass
+        {
+            ProfScope p(c, PF_K_Z_FINAL, 4 * NK * (16.0 + fterms + 16.0 + (lte ? cb : 0.0)));
+            launch_step_complete(g, c->y, bt, dtm, lte ? 1 : 0, c->ynew, c->W, s);
+        }
+        if (lte) {
+            ProfScope p(c, PF_K_Z_IFFT, 4 * NK * 2 * cb);
+            launch_z_pass<T>(g, c->W, 4, +1, s);
+        }
+    } else {
         ProfScope p(c, PF_K_Z_FINAL, 4 * NK * (16.0 + fterms + 16.0 + (lte ? cb : 0.0)));
         launch_z_final<T>(g, ph, c->y, bt, dtm, lte ? 1 : 0, c->ynew, c->W, s);
     }

@@ -505,19 +505,22 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
 // FP32-bulk step completion (double-float):
 //   y_n = y + [lambda sum_j (dt b^I_j) z_j + sum_j (dt b^E_j) f^E_j]
 // with the bracket rounded to FP64 once and added to the FP64 state; returns
-// the local error estimate (the same sums with dt (b - bt)) in FP32.
+// the local error estimate (the same sums with dt (b - bt)) in FP32.  MAXT,
+// DC and Idx as in stage_value_df.
+template <int MAXT = kMaxStages, int DC = -1, typename Idx = long long>
 __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms& bt, const StageTerms& dt,
-                                                 int want_lte, const double2* __restrict__ y, long long gi,
+                                                 int want_lte, const double2* __restrict__ y, Idx gi,
                                                  double2* __restrict__ ynew) {
+    const CoefSrc<DC> cb{bt}, cd{dt};
     const unsigned lmI = want_lte ? dt.mI : 0u, lmE = want_lte ? dt.mE : 0u;
     const unsigned mI = bt.mI | lmI, mE = bt.mE | lmE, mz = mI & ~bt.mY;
     // every load first, then the sums
     const double2 yv = __ldg(y + gi);
     const float2 lt = mI != 0u ? __ldg(g.lamdf + gi) : make_float2(0.f, 0.f);
-    float4 zv[kMaxStages];
-    float2 fv[kMaxStages];
+    float4 zv[MAXT];
+    float2 fv[MAXT];
 #pragma unroll
-    for (int j = 0; j < kMaxStages; ++j) {
+    for (int j = 0; j < MAXT; ++j) {
         zv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         fv[j] = make_float2(0.f, 0.f);
         if (j < bt.n) {
@@ -535,7 +538,7 @@ __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms&
     DFAcc Ib, Eb;
     float dIx = 0.f, dIy = 0.f, dEx = 0.f, dEy = 0.f;
 #pragma unroll
-    for (int j = 0; j < kMaxStages; ++j) {
+    for (int j = 0; j < MAXT; ++j) {
         if (j < bt.n) {
             const bool bI = (bt.mI >> j) & 1u, bE = (bt.mE >> j) & 1u;
             const bool lI = (lmI >> j) & 1u, lE = (lmE >> j) & 1u;
@@ -545,16 +548,16 @@ __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms&
                     zx = DF{zv[j].x, zv[j].z};
                     zy = DF{zv[j].y, zv[j].w};
                 }
-                if (bI) Ib.add(cIh_of(bt, j), cIl_of(bt, j), zx, zy);
+                if (bI) Ib.add(cb.Ih(j), cb.Il(j), zx, zy);
                 if (lI) {
-                    dIx = __fmaf_rn(cIh_of(dt, j), zx.h, dIx);
-                    dIy = __fmaf_rn(cIh_of(dt, j), zy.h, dIy);
+                    dIx = __fmaf_rn(cd.Ih(j), zx.h, dIx);
+                    dIy = __fmaf_rn(cd.Ih(j), zy.h, dIy);
                 }
             }
-            if (bE) Eb.add(cEh_of(bt, j), cEl_of(bt, j), fv[j]);
+            if (bE) Eb.add(cb.Eh(j), cb.El(j), fv[j]);
             if (lE) {
-                dEx = __fmaf_rn(cEh_of(dt, j), fv[j].x, dEx);
-                dEy = __fmaf_rn(cEh_of(dt, j), fv[j].y, dEy);
+                dEx = __fmaf_rn(cd.Eh(j), fv[j].x, dEx);
+                dEy = __fmaf_rn(cd.Eh(j), fv[j].y, dEy);
             }
         }
     }

@@ -168,6 +168,9 @@ void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s);
 template <typename T>
 void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int scale_mode, cudaStream_t s,
                   int nf = 4);
+// FP32-bulk step completion as a stream (new state + FP32 local error into W)
+void launch_step_complete(const Geo& g, const double2* y, const StageTerms& bt, const StageTerms& dt, int want_lte,
+                          double2* ynew, void* W, cudaStream_t s);
 template <typename T>
 void launch_z_final(const Geo& g, const Phys& ph, const double2* y, const StageTerms& bterm,
                     const StageTerms& dterm, int want_lte, double2* ynew, void* W, cudaStream_t s);

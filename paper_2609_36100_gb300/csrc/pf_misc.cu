@@ -123,6 +123,61 @@ void launch_stage_assemble(const Geo& g, const double2* y, const StageTerms& st,
         assemble<kMaxStages, 1>(g, y, st, z, w, s);
 }
 
+// FP32-bulk step completion, streaming: the new FP64 state and the FP32
+// local error estimate of every element (the error's inverse z transform is a
+// separate in-place pass).  Template arguments as in the stage assembly.
+template <int MAXT, int DC, typename Idx>
+__global__ void __launch_bounds__(256) k_step_complete_df(Geo g, const double2* __restrict__ y, StageTerms bt,
+                                                          StageTerms dt, int want_lte, double2* __restrict__ ynew,
+                                                          float2* __restrict__ W) {
+    PF_SKIP_INACTIVE(g);
+    if (y_swapped(g)) {
+        double2* other = const_cast<double2*>(y);
+        y = ynew;
+        ynew = other;
+    }
+    const Idx total = (Idx)(4LL * g.NK);
+    const Idx stride = (Idx)gridDim.x * blockDim.x;
+    for (Idx gi = (Idx)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += stride) {
+        const float2 e = final_value_df<MAXT, DC, Idx>(g, bt, dt, want_lte, y, gi, ynew);
+        if (want_lte) W[gi] = e;
+    }
+}
+
+template <int MAXT, int DC, typename Idx>
+static void complete_k(const Geo& g, const double2* y, const StageTerms& bt, const StageTerms& dt, int want_lte,
+                       double2* ynew, float2* w, cudaStream_t s) {
+    static int blocks = 0;
+    if (blocks == 0) blocks = resident_blocks(k_step_complete_df<MAXT, DC, Idx>, 256);
+    k_step_complete_df<MAXT, DC, Idx><<<blocks, 256, 0, s>>>(g, y, bt, dt, want_lte, ynew, w);
+}
+
+template <int MAXT>
+static void complete(const Geo& g, const double2* y, const StageTerms& bt, const StageTerms& dt, int want_lte,
+                     double2* ynew, float2* w, cudaStream_t s) {
+    const bool idx32 = 4LL * g.NK <= (1LL << 32) - (1LL << 26);
+    if (bt.dc) {
+        if (idx32)
+            complete_k<MAXT, 1, unsigned>(g, y, bt, dt, want_lte, ynew, w, s);
+        else
+            complete_k<MAXT, 1, long long>(g, y, bt, dt, want_lte, ynew, w, s);
+    } else {
+        if (idx32)
+            complete_k<MAXT, 0, unsigned>(g, y, bt, dt, want_lte, ynew, w, s);
+        else
+            complete_k<MAXT, 0, long long>(g, y, bt, dt, want_lte, ynew, w, s);
+    }
+}
+
+void launch_step_complete(const Geo& g, const double2* y, const StageTerms& bt, const StageTerms& dt, int want_lte,
+                          double2* ynew, void* W, cudaStream_t s) {
+    float2* w = reinterpret_cast<float2*>(W);
+    if (bt.n <= 6)
+        complete<6>(g, y, bt, dt, want_lte, ynew, w, s);
+    else
+        complete<kMaxStages>(g, y, bt, dt, want_lte, ynew, w, s);
+}
+
 void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, const StageTerms& st, int fe_is_f32,
                             double2* zout, cudaStream_t s) {
     if (fe_is_f32)
