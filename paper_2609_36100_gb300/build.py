@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpf.so")
-SOURCES = ["pf_zelastic.cu", "pf_zfwd.cu", "pf_ypass.cu", "pf_xpass_f32.cu", "pf_xpass_f64.cu", "pf_zfinal_f32.cu",
+SOURCES = ["pf_zelastic.cu", "pf_zfwd.cu", "pf_ypass.cu", "pf_xpass_f32.cu", "pf_xpass_f64.cu",
            "pf_zfinal_f64.cu", "pf_zstage_f64.cu", "pf_fno.cu", "pf_api.cu", "pf_misc.cu",
            "pf_plan.cu", "pf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -16,9 +16,12 @@
 // Step completion (Eq. ARK_method), the embedded local error (Eq.
 // ARK_embedding) and its WRMS norm (Eqs. wrms_norm, wrms_weights) are three
 // more passes; this file holds the two that combine stages (stage assembly
-// and step completion).  Template parameter T is the compute type of the
-// transforms and RHS (double, or float for the FP32-bulk form); the state is
-// always FP64, the stage vectors FP64 or, in the FP32-bulk form, double-float.
+// and step completion) with the transform fused in.  The library instantiates
+// them for T = double; the FP32-bulk form runs the same combinations as
+// streams (k_stage_assemble_df, k_step_complete_df) followed by an in-place
+// inverse z pass, which keeps the memory stream and the transform apart.  The
+// state is always FP64, the stage vectors FP64 or, in the FP32-bulk form,
+// double-float.
 #pragma once
 #include "pf_common.cuh"
 
