@@ -34,6 +34,15 @@ def test_header_symbols_exported(L):
     assert set(names) == set(pfg.SIGNATURES)
 
 
+def test_build_compiles_every_translation_unit():
+    # every .cu under csrc/ is one translation unit of libpf.so, and the
+    # source list names no missing file
+    import importlib
+    B = importlib.import_module("paper_2609_36100_gb300.build")
+    units = sorted(f for f in os.listdir(B.CSRC) if f.endswith(".cu"))
+    assert sorted(B.SOURCES) == units
+
+
 def test_library_tableau_order_conditions(L):
     AE, AI, bE, bI, btE, btI = pfg.method_tableau("ark4")
     assert AE.shape == (6, 6)
