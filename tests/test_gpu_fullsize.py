@@ -1,0 +1,59 @@
+"""Full-size parity on the bench workload: the 256^3 config-2 initial state
+(32 seeded spheres), one ARK4(3)6L[2]SA step of h = 1 s (the controller's
+first attempt in the bench), compared over the whole field with one FP64
+oracle step.  The FP32-bulk form runs in the launch configuration the bench
+times (its schedule chosen by the autotuner first); the plain FP64 path with
+its default schedule.  Bars as in the small cases: FP64 rel L2 per field
+<= 1e-11 and ||LTE|| to 1e-9 relative; FP32-bulk rel L2 per field <= 1e-5,
+||LTE|| within 1e-3, composition mean bitwise.  The oracle step takes about
+a minute of host time."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+N = 256
+
+
+@pytest.fixture(scope="module")
+def pfg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_36100_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ref(pfg, params):
+    y0 = synth.ic_spheres(N, 32, 4.0, 10.0, 2, params)
+    m = oracle.Model(y0.shape[1:], params)
+    yh, e, _ = oracle.ark_step(m, m.to_k(y0), 1.0, oracle.ark436l2sa(), params["rtol"], params["atol"])
+    return y0, yh, e
+
+
+def relerr(a, b):
+    return np.array([np.linalg.norm((a[f] - b[f]).ravel()) / np.linalg.norm(b[f].ravel()) for f in range(4)])
+
+
+@pytest.mark.parametrize("prec,tol,etol", [("fp32bulk", 1e-5, None), ("fp64", 1e-11, 1e-9)])
+def test_bench_workload_first_step(pfg, params, ref, prec, tol, etol):
+    y0, yh, e_ref = ref
+    with pfg.Simulation(y0.shape[1:], params, "ark4", prec) as s:
+        s.set_state(y0)
+        if prec == "fp32bulk":
+            s.autotune(reps=2)
+        dc = s.state_hat()[0, 0, 0, 0].item()
+        e = s.step(1.0)
+        got = s.state_hat().cpu().numpy()
+    err = relerr(got, yh)
+    assert np.all(err <= tol), err
+    if etol is None:
+        assert abs(e - e_ref) <= 1e-3 * max(1.0, abs(e_ref)), (e, e_ref)
+        assert got[0, 0, 0, 0] == dc  # the composition mean stays FP64-exact
+    else:
+        assert e == pytest.approx(e_ref, rel=etol)
