@@ -1,6 +1,7 @@
 // Pointwise and single-thread kernels: stage assembly without a transform,
-// the diagonal implicit solve, lambda tables, the batch controller kernels,
-// the deterministic reduction and the k-space free-energy sum.
+// the FP32-bulk stage-assembly and step-completion streams, the diagonal
+// implicit solve, lambda tables, the batch controller kernels, the
+// deterministic reduction and the k-space free-energy sum.
 #include "pf_common.cuh"
 
 namespace pf {
