@@ -1,20 +1,34 @@
 #!/usr/bin/env python
 """Throughput of the pseudospectral ImEx-ARK phase-field hot path on GB300.
 
-Workload: 256^3 periodic grid, 4 fields (X, phi_1..3), 32 seeded spherical
-gamma'' nuclei (radius 4-10 cells, composition at the precipitate value
-inside), ARK4(3)6L[2]SA with the embedded-error WRMS controller at rtol 1e-4,
-atol 1e-8.  One bench step = one controller-driven step attempt: 6 stages
-(each a full explicit RHS evaluation: 14 real 3D FFTs with the physics fused
-in, plus the implicit stage solve), step completion, the embedded local
-error, its WRMS norm and the accept/reject decision.
+Workload (the configuration the metric is quoted on: "FP64 vs FP32-bulk,
+256^3 grid ... integrated to a fixed simulated time; error per field"):
+256^3 periodic grid, 4 fields (X, phi_1..3), 32 seeded spherical gamma''
+nuclei (radius 4-10 cells, composition at the precipitate value inside),
+ARK4(3)6L[2]SA with the embedded-error WRMS controller at rtol 1e-4,
+atol 1e-8, integrated from t = 0 (h0 = 1 s) to t_final = 60 s.  One bench
+step = one such integration: every controller-driven step attempt (6 stages,
+each a full explicit RHS evaluation -- 14 real 3D FFTs with the physics fused
+in -- plus the implicit stage solves, the step completion, the embedded local
+error, its WRMS norm and the accept/reject decision) until t_final.
 
-Headline value: Gpt-stage/s (grid points x RHS evaluations per second) of the
-FP32-bulk form (FFTs/RHS in FP32; state, norm and controller in FP64; stage
-vectors and their combinations in double-float, ~47 significant bits); the
-plain FP64 GPU path is timed beside it.  Every array a step streams (the FP64
-state alone is 512 MiB at 256^3; ~7 GB of step buffers in all) is far larger
-than the 129 MB L2, so no flush is needed between steps.
+Headline value: Gpt-stage/s (grid points x RHS evaluations per second,
+rejected attempts included) of the FP32-bulk form (FFTs/RHS in FP32; state,
+norm and controller in FP64; stage vectors and their combinations in
+double-float, ~47 significant bits).  The same line carries, for the same
+integration: simulated seconds per wall second of the FP32-bulk form and of
+the plain FP64 GPU path, their ratio (the gain at the same end time and
+tolerance), the FP32-bulk final state's error per field against the FP64
+final state, and both forms' errors against a tight-tolerance FP64
+integration (rtol 1e-6), which shows the two reach the same final-state
+error.  Every array a step streams (the FP64 state alone is 512 MiB at
+256^3; ~7 GB of step buffers in all) is far larger than the 129 MB L2, so no
+flush is needed between steps.
+
+Further legs on the same line: the 640^3 / 300-nucleus workload (the
+largest single-GPU configuration) over a bounded stretch of simulated time,
+the uneven-grid ensemble advanced to 60 s, the surrogate, the measured FMA
+peaks, and the FP64 oracle on the host cores.
 
 --impl reference times the FP64 CPU oracle (the only reference there is: the
 paper ships no code) on bounded samples of the same workload.
@@ -32,19 +46,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "simulated s per wall s at fixed tol vs plain FP64 GPU; Gpt-stage/s; % HBM BW"
 UNIT = "Gpt-stage/s"
+WORKLOAD2 = ("256^3 gamma'' KKS phase field (4 fields), 32 seeded nuclei r 4-10 cells, ARK4(3)6L[2]SA adaptive "
+             "rtol 1e-4 atol 1e-8 from t=0 (h0=1 s) to t_final=60 s; FP32-bulk (FP64 state/norms) vs plain FP64")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5, help="timed integrations to t_final")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--t-final", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 path")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 integration")
+    ap.add_argument("--no-tight", action="store_true", help="skip the tight-tolerance FP64 reference")
+    ap.add_argument("--big", type=int, default=640, help="side of the largest-grid leg (0: skip)")
+    ap.add_argument("--big-t", type=float, default=20.0, help="simulated seconds of the largest-grid leg")
     ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble measurement (0: skip)")
-    ap.add_argument("--ensemble-t", type=float, default=5.0, help="simulated seconds of the ensemble measurement")
+    ap.add_argument("--ensemble-t", type=float, default=60.0, help="simulated seconds of the ensemble measurement")
     ap.add_argument("--surrogate", type=int, default=16, help="training trajectories of the surrogate measurement (0: skip)")
     return ap.parse_args()
 
@@ -115,6 +135,20 @@ def traffic_from_profiles(kernel, precision, n):
         return None
 
 
+def relerr(a, b):
+    import numpy as np
+    return [float(np.linalg.norm((a[f] - b[f]).ravel()) / np.linalg.norm(b[f].ravel())) for f in range(a.shape[0])]
+
+
+# nominal FP64 flops of one explicit RHS evaluation per grid point: 14 real
+# 3D transforms at 2.5 log2(N) flops per point each (half of the 5 N log2 N
+# of a complex transform) plus ~300 flops of pointwise physics and elastic
+# kernel; the stage sums add ~50
+def nominal_flops_per_point_stage(N):
+    import math
+    return 14 * 2.5 * math.log2(N) + 350.0
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -127,13 +161,10 @@ def run_ours(args, rank, world, dist):
     pfg.build()
     p = synth.load_params()
     n = args.n
-    if n == 640:
-        y0 = synth.ic_config5(n, 5, p)  # 300 nuclei r in [4, 12] cells
-    else:
-        y0 = synth.ic_spheres(n, 32 if n >= 256 else max(4, 32 * n ** 3 // 256 ** 3), 4.0, 10.0, 2, p)
+    T = args.t_final
+    y0 = synth.ic_spheres(n, 32 if n >= 256 else max(4, 32 * n ** 3 // 256 ** 3), 4.0, 10.0, 2, p)
     stream = torch.cuda.current_stream()
     N = n ** 3
-    out = {}
 
     def barrier():
         if dist is not None:
@@ -147,128 +178,208 @@ def run_ours(args, rank, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def timed(prec, K, W, profile=False):
-        """W warm-up attempts, K timed attempts (the headline), then -- with
-        `profile` -- K more attempts with a CUDA event pair around every
-        kernel (the per-kernel times and the roofline; the events add a few
-        per cent to those attempts, so they are kept out of the headline)."""
+    y0_dev = torch.from_numpy(y0).to("cuda")
+
+    def new_sim(prec, rtol=1e-4, tune=True):
         sim = pfg.Simulation((n, n, n), p, "ark4", prec)
-        sim.set_state(y0)
-        tuning = sim.autotune(reps=2)  # launch schedule picked by the autotuner
+        sim.set_state(y0_dev)
+        tuning = sim.autotune(reps=2) if tune else None
+        return sim, tuning, sim.state_hat()
+
+    def integrate(sim, y0h, rtol=1e-4):
+        sim.set_state_hat(y0h)
         sim.set_time(0.0, 1.0)
-        # clocks sampled over the warm-up and timed attempts (identical work)
-        clk = Clocks(local) if (profile and rank == 0) else None
-        sim.advance_attempts(W)
-        st0 = sim.stats()
+        return sim.advance(T, rtol, 1e-8)
+
+    def timed(sim, y0h, K, W, clocks=False, rtol=1e-4):
+        """W untimed integrations, then K timed ones (CUDA events on the
+        launching stream, barrier + synchronize on both sides)."""
+        clk = Clocks(local) if (clocks and rank == 0) else None
+        for _ in range(W):
+            integrate(sim, y0h, rtol)
         barrier()
+        st0 = sim.stats()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        w0 = time.perf_counter()
         torch.cuda.nvtx.range_push("timed")  # ncu --nvtx-include timed/ selects these launches
         e0.record(stream)
-        sim.advance_attempts(K)
+        for _ in range(K):
+            integrate(sim, y0h, rtol)
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         barrier()
-        wall = time.perf_counter() - w0
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1))
         st1 = sim.stats()
-        prof, ms_prof = None, None
-        if profile:
-            sim.profile(True)
-            barrier()
-            e0.record(stream)
-            sim.advance_attempts(K)
-            e1.record(stream)
-            barrier()
-            ms_prof = e0.elapsed_time(e1)
-            prof = sim.profile_read()
-            sim.profile(False)
-        clocks = clk.stop() if clk else None
-        res = {"ms": max_over_ranks(ms), "wall": wall, "rhs": st1["rhs_evals"] - st0["rhs_evals"],
-               "sim_s": st1["t"] - st0["t"], "accepted": st1["steps_accepted"] - st0["steps_accepted"],
-               "rejected": st1["steps_rejected"] - st0["steps_rejected"], "prof": prof, "clocks": clocks,
-               "sim": sim, "tuning": tuning, "ms_profiled": ms_prof}
-        return res
+        att = sim.attempts()
+        rhs = (st1["rhs_evals"] - st0["rhs_evals"]) // K
+        return {"ms_per_integration": ms / K, "rhs_per_integration": rhs,
+                "accepted": sum(1 for a in att if a[3]), "rejected": sum(1 for a in att if not a[3]),
+                "h_last": att[-1][1] if att else None, "h_max": max((a[1] for a in att if a[3]), default=None),
+                "gpt_stage_s": rhs * N * world / (ms / K / 1e3) / 1e9,
+                "sim_s_per_wall_s": T / (ms / K / 1e3),
+                "clocks": clk.stop() if clk else None}
 
     K, W = args.steps, args.warmup
-    r32 = timed("fp32bulk", K, W, profile=True)
-    units = r32["rhs"] * N * world
-    value = units / (r32["ms"] / 1e3) / 1e9
-    sim_rate = r32["sim_s"] / (r32["ms"] / 1e3)
-    # dominant kernel and its live roofline
-    prof = r32["prof"]
+    s32, tun32, y0h = new_sim("fp32bulk")
+    r32 = timed(s32, y0h, K, W, clocks=True)
+    final32 = s32.get_state()
+    # per-kernel CUDA events over one more integration (kept out of the headline)
+    s32.profile(True)
+    barrier()
+    integrate(s32, y0h)
+    barrier()
+    prof = s32.profile_read()
+    s32.profile(False)
     top = max(prof.items(), key=lambda kv: kv[1][0])
     kname, (kms, kbytes, klaunch) = top
     hbm, src = peaks()
     achieved = kbytes / (kms / 1e3) / 1e9
     launches = int(sum(v[2] for v in prof.values()))
-    # end to end through the public API with host buffers: H2D of the
-    # real-space state, one step attempt, D2H of the real-space state
-    sim = r32["sim"]
+    # end to end through the public API with host buffers: the real-space
+    # initial state copied host -> device, the integration to t_final, the
+    # real-space final state copied device -> host, every step
     host_in = torch.from_numpy(y0).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    for _ in range(2):
-        sim.set_state(host_in)
-        sim.advance_attempts(1)
-        sim.get_state(host_out)
+
+    def e2e_step():
+        s32.set_state(host_in)
+        s32.set_time(0.0, 1.0)
+        s32.advance(T, 1e-4, 1e-8)
+        s32.get_state(host_out)
+
+    e2e_step()
     barrier()
-    st0 = sim.stats()
+    st0 = s32.stats()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    Ke = max(3, K // 2)
+    Ke = max(2, K // 2)
     e0.record(stream)
     for _ in range(Ke):
-        sim.set_state(host_in)
-        sim.advance_attempts(1)
-        sim.get_state(host_out)
+        e2e_step()
     e1.record(stream)
     barrier()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1))
-    st1 = sim.stats()
+    st1 = s32.stats()
     e2e_value = (st1["rhs_evals"] - st0["rhs_evals"]) * N * world / (ms_e2e / 1e3) / 1e9
-    sim.close()
-    out["fp32"] = r32
+    s32.close()
+    del y0h
+    out = {}
     fp64 = None
     if not args.no_fp64:
-        r64 = timed("fp64", max(2, K // 2), 1, profile=True)
-        v64 = r64["rhs"] * N * world / (r64["ms"] / 1e3) / 1e9
-        p64 = r64["prof"]
-        t64 = max(p64.items(), key=lambda kv: kv[1][0])
-        fp64 = {"gpt_stage_s": v64, "ms_per_step": r64["ms"] / max(1, r64["rhs"] // 6),
-                "sim_s_per_wall_s": r64["sim_s"] / (r64["ms"] / 1e3),
-                "top_kernel": t64[0], "top_kernel_gbs": t64[1][1] / (t64[1][0] / 1e3) / 1e9}
-        r64["sim"].close()
-    r32["sim"].close()
+        s64, _, y0h = new_sim("fp64", tune=False)
+        r64 = timed(s64, y0h, 1, 1)
+        final64 = s64.get_state()
+        fl = nominal_flops_per_point_stage(N)
+        fp64 = dict(r64, nominal_tflops=r64["gpt_stage_s"] * 1e9 * fl / 1e12,
+                    nominal_flops_per_point_stage=fl)
+        out["error_per_field_fp32bulk_vs_fp64"] = relerr(final32, final64)
+        if not args.no_tight:
+            # tight-tolerance FP64 integration: both forms' final-state errors
+            s64.set_state_hat(y0h)
+            s64.set_time(0.0, 0.25)
+            stt = s64.advance(T, 1e-6, 1e-10)
+            tight = s64.get_state()
+            out["final_state_error_vs_rtol1e-6_fp64"] = {
+                "fp64": relerr(final64, tight), "fp32bulk": relerr(final32, tight),
+                "tight_attempts": int(stt["steps_accepted"] + stt["steps_rejected"])}
+        s64.close()
+        del y0h
+    fma = {"fp64_tflops": pfg.fma_peak("fp64"), "fp32_tflops": pfg.fma_peak("fp32")}
+    if fp64:
+        fp64["frac_of_measured_fp64_fma_peak"] = fp64["nominal_tflops"] / fma["fp64_tflops"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": r32["ms"] / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "%d^3 gamma'' KKS phase field, %d seeded nuclei, ARK4(3)6L[2]SA adaptive "
-                               "rtol 1e-4 atol 1e-8, FP32-bulk (FP64 state/norms)" % (n, 300 if n == 640 else 32),
+        "metric": METRIC, "value": r32["gpt_stage_s"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": r32["ms_per_integration"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 transforms/RHS, f64 state/norms", "data": "synthetic",
+        "config": {"workload": WORKLOAD2 if n == 256 else WORKLOAD2.replace("256^3", "%d^3" % n),
                    "grid": [n, n, n], "fields": 4, "method": "ARK4(3)6L[2]SA", "precision": "fp32bulk",
-                   "rtol": 1e-4, "atol": 1e-8, "l2": "inputs larger than L2 (FP64 k-space state %.0f MiB; no flush needed)" % (
+                   "rtol": 1e-4, "atol": 1e-8, "t_final": T, "step": "one integration from t=0 to t_final",
+                   "l2": "inputs larger than L2 (FP64 k-space state %.0f MiB; no flush needed)" % (
                        4 * n * n * (n // 2 + 1) * 16 / 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "sim_s_per_wall_s": sim_rate,
-        "autotune": {"fp32bulk": {k: r32["tuning"][k] for k in ("ms_before", "ms_after", "cfg")}},
-        "attempts": {"accepted": r32["accepted"], "rejected": r32["rejected"], "sim_s": r32["sim_s"]},
+        "sim_s_per_wall_s": r32["sim_s_per_wall_s"],
+        "fp32bulk": {k: v for k, v in r32.items() if k != "clocks"},
         "fp64_plain": fp64,
-        "gain_fp32bulk_vs_fp64": (value / fp64["gpt_stage_s"]) if fp64 else None,
+        "gain_at_equal_time": (r32["sim_s_per_wall_s"] / fp64["sim_s_per_wall_s"]) if fp64 else None,
+        "autotune": {"fp32bulk": {k: tun32[k] for k in ("ms_before", "ms_after", "cfg")}},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": src,
                      "algorithmic_bytes_per_launch": kbytes / klaunch, "launches": int(klaunch),
                      "traffic": traffic_from_profiles(kname, "fp32bulk", n),
-                     "timing": "CUDA events around every launch over %d further attempts (%.2f ms per attempt "
-                               "with the events)" % (K, r32["ms_profiled"] / K)},
+                     "timing": "CUDA events around every launch over one further integration"},
         "kernels": {k: {"ms": v[0], "launches": int(v[2]), "GBps": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None,
+                        "frac_of_hbm": v[1] / (v[0] / 1e3) / 1e9 / hbm if v[0] > 0 else None,
                         "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()},
-        "gpu_launches": launches,
+        "gpu_launches": launches * K,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y0.nbytes),
                 "d2h_bytes_per_step": int(y0.nbytes), "steps": Ke},
+        "fma_peak_measured": fma,
         "clocks": r32["clocks"],
     }
+    line.update(out)
     return line
+
+
+def run_big(n, t_final, rank=0, world=1):
+    """The largest single-GPU configuration: n^3 grid, 300 non-overlapping
+    nuclei of radius 4-12 cells, ARK4 adaptive at rtol 1e-4 in FP32-bulk from
+    t = 0 (h0 = 1 s) to t_final (a bounded stretch of the configuration's
+    300 s), with per-kernel rooflines; the plain FP64 path over two attempts
+    for the throughput ratio."""
+    import torch
+
+    import paper_2609_36100_gb300 as pfg
+    import synth
+
+    p = synth.load_params()
+    w0 = time.perf_counter()
+    y0 = synth.ic_spheres(n, 300, 4.0, 12.0, 5, p)
+    t_ic = time.perf_counter() - w0
+    N = n ** 3
+    hbm, _ = peaks()
+    y0d = torch.from_numpy(y0).to("cuda")
+    del y0
+    res = {"grid": [n, n, n], "nuclei": 300, "t_final": t_final, "ic_s": t_ic}
+    for prec in ("fp32bulk", "fp64"):
+        sim = pfg.Simulation((n, n, n), p, "ark4", prec)
+        sim.set_state(y0d)
+        if prec == "fp32bulk":
+            res["autotune"] = sim.autotune(reps=1)
+        sim.set_time(0.0, 1.0)
+        sim.advance_attempts(1)  # warm-up
+        torch.cuda.synchronize()
+        sim.set_state(y0d)
+        sim.set_time(0.0, 1.0)
+        st0 = sim.stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if prec == "fp32bulk":
+            sim.advance(t_final, 1e-4, 1e-8)
+        else:
+            sim.advance_attempts(2, t_final, 1e-4, 1e-8)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st1 = sim.stats()
+        rhs = st1["rhs_evals"] - st0["rhs_evals"]
+        r = {"ms": ms, "attempts": len(sim.attempts()), "sim_s": st1["t"] - st0["t"],
+             "gpt_stage_s": rhs * N / (ms / 1e3) / 1e9, "sim_s_per_wall_s": (st1["t"] - st0["t"]) / (ms / 1e3)}
+        if prec == "fp32bulk":
+            sim.profile(True)
+            sim.set_time(0.0, 1.0)
+            sim.advance_attempts(2, 1e30, 1e-4, 1e-8)
+            prof = sim.profile_read()
+            sim.profile(False)
+            r["kernels"] = {k: {"ms": v[0], "launches": int(v[2]),
+                                "GBps": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None,
+                                "frac_of_hbm": v[1] / (v[0] / 1e3) / 1e9 / hbm if v[0] > 0 else None,
+                                "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
+        res[prec] = r
+        sim.close()
+        torch.cuda.synchronize()
+    res["gain_fp32bulk_vs_fp64_gpt_stage_s"] = res["fp32bulk"]["gpt_stage_s"] / res["fp64"]["gpt_stage_s"]
+    return res
 
 
 def run_ensemble(K, t_final, rank=0, world=1):
@@ -403,7 +514,7 @@ def cpu_baseline(n, budget_s=15.0):
             break
     val = k * n ** 3 / el / 1e9
     return {"value": val, "unit": UNIT, "cores": om._WORKERS, "kind": "oracle",
-            "sample": "%d explicit RHS evaluation(s) of the %d^3 workload (FP64 numpy/scipy, %.1f s)" % (k, n, el)}
+            "sample": "%d explicit RHS evaluation(s) of the %d^3 config-2 initial state (FP64 numpy/scipy, %.1f s)" % (k, n, el)}
 
 
 def run_reference(args):
@@ -429,8 +540,9 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "%d^3 gamma'' KKS phase field, 32 seeded nuclei, ARK4(3)6L[2]SA stage RHS, FP64 "
-                                   "CPU oracle" % n, "grid": [n, n, n]},
+            "config": {"workload": WORKLOAD2 if n == 256 else WORKLOAD2.replace("256^3", "%d^3" % n),
+                       "grid": [n, n, n], "implementation": "FP64 CPU oracle (numpy/scipy) on the host cores",
+                       "step": "one explicit RHS evaluation (one ARK4 stage) of the initial state"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": om._WORKERS, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -451,6 +563,8 @@ def main():
         td.init_process_group("nccl")
         dist = td
     line = run_ours(args, rank, world, dist)
+    if args.big > 0 and rank == 0:
+        line["largest_grid"] = run_big(args.big, args.big_t)
     if args.ensemble > 0:
         line["ensemble"] = run_ensemble(args.ensemble, args.ensemble_t, rank, world)
     if args.surrogate > 0 and rank == 0:

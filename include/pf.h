@@ -38,11 +38,13 @@ extern "C" {
 #define PF_ECUDA (-3)        /* a CUDA runtime call failed                          */
 #define PF_ENONFINITE (-4)   /* NaN/Inf in the state or error estimate              */
 #define PF_ESTEPFAIL (-5)    /* step size fell below h_min or too many rejections  */
-#define PF_ETIMEOUT (-6)     /* a bounded device wait ran out                       */
+#define PF_ETIMEOUT (-6)     /* a bounded device loop ran out (pf_batch_round_cap)   */
 #define PF_EUNSUPPORTED (-7) /* grid size not 2,3,5-smooth/even, or method unknown */
 
 /* time integration methods (Sec. 4.4) */
 #define PF_EULER 1 /* ImEx (forward-backward) Euler, 1 RHS per step, no embedding */
+#define PF_ARK2 2  /* ARK2 of Giraldo, Kelly & Constantinescu (2013), 3 RHS per step, 1st-order embedding */
+#define PF_ARK3 3  /* ARK3(2)4L[2]SA of Kennedy & Carpenter, 4 RHS per step, 2nd-order embedding */
 #define PF_ARK4 4  /* ARK4(3)6L[2]SA of Kennedy & Carpenter, 6 RHS per step, 3rd-order embedding */
 
 /* arithmetic of the transforms and right-hand side */
@@ -79,7 +81,7 @@ typedef struct {
     double C11, C12, C44;
     double eps_star[3][6]; /* eigenstrain per variant */
     /* integrator */
-    int method;    /* PF_EULER or PF_ARK4 */
+    int method;    /* PF_EULER, PF_ARK2, PF_ARK3 or PF_ARK4 */
     int precision; /* PF_FP64 or PF_FP32BULK */
     double rtol, atol; /* WRMS weights w = 1/(rtol |y| + atol) (Eq. wrms_weights) */
     /* PI step-size controller (the paper uses ARKODE's; these constants are
@@ -108,11 +110,15 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
 void pf_destroy(pf_ctx* ctx);
 
 /* Set the state from real-space fields (layout above); `on_device` says
- * whether `fields` is a device pointer.  Forward FFT in FP64, y = FFT/N. */
+ * whether `fields` is a device pointer.  Forward FFT in FP64, y = FFT/N.
+ * Input holding a NaN or infinity is refused with PF_ENONFINITE and the
+ * previous state is kept. */
 int pf_set_state(pf_ctx* ctx, const double* fields, int on_device);
 /* Copy the real-space state out (inverse FFT in FP64). Caller owns `fields`. */
 int pf_get_state(pf_ctx* ctx, double* fields, int on_device);
-/* Copy the k-space state vector y (layout above) in or out. */
+/* Copy the k-space state vector y (layout above) in or out.  As with
+ * pf_set_state, non-finite input is refused with PF_ENONFINITE and the
+ * previous state is kept. */
 int pf_set_state_hat(pf_ctx* ctx, const void* y_hat, int on_device);
 int pf_get_state_hat(pf_ctx* ctx, void* y_hat, int on_device);
 
@@ -155,7 +161,7 @@ int pf_advance_attempts(pf_ctx* ctx, double t_final, double rtol, double atol, i
  * rounds, a conditional IF node per member that skips finished members) and
  * the host waits once; where the driver lacks conditional nodes, or in
  * PF_BATCH_POLLED mode, the round graph is relaunched under a host poll.  At
- * most 2^20 rounds (PF_ESTEPFAIL beyond).  `out` has n entries or is NULL. */
+ * most pf_batch_round_cap() rounds (PF_ETIMEOUT beyond).  `out` has n entries or is NULL. */
 int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, double atol, pf_stats* out);
 
 /* Driver of pf_batch_advance for this process: PF_BATCH_AUTO (device-looped
@@ -168,14 +174,27 @@ int pf_batch_mode(int mode);
 /* Rounds run by the last pf_batch_advance call of this process and whether
  * they ran device-looped (1) or host-polled (0); NULL pointers allowed. */
 int pf_batch_last(long long* rounds, int* looped);
+/* Round cap of pf_batch_advance for this process (default 2^20): a batch
+ * still live after that many rounds stops with PF_ETIMEOUT, each member left
+ * at its last accepted state and clock.  cap <= 0 only queries.  Returns the
+ * previous cap.  Not thread-safe against concurrent pf_batch_advance calls. */
+long long pf_batch_round_cap(long long cap);
 
 /* Total free energy F = int (f_b + f_el + f_ch) dV of the current state
  * (Sec. 4.1), FP64. */
 int pf_free_energy(pf_ctx* ctx, double* F_out);
 
-/* Integrator clock (for checkpoint/resume). */
+/* Integrator clock (for checkpoint/resume).  pf_set_time also resets the
+ * controller history (e_prev = 1, no pending rejection). */
 int pf_get_time(pf_ctx* ctx, double* t, double* h);
 int pf_set_time(pf_ctx* ctx, double t, double h);
+/* Controller history for an exact resume: the last accepted ||LTE||_WRMS
+ * (e_prev of the PI rule) and whether the last attempt was rejected (growth
+ * capped at 1 next).  A checkpoint is pf_get_state_hat + pf_get_time +
+ * pf_get_controller; restoring the three (pf_set_time before
+ * pf_set_controller) continues bitwise as if never interrupted. */
+int pf_get_controller(pf_ctx* ctx, double* e_prev, int* after_reject);
+int pf_set_controller(pf_ctx* ctx, double e_prev, int after_reject);
 int pf_get_stats(pf_ctx* ctx, pf_stats* out);
 /* Step attempts of the last pf_advance as (t, h, ||LTE||_WRMS, accepted)
  * quadruples; writes at most max_attempts of them to buf (NULL allowed) and
@@ -277,13 +296,23 @@ int pf_surrogate_step(pf_ctx* ctx, pf_fno* f, double tau, double h, double rtol,
  * library until the process exits.  Limits: each size even, 2,3,5-smooth,
  * 4..1024, and nz*ny*(nx/2+1) <= 135168 (a 64^3 grid); larger grids return
  * PF_EINVAL.  The first call on a device resolves the arrays' device
- * addresses (once per device), so make that first call before any stream
- * capture.  Every call reuses the same arrays: calls that overlap on the GPU
+ * addresses (once per device).  Every call copies its twiddle tables from
+ * host memory and synchronises `cuda_stream` before it returns, so no call
+ * can be captured into a CUDA graph.  Every call reuses the same arrays: calls that overlap on the GPU
  * (other threads or streams) race and must be serialised by the caller; no
  * part of the scratch needs clearing, each call overwrites what it reads.
  * No cudaMalloc/cudaFree or other allocating routine is called.  Errors:
  * PF_EINVAL, PF_EUNSUPPORTED, PF_ECUDA; pf_last_error(NULL) describes them. */
 int pf_state_to_real_noalloc(const pf_grid* grid, const void* y_hat, double* fields, void* cuda_stream);
+
+/* Measurement support (the paper has no counterpart): dense FMA throughput
+ * of the current device in TFLOP/s (2 flops per FMA), precision PF_FP64 or
+ * PF_FP32BULK (= FP32), from eight independent FMA chains per thread over
+ * 8 CTAs of 256 threads per SM; best of three timed launches after a warm-up
+ * on the legacy default stream (synchronises the device).  Gives the
+ * denominators of the ALU rooflines of the FP64 and FP32 kernels.
+ * Returns PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA. */
+int pf_fma_peak(int precision, double* tflops);
 
 /* Description of the last error of `ctx` (or of the last failed pf_create
  * when ctx is NULL). Never NULL. */

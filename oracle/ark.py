@@ -5,14 +5,22 @@ TEST INFRASTRUCTURE ONLY (see oracle/model.py).
 Stage equations (Eq. ARK_stage), step completion (Eq. ARK_method), embedded
 solution (Eq. ARK_embedding), WRMS norm and weights (Eqs. wrms_norm,
 wrms_weights). The WRMS norm is taken over the real-space values of all four
-fields, weights from the real-space previous solution (the paper applies the
-tolerances pointwise to the field change; reading stated in the design notes).
+fields (N = 4 n^3 entries), with weights from the real-space previous
+solution: the paper integrates in reciprocal space but applies the
+tolerances pointwise to the field change (Sec. 2.3), so the error estimate
+is transformed back to real space before it is normed.
 
-Tables:
+Tables (Sec. 4.4 names the family: first to fourth order with 1, 3, 4 and 6
+right-hand-side evaluations per step):
 * ImEx (forward-backward) Euler written as a 2-stage ARK pair;
+* ARK2 of Giraldo, Kelly & Constantinescu (2013): three stages, ESDIRK with
+  gamma = 1 - 1/sqrt(2), first-order embedding;
+* ARK3(2)4L[2]SA of Kennedy & Carpenter (2003): four stages, second-order
+  embedding;
 * ARK4(3)6L[2]SA of Kennedy & Carpenter (2003), the fourth-order method of
-  Sec. 2.3, with its third-order embedding. Its coefficients are checked by
-  the order-condition tests, not trusted as typed.
+  Sec. 2.3, with its third-order embedding.
+All coefficients are checked by the order-condition tests, not trusted as
+typed.
 """
 from __future__ import annotations
 
@@ -82,7 +90,46 @@ def ark436l2sa() -> Tableau:
     return Tableau("ark4(3)6l[2]sa", AE, AI, b.copy(), b.copy(), bt.copy(), bt.copy(), order=4, emb_order=3)
 
 
-TABLES = {"euler": euler, "ark4": ark436l2sa}
+def ark2_giraldo() -> Tableau:
+    """ARK2 of Giraldo, Kelly & Constantinescu (2013): explicit first stage,
+    ESDIRK implicit part with gamma = 1 - 1/sqrt(2), stiffly accurate, shared
+    weights b, first-order embedding; abscissae c = (0, 2 - sqrt(2), 1)."""
+    r2 = np.sqrt(2.0)
+    g = 1.0 - 1.0 / r2
+    a = (3.0 + 2.0 * r2) / 6.0
+    AE = np.array([[0.0, 0.0, 0.0], [2.0 - r2, 0.0, 0.0], [1.0 - a, a, 0.0]])
+    AI = np.array([[0.0, 0.0, 0.0], [g, g, 0.0], [1.0 / (2.0 * r2), 1.0 / (2.0 * r2), g]])
+    b = AI[2].copy()
+    bt = np.array([(4.0 - r2) / 8.0, (4.0 - r2) / 8.0, 1.0 / (2.0 * r2)])
+    return Tableau("ark2", AE, AI, b.copy(), b.copy(), bt.copy(), bt.copy(), order=2, emb_order=1)
+
+
+def ark324l2sa() -> Tableau:
+    """ARK3(2)4L[2]SA (Kennedy & Carpenter 2003): four stages, explicit first
+    stage, ESDIRK implicit part with gamma = 1767732205903/4055673282236,
+    stiffly accurate, shared weights b, second-order embedding."""
+    g = "1767732205903/4055673282236"
+    AE = _f([
+        ["0", "0", "0", "0"],
+        ["1767732205903/2027836641118", "0", "0", "0"],
+        ["5535828885825/10492691773637", "788022342437/10882634858940", "0", "0"],
+        ["6485989280629/16251701735622", "-4246266847089/9704473918619",
+         "10755448449292/10357097424841", "0"],
+    ])
+    AI = _f([
+        ["0", "0", "0", "0"],
+        [g, g, "0", "0"],
+        ["2746238789719/10658868560708", "-640167445237/6845629431997", g, "0"],
+        ["1471266399579/7840856788654", "-4482444167858/7529755066697",
+         "11266239266428/11593286722821", g],
+    ])
+    b = AI[3].copy()
+    bt = _v(["2756255671327/12835298489170", "-10771552573575/22201958757719",
+             "9247589265047/10645013368117", "2193209047091/5459859503100"])
+    return Tableau("ark3(2)4l[2]sa", AE, AI, b.copy(), b.copy(), bt.copy(), bt.copy(), order=3, emb_order=2)
+
+
+TABLES = {"euler": euler, "ark2": ark2_giraldo, "ark3": ark324l2sa, "ark4": ark436l2sa}
 
 
 def stability_function(tab: Tableau, zI: complex, zE: complex) -> complex:

@@ -16,9 +16,9 @@ from .build import LIB, build  # noqa: F401
 
 PF_OK = 0
 PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ESTEPFAIL, PF_ETIMEOUT, PF_EUNSUPPORTED = range(-1, -8, -1)
-PF_EULER, PF_ARK4 = 1, 4
+PF_EULER, PF_ARK2, PF_ARK3, PF_ARK4 = 1, 2, 3, 4
 PF_FP64, PF_FP32BULK = 0, 1
-METHODS = {"euler": PF_EULER, "ark4": PF_ARK4}
+METHODS = {"euler": PF_EULER, "ark2": PF_ARK2, "ark3": PF_ARK3, "ark4": PF_ARK4}
 PRECISIONS = {"fp64": PF_FP64, "fp32bulk": PF_FP32BULK, "fp32": PF_FP32BULK}
 
 
@@ -76,6 +76,10 @@ SIGNATURES = {
     "pf_get_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pf_set_time": (C.c_int, [_P, C.c_double, C.c_double]),
     "pf_get_stats": (C.c_int, [_P, C.POINTER(PFStats)]),
+    "pf_get_controller": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "pf_set_controller": (C.c_int, [_P, C.c_double, C.c_int]),
+    "pf_batch_round_cap": (C.c_longlong, [C.c_longlong]),
+    "pf_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "pf_get_attempts": (C.c_int, [_P, C.POINTER(C.c_double), C.c_int]),
     "pf_method_tableau": (C.c_int, [C.c_int] + [C.POINTER(C.c_double)] * 6),
     "pf_last_error": (C.c_char_p, [_P]),
@@ -313,6 +317,29 @@ class Simulation:
     def set_time(self, t, h):
         _check(lib().pf_set_time(self.ctx, float(t), float(h)), self.ctx)
 
+    def controller(self):
+        """(e_prev, after_reject) of the PI controller (checkpoint/resume)."""
+        e, r = C.c_double(), C.c_int()
+        _check(lib().pf_get_controller(self.ctx, C.byref(e), C.byref(r)), self.ctx)
+        return e.value, bool(r.value)
+
+    def set_controller(self, e_prev, after_reject):
+        _check(lib().pf_set_controller(self.ctx, float(e_prev), 1 if after_reject else 0), self.ctx)
+
+    def checkpoint(self):
+        """(k-space state as a host array, t, h, e_prev, after_reject)."""
+        a = np.empty(self.k_shape(), dtype=np.complex128)
+        _check(lib().pf_get_state_hat(self.ctx, a.ctypes.data_as(C.c_void_p), 0), self.ctx)
+        t, h = self.time()
+        e, r = self.controller()
+        return a, t, h, e, r
+
+    def restore(self, ck):
+        y, t, h, e, r = ck
+        self.set_state_hat(y)
+        self.set_time(t, h)
+        self.set_controller(e, r)
+
     def profile(self, on=True):
         _check(lib().pf_profile_enable(self.ctx, 1 if on else 0), self.ctx)
 
@@ -378,6 +405,19 @@ def batch_advance(sims, t_final, rtol=1e-4, atol=1e-8, polled=False):
         lib().pf_batch_mode(prev)
     _check(rc, sims[0].ctx if rc != PF_OK else None)
     return [s.as_dict() for s in st]
+
+
+def fma_peak(precision="fp64"):
+    """Measured dense FMA throughput of the current device (TFLOP/s)."""
+    v = C.c_double()
+    _check(lib().pf_fma_peak(PRECISIONS[precision] if isinstance(precision, str) else int(precision), C.byref(v)))
+    return v.value
+
+
+def batch_round_cap(cap=0):
+    """Set the round cap of batch_advance (cap > 0) and return the previous
+    one; cap <= 0 only queries."""
+    return int(lib().pf_batch_round_cap(int(cap)))
 
 
 def batch_last():

@@ -25,9 +25,13 @@ const double kRgas = 8.314462618;
 thread_local char g_create_err[256] = "no error";
 
 // ---------------------------------------------------------------------------
-// Butcher tables (Sec. 4.4).  ImEx Euler as a 2-stage pair; ARK4(3)6L[2]SA of
-// Kennedy & Carpenter (2003), six stages, ESDIRK gamma = 1/4, third-order
-// embedding.  Entries are the published rationals.
+// Butcher tables (Sec. 4.4: the first- to fourth-order members take 1, 3, 4
+// and 6 right-hand-side evaluations per step).  ImEx Euler as a 2-stage pair;
+// ARK2 of Giraldo, Kelly & Constantinescu (2013), three stages, ESDIRK gamma =
+// 1 - 1/sqrt(2), first-order embedding; ARK3(2)4L[2]SA and ARK4(3)6L[2]SA of
+// Kennedy & Carpenter (2003), four and six stages, second- and third-order
+// embeddings.  Entries are the published rationals (ARK2: the published
+// expressions in sqrt(2)).
 // ---------------------------------------------------------------------------
 struct Tableau {
     int s = 0;
@@ -47,6 +51,56 @@ bool make_tableau(int method, Tableau& t) {
         t.AI[1][1] = 1.0;
         t.bE[0] = 1.0;
         t.bI[1] = 1.0;
+        return true;
+    }
+    if (method == PF_ARK2) {
+        t.s = 3;
+        t.embedded = true;
+        t.emb_order = 1;
+        const double r2 = std::sqrt(2.0), g = 1.0 - 1.0 / r2, a = (3.0 + 2.0 * r2) / 6.0;
+        t.AE[1][0] = 2.0 - r2;
+        t.AE[2][0] = 1.0 - a;
+        t.AE[2][1] = a;
+        t.AI[1][0] = g;
+        t.AI[1][1] = g;
+        t.AI[2][0] = 1.0 / (2.0 * r2);
+        t.AI[2][1] = 1.0 / (2.0 * r2);
+        t.AI[2][2] = g;
+        const double bt[3] = {(4.0 - r2) / 8.0, (4.0 - r2) / 8.0, 1.0 / (2.0 * r2)};
+        for (int i = 0; i < 3; ++i) {
+            t.bE[i] = t.bI[i] = t.AI[2][i];
+            t.btE[i] = t.btI[i] = bt[i];
+        }
+        return true;
+    }
+    if (method == PF_ARK3) {
+        t.s = 4;
+        t.embedded = true;
+        t.emb_order = 2;
+        const double g = 1767732205903.0 / 4055673282236.0;
+        double (*E)[kMaxStages] = t.AE;
+        E[1][0] = 1767732205903.0 / 2027836641118.0;
+        E[2][0] = 5535828885825.0 / 10492691773637.0;
+        E[2][1] = 788022342437.0 / 10882634858940.0;
+        E[3][0] = 6485989280629.0 / 16251701735622.0;
+        E[3][1] = -4246266847089.0 / 9704473918619.0;
+        E[3][2] = 10755448449292.0 / 10357097424841.0;
+        double (*I)[kMaxStages] = t.AI;
+        I[1][0] = g;
+        I[1][1] = g;
+        I[2][0] = 2746238789719.0 / 10658868560708.0;
+        I[2][1] = -640167445237.0 / 6845629431997.0;
+        I[2][2] = g;
+        I[3][0] = 1471266399579.0 / 7840856788654.0;
+        I[3][1] = -4482444167858.0 / 7529755066697.0;
+        I[3][2] = 11266239266428.0 / 11593286722821.0;
+        I[3][3] = g;
+        const double bt[4] = {2756255671327.0 / 12835298489170.0, -10771552573575.0 / 22201958757719.0,
+                              9247589265047.0 / 10645013368117.0, 2193209047091.0 / 5459859503100.0};
+        for (int i = 0; i < 4; ++i) {
+            t.bE[i] = t.bI[i] = I[3][i];
+            t.btE[i] = t.btI[i] = bt[i];
+        }
         return true;
     }
     if (method == PF_ARK4) {
@@ -101,12 +155,12 @@ bool make_tableau(int method, Tableau& t) {
 // ---------------------------------------------------------------------------
 // FFT plans
 // ---------------------------------------------------------------------------
-// exp(-2 pi i k / n) evaluated in extended precision with the angle reduced
-// to the first octant, then rounded to double.
+// exp(-2 pi i k / n): cos and sin of the angle 2 pi k/n evaluated in long
+// double (no argument reduction beyond the library's), the four quarter
+// points k/n in {0, 1/4, 1/2, 3/4} set exactly, then rounded to double.
 void twiddle_table(int n, std::vector<double2>& tw) {
     tw.resize(n);
     for (int k = 0; k < n; ++k) {
-        // angle = 2 pi k / n; reduce with exact integer arithmetic on 8k/n
         const long double frac = (long double)k / (long double)n;  // in [0,1)
         const long double th = 2.0L * 3.141592653589793238462643383279502884L * frac;
         long double c = cosl(th), s = sinl(th);
@@ -819,6 +873,18 @@ void pf_destroy(pf_ctx* ctx) {
     delete ctx;
 }
 
+// PF_ENONFINITE if any of the n device doubles at v is NaN or infinite
+static int check_finite(pf_ctx* c, const double* v, long long n, const char* where) {
+    int* flag = reinterpret_cast<int*>(c->d_scalar + 3);
+    int* hflag = reinterpret_cast<int*>(c->h_scalar + 3);
+    PF_CUDA(c, cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+    launch_nonfinite(v, n, flag, c->stream);
+    PF_CUDA(c, cudaMemcpyAsync(hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (*hflag) return fail(c, PF_ENONFINITE, "%s: NaN or infinite input; state unchanged", where);
+    return PF_OK;
+}
+
 int pf_set_state(pf_ctx* c, const double* fields, int on_device) {
     if (!c || !fields) return fail(c, PF_EINVAL, "pf_set_state: NULL argument");
     cudaSetDevice(c->dev);
@@ -830,6 +896,7 @@ int pf_set_state(pf_ctx* c, const double* fields, int on_device) {
                                    c->stream));
         src = real;
     }
+    if (int rc = check_finite(c, src, 4 * g.N, "pf_set_state")) return rc;
     launch_x_pass<double>(g, c->ph, XM_R2C_REAL, nullptr, c->ynew, nullptr, nullptr, nullptr, 0, 0, src, nullptr,
                           c->stream);
     launch_y_pass<double>(g, c->ynew, 4, -1, c->stream);
@@ -862,9 +929,13 @@ int pf_get_state(pf_ctx* c, double* fields, int on_device) {
 int pf_set_state_hat(pf_ctx* c, const void* y_hat, int on_device) {
     if (!c || !y_hat) return fail(c, PF_EINVAL, "pf_set_state_hat: NULL argument");
     cudaSetDevice(c->dev);
-    PF_CUDA(c, cudaMemcpyAsync(c->y, y_hat, 4 * (size_t)c->g.NK * sizeof(double2),
+    // copied into the y_new buffer and checked there, so that a rejected
+    // input leaves the state untouched
+    PF_CUDA(c, cudaMemcpyAsync(c->ynew, y_hat, 4 * (size_t)c->g.NK * sizeof(double2),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (int rc = check_finite(c, reinterpret_cast<const double*>(c->ynew), 8 * c->g.NK, "pf_set_state_hat"))
+        return rc;
+    std::swap(c->y, c->ynew);
     return PF_OK;
 }
 
@@ -978,6 +1049,13 @@ int pf_advance_attempts(pf_ctx* c, double t_final, double rtol, double atol, int
 static int g_batch_mode = PF_BATCH_AUTO;
 static long long g_batch_rounds = 0;
 static int g_batch_looped = 0;
+static long long g_round_cap = 1LL << 20;
+
+long long pf_batch_round_cap(long long cap) {
+    const long long prev = g_round_cap;
+    if (cap > 0) g_round_cap = cap;
+    return prev;
+}
 
 int pf_batch_mode(int mode) {
     if (mode != PF_BATCH_AUTO && mode != PF_BATCH_POLLED) return fail(nullptr, PF_EINVAL, "pf_batch_mode: unknown mode");
@@ -1111,7 +1189,7 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
         unsigned long long rounds;
         int capped;
     };
-    const unsigned long long kRoundCap = 1ull << 20;
+    const unsigned long long kRoundCap = (unsigned long long)g_round_cap;
     LoopState* d_loop = nullptr;
     cudaGraphConditionalHandle* d_hif = nullptr;
     bool looped = false;
@@ -1177,7 +1255,7 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = fail(c0, PF_ECUDA, "batch launch: %s", cudaGetErrorString(e));
         rounds = (long long)hl.rounds;
-        if (!rc && hl.capped) rc = fail(c0, PF_ESTEPFAIL, "pf_batch_advance: no end after %llu rounds", hl.rounds);
+        if (!rc && hl.capped) rc = fail(c0, PF_ETIMEOUT, "pf_batch_advance: no end after %llu rounds", hl.rounds);
     } else if (!rc) {
         cudaError_t e = cudaGraphCreate(&batch, 0);
         for (int m = 0; m < n && e == cudaSuccess; ++m) {
@@ -1200,8 +1278,8 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
             int live = 0;
             for (int m = 0; m < n; ++m) live += h_ctl[m].active;
             if (!live) break;
-            if (rounds > (long long)kRoundCap) {
-                rc = fail(c0, PF_ESTEPFAIL, "pf_batch_advance: no end after %lld rounds", rounds);
+            if (rounds >= (long long)kRoundCap) {
+                rc = fail(c0, PF_ETIMEOUT, "pf_batch_advance: no end after %lld rounds", rounds);
                 break;
             }
         }
@@ -1286,6 +1364,20 @@ int pf_set_time(pf_ctx* c, double t, double h) {
     c->h = h;
     c->e_prev = 1.0;
     c->after_reject = false;
+    return PF_OK;
+}
+
+int pf_get_controller(pf_ctx* c, double* e_prev, int* after_reject) {
+    if (!c) return fail(c, PF_EINVAL, "pf_get_controller: NULL context");
+    if (e_prev) *e_prev = c->e_prev;
+    if (after_reject) *after_reject = c->after_reject ? 1 : 0;
+    return PF_OK;
+}
+
+int pf_set_controller(pf_ctx* c, double e_prev, int after_reject) {
+    if (!c || !(e_prev > 0) || !std::isfinite(e_prev)) return fail(c, PF_EINVAL, "pf_set_controller: bad argument");
+    c->e_prev = e_prev;
+    c->after_reject = after_reject != 0;
     return PF_OK;
 }
 

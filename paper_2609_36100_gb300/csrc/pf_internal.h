@@ -195,6 +195,8 @@ cudaError_t add_batch_more_node(cudaGraphNode_t* node, cudaGraph_t graph, const 
                                 const MemberCtl* ctl, int n, cudaGraphConditionalHandle hwhile,
                                 unsigned long long* rounds, unsigned long long cap, int* capped);
 void launch_reduce(const double* partials, int n, double scale, double* out, cudaStream_t s);
+// sets *flag (cleared beforehand) if any of the n doubles is NaN or infinite
+void launch_nonfinite(const double* v, long long n, int* flag, cudaStream_t s);
 void launch_energy_k(const Geo& g, const Phys& ph, const double2* y, const double2* hk, double* partials,
                      cudaStream_t s);
 int x_pass_blocks(const Geo& g, int f64);

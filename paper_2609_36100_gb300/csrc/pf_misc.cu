@@ -388,6 +388,81 @@ void launch_reduce(const double* partials, int n, double scale, double* out, cud
     k_reduce<<<1, 1024, 0, s>>>(partials, n, scale, out);
 }
 
+// *flag = 1 if any of the n FP64 words is NaN or infinite (all exponent bits
+// set); the flag is cleared by the caller before the launch
+__global__ void k_nonfinite(const unsigned long long* __restrict__ v, long long n, int* __restrict__ flag) {
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        bad |= ((v[i] >> 52) & 0x7ffull) == 0x7ffull;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+void launch_nonfinite(const double* v, long long n, int* flag, cudaStream_t s) {
+    k_nonfinite<<<152 * 8, 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(v), n, flag);
+}
+
+// FMA throughput probe: eight independent FMA chains per thread (enough to
+// hide the pipeline latency), `iters` rounds; the result is stored only if
+// it equals a value it cannot reach, so nothing is optimised away.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, T b, T c, T* sink) {
+    T a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (T)(threadIdx.x + i) * (T)1e-3;
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = fma(a[i], b, c);
+        }
+    }
+    T t = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += a[i];
+    if (t == (T)-12345.678) *sink = t;
+}
+
+}  // namespace pf
+
+extern "C" int pf_fma_peak(int precision, double* tflops) {
+    using namespace pf;
+    if (!tflops || (precision != 0 && precision != 1)) return -1;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -3;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    void* sink = nullptr;
+    if (cudaMalloc(&sink, 16) != cudaSuccess) return -2;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = nsm * 8, threads = 256;
+    // ~10^5 FMAs per thread in FP64 (the narrow pipe), ~5 10^6 in FP32
+    const int iters = precision == 0 ? 800 : 40000;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, 0);
+        if (precision == 0)
+            k_fma_peak<double><<<blocks, threads>>>(iters, 0.999999, 1e-7, (double*)sink);
+        else
+            k_fma_peak<float><<<blocks, threads>>>(iters, 0.999999f, 1e-7f, (float*)sink);
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;  // the first launch is a warm-up
+    }
+    const cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (err != cudaSuccess) return -3;
+    const double flops = 2.0 * 8.0 * 16.0 * (double)iters * blocks * threads;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return 0;
+}
+
+namespace pf {
+
 // k-space part of the free energy: sum_k w_k [ sum_v k.kappa_v.k |phi^_v|^2
 //                                              + sum_vq B_vq Re(h^_v conj h^_q) ]
 __global__ void k_energy_k(Geo g, Phys ph, const double2* __restrict__ y, const double2* __restrict__ hk,

@@ -83,7 +83,8 @@ bool smooth_even_axis(int n) {
     return m == 1;
 }
 
-// Twiddles exactly as the context path builds them.
+// Twiddles as the context path builds them: cos and sin of 2 pi k/n in long
+// double, the four quarter points exact, rounded to double (and to float).
 void twiddles(int n, double2* tw, float2* tw32) {
     for (int k = 0; k < n; ++k) {
         const long double th = 2.0L * 3.141592653589793238462643383279502884L * ((long double)k / (long double)n);

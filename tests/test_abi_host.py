@@ -50,6 +50,35 @@ def test_library_tableau_order_conditions(L):
     assert max_violation(AE, AI, btE, btI, 3) < 1e-14
     AE, AI, bE, bI, _, _ = pfg.method_tableau("euler")
     assert max_violation(AE, AI, bE, bI, 1) < 1e-15
+    for name, p in [("ark2", 2), ("ark3", 3)]:
+        AE, AI, bE, bI, btE, btI = pfg.method_tableau(name)
+        assert AE.shape == ({"ark2": 3, "ark3": 4}[name],) * 2
+        assert max_violation(AE, AI, bE, bI, p) < 1e-14
+        assert max_violation(AE, AI, btE, btI, p - 1) < 1e-14
+        assert max_violation(AE, AI, btE, btI, p) > 1e-3
+
+
+def test_library_and_oracle_tables_agree(L):
+    """The two typed copies of every table (library and oracle) agree to
+    rounding: a mistyped digit in either shows here as well as in the order
+    conditions."""
+    import oracle
+    for name in ("euler", "ark2", "ark3", "ark4"):
+        AE, AI, bE, bI, btE, btI = pfg.method_tableau(name)
+        t = oracle.TABLES[name]()
+        assert np.max(np.abs(AE - t.AE)) <= 4e-16 and np.max(np.abs(AI - t.AI)) <= 4e-16
+        assert np.max(np.abs(bE - t.bE)) <= 4e-16 and np.max(np.abs(bI - t.bI)) <= 4e-16
+        if t.btE is not None:
+            assert np.max(np.abs(btE - t.btE)) <= 4e-16 and np.max(np.abs(btI - t.btI)) <= 4e-16
+
+
+def test_batch_round_cap_query_and_set(L):
+    prev = pfg.batch_round_cap(0)
+    assert prev == 1 << 20
+    assert pfg.batch_round_cap(5) == prev
+    assert pfg.batch_round_cap(0) == 5
+    pfg.batch_round_cap(prev)
+    assert pfg.batch_round_cap(0) == prev
 
 
 def test_unknown_method_rejected(L):

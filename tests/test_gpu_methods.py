@@ -1,0 +1,122 @@
+"""The second- and third-order members of the ImEx-ARK family (Sec. 4.4:
+ARK2 of Giraldo et al. and ARK3(2)4L[2]SA) through the C ABI against the FP64
+oracle, and the FP32-bulk error estimate against the FP64 one."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pfg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_36100_gb300 as m
+    m.build()
+    return m
+
+
+def relerr(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.array([np.linalg.norm((a[f] - b[f]).ravel()) / max(np.linalg.norm(b[f].ravel()), 1e-300)
+                     for f in range(a.shape[0])])
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.mark.parametrize("meth", ["ark2", "ark3"])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (24, 20, 30)])
+def test_steps_and_lte_vs_oracle(pfg, params, meth, shape):
+    """Four fixed steps of 0.5 s: state rel L2 <= 1e-11 per field, the WRMS
+    norms of the embedded error estimates to 1e-9 relative (FP64)."""
+    if shape[0] == shape[1] == shape[2]:
+        y0 = synth.ic_spheres(shape[0], 3, 3.0, 5.0, 9, params)
+    else:
+        y0 = synth.random_state(shape, 5, phi_scale=0.9)
+    m = oracle.Model(shape, params)
+    yh = m.to_k(y0)
+    tab = oracle.TABLES[meth]()
+    errs = []
+    for _ in range(4):
+        yh, e, _ = oracle.ark_step(m, yh, 0.5, tab, params["rtol"], params["atol"])
+        errs.append(e)
+    with pfg.Simulation(shape, params, meth, "fp64") as s:
+        s.set_state(y0)
+        dc = to_np(s.state_hat())[0, 0, 0, 0]
+        got_e = [s.step(0.5) for _ in range(4)]
+        got = to_np(s.state_hat())
+        st = s.stats()
+    assert got[0, 0, 0, 0] == dc
+    assert np.all(relerr(got, yh) <= 1e-11), relerr(got, yh)
+    np.testing.assert_allclose(got_e, errs, rtol=1e-9)
+    assert st["rhs_evals"] == 4 * {"ark2": 3, "ark3": 4}[meth]  # Sec. 4.4: 3 and 4 per step
+
+
+@pytest.mark.parametrize("meth", ["ark2", "ark3"])
+def test_fp32bulk_steps(pfg, params, meth):
+    y0 = synth.ic_spheres(32, 3, 3.0, 5.0, 9, params)
+    m = oracle.Model(y0.shape[1:], params)
+    yh = m.to_k(y0)
+    for _ in range(4):
+        yh, _, _ = oracle.ark_step(m, yh, 0.5, oracle.TABLES[meth]())
+    with pfg.Simulation(y0.shape[1:], params, meth, "fp32bulk") as s:
+        s.set_state(y0)
+        for _ in range(4):
+            s.step(0.5)
+        got = to_np(s.state_hat())
+    assert np.all(relerr(got, yh) <= 1e-5), relerr(got, yh)
+
+
+def test_ark3_adaptive_replayed(pfg, params):
+    """Adaptive ARK3(2)4L[2]SA at rtol 1e-4 (controller exponent q = 3): the
+    oracle replays the GPU's attempts; errors agree to 1e-6 relative,
+    decisions wherever |e - 1| > 1e-6, and the final state to 1e-11."""
+    y0 = synth.ic_spheres(32, 3, 3.0, 5.0, 9, params)
+    with pfg.Simulation(y0.shape[1:], params, "ark3", "fp64") as s:
+        s.set_state(y0)
+        st = s.advance(8.0, 1e-4, 1e-8)
+        att = s.attempts()
+        got = to_np(s.state_hat())
+    assert st["t"] == pytest.approx(8.0, rel=1e-14)
+    m = oracle.Model(y0.shape[1:], params)
+    replay = [(h, ok) for (_, h, _, ok) in att]
+    yh, t, log = oracle.advance(m, m.to_k(y0), 0.0, 8.0, oracle.ark324l2sa(), params, 1e-4, 1e-8, replay=replay)
+    for (tg, hg, eg, okg), (to, ho, eo, _) in zip(att, log):
+        assert tg == pytest.approx(to, rel=1e-12, abs=1e-12)
+        assert eg == pytest.approx(eo, rel=1e-6)
+        if abs(eo - 1.0) > 1e-6:
+            assert okg == (eo <= 1.0)
+    assert np.all(relerr(got, yh) <= 1e-11)
+
+
+def test_fp32bulk_error_estimate_tracks_fp64(pfg, params):
+    """The FP32-bulk form accumulates its local error estimate in FP32 and
+    transforms it in FP32 before the FP64 WRMS norm.  Along an adaptive
+    FP32-bulk run, every attempt is repeated in the FP64 path from the same
+    state with the same step: the two norms agree to 1e-2 relative (1e-2 of
+    0.05 absolute where the norm is small), so the accept/reject decisions
+    agree wherever ||LTE|| is more than 1 % away from 1."""
+    import torch
+    y0 = synth.ic_spheres(32, 3, 3.0, 5.0, 9, params)
+    with pfg.Simulation(y0.shape[1:], params, "ark4", "fp32bulk") as s32, \
+            pfg.Simulation(y0.shape[1:], params, "ark4", "fp64") as s64:
+        s32.set_state(y0)
+        s32.set_time(0.0, 0.5)
+        n = 0
+        while n < 12:
+            before = s32.state_hat()
+            s32.advance_attempts(1)
+            (t, h, e32, ok), = s32.attempts()
+            s64.set_state_hat(before)
+            e64 = s64.step(h)
+            assert abs(e32 - e64) <= 1e-2 * max(e64, 0.05), (n, h, e32, e64)
+            if abs(e64 - 1.0) > 1e-2:
+                assert ok == (e64 <= 1.0)
+            n += 1
+        torch.cuda.synchronize()

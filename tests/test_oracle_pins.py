@@ -63,6 +63,26 @@ def test_ark4_order_conditions():
     assert np.allclose(t.bI, t.AI[-1], atol=0)
 
 
+def test_ark2_ark3_order_conditions():
+    """ARK2 (Giraldo et al. 2013) and ARK3(2)4L[2]SA (Kennedy & Carpenter
+    2003), the second- and third-order members of the family of Sec. 4.4:
+    coupled order conditions to their orders, embeddings one lower, and the
+    shared structure (explicit first stage, ESDIRK diagonal, equal abscissae,
+    stiffly accurate)."""
+    for name, p, gam in [("ark2", 2, 1.0 - 1.0 / math.sqrt(2.0)),
+                         ("ark3", 3, 1767732205903 / 4055673282236)]:
+        t = oracle.TABLES[name]()
+        assert max_violation(t.AE, t.AI, t.bE, t.bI, p) < 1e-14
+        assert max_violation(t.AE, t.AI, t.btE, t.btI, p - 1) < 1e-14
+        assert max_violation(t.AE, t.AI, t.bE, t.bI, p + 1) > 1e-3
+        assert max_violation(t.AE, t.AI, t.btE, t.btI, p) > 1e-3
+        assert np.all(np.triu(t.AE) == 0.0)
+        assert t.AI[0, 0] == 0.0 and np.allclose(np.diag(t.AI)[1:], gam, rtol=1e-15)
+        assert np.allclose(t.cE, t.cI, atol=1e-15)
+        assert np.allclose(t.bI, t.AI[-1], atol=0)
+        assert t.cE[-1] == pytest.approx(1.0, abs=1e-15)
+
+
 def test_euler_table_is_first_order_only():
     t = oracle.euler()
     assert max_violation(t.AE, t.AI, t.bE, t.bI, 1) < 1e-15
@@ -74,14 +94,36 @@ def test_euler_table_is_first_order_only():
 # (stiff/non-stiff split of Eqs. composition and order)
 # --------------------------------------------------------------------------
 def _R(tab, zI, zE):
-    """Scalar-test-equation amplification written from the Butcher arrays:
-    R = 1 + (zI bI + zE bE)^T (I - zI AI - zE AE)^{-1} 1."""
-    s = tab.s
-    M = np.eye(s) - zI * tab.AI - zE * tab.AE
-    return 1.0 + (zI * tab.bI + zE * tab.bE) @ np.linalg.solve(M, np.ones(s))
+    """The oracle's scalar-test-equation amplification (pinned below against
+    closed forms, Taylor agreement with exp and L-stability)."""
+    return complex(oracle.stability_function(tab, zI, zE)).real
 
 
-@pytest.mark.parametrize("meth", ["euler", "ark4"])
+def test_stability_function_pins():
+    """R(zI, zE) of the test equation y' = (lambda_I + lambda_E) y:
+    * ImEx Euler has the closed form (1 + zE) / (1 - zI);
+    * a method of order p agrees with exp(z) to at least O(z^{p+1}) along
+      either part alone and along both together (halving z divides the
+      error by 2^{p+1} or more: a linear stability function may match exp
+      beyond the method's order);
+    * the stiffly accurate ESDIRK parts are L-stable: R(z, 0) -> 0 like 1/z
+      as z -> -inf."""
+    e = oracle.euler()
+    for zI, zE in [(-0.3, 0.2), (-5.0, -0.7), (-1e3, 0.0)]:
+        assert _R(e, zI, zE) == pytest.approx((1 + zE) / (1 - zI), rel=1e-14)
+    for name, p in [("ark2", 2), ("ark3", 3), ("ark4", 4)]:
+        t = oracle.TABLES[name]()
+        for dirn in [(1.0, 0.0), (0.0, 1.0), (0.6, 0.4)]:
+            errs = []
+            for z in (-0.04, -0.02):
+                zI, zE = z * dirn[0], z * dirn[1]
+                errs.append(abs(_R(t, zI, zE) - math.exp(zI + zE)))
+            assert errs[0] / errs[1] >= 0.85 * 2.0 ** (p + 1), (name, dirn, errs)
+        r = [abs(_R(t, -z, 0.0)) for z in (1e3, 1e4, 1e5)]
+        assert r[0] < 1e-2 and r[1] / r[0] == pytest.approx(0.1, rel=0.05) and r[2] / r[1] == pytest.approx(0.1, rel=0.05)
+
+
+@pytest.mark.parametrize("meth", ["euler", "ark2", "ark3", "ark4"])
 @pytest.mark.parametrize("mode", [(1, 0, 0), (2, 3, 1), (4, 4, 4)])
 def test_single_mode_amplification(meth, mode, params):
     shape = (8, 8, 8)
@@ -122,6 +164,121 @@ def test_dispersion_continuum_limit(params):
     rate = math.log(m.to_r(y1)[1][0, 0, 0] / y0[1][0, 0, 0]) / dt
     want = -params["L"] * (params["kappa_iso"] * k2 + 2 * params["omega_bar"])
     assert rate == pytest.approx(want, rel=1e-3)
+
+
+# --------------------------------------------------------------------------
+# interpolation function and barrier of Sec. 4.1 (Eq. f_b)
+# --------------------------------------------------------------------------
+def test_h_interp_is_the_quintic_smoothstep():
+    """h is the polynomial of degree 5 with h(0) = 0, h(1) = 1 and vanishing
+    first and second derivatives at 0 and 1 (six conditions fix it). The
+    coefficients are recovered from samples of the oracle's h by a least-
+    squares fit of degree 7 (the two top coefficients vanish: degree <= 5);
+    the conditions are then checked on the fitted polynomial, together with
+    h(1/2) = 1/2, the symmetry h(1 - phi) = 1 - h(phi), and h_prime = h'."""
+    x = np.linspace(-0.5, 1.5, 41)
+    c = np.polynomial.polynomial.polyfit(x, oracle.h_interp(x), 7)
+    assert np.all(np.abs(c[6:]) < 1e-9)
+    P = np.polynomial.Polynomial(c[:6])
+    d1, d2 = P.deriv(1), P.deriv(2)
+    assert abs(P(0.0)) < 1e-12 and abs(P(1.0) - 1.0) < 1e-12
+    for z in (0.0, 1.0):
+        assert abs(d1(z)) < 1e-10 and abs(d2(z)) < 1e-9
+    assert oracle.h_interp(0.0) == 0.0 and oracle.h_interp(1.0) == 1.0 and oracle.h_interp(0.5) == 0.5
+    u = np.linspace(-0.3, 1.3, 17)
+    assert np.max(np.abs(oracle.h_interp(1.0 - u) - (1.0 - oracle.h_interp(u)))) < 1e-14
+    assert np.max(np.abs(oracle.h_prime(u) - d1(u))) < 1e-9
+    # h rises monotonically from 0 to 1 on [0, 1]
+    v = np.linspace(0.0, 1.0, 101)
+    assert np.all(np.diff(oracle.h_interp(v)) > 0)
+
+
+def _pair_part(params, phi, eps):
+    """The pairwise-barrier share of d f_b / d phi: the oracle's derivative
+    with the pairwise weights on minus the same with them off."""
+    on = oracle.Model((2, 2, 2), synth.load_params(pair_eps=eps))
+    off = oracle.Model((2, 2, 2), synth.load_params(pair_eps=eps, omega_vq=0.0))
+    return on.dfb_dphi(phi) - off.dfb_dphi(phi)
+
+
+def test_pair_barrier_is_literal_outside_the_band(params):
+    """Eq. f_b's omega_vq |phi_v phi_q| has the derivative omega_vq
+    sgn(phi_v) |phi_q| wherever phi_v phi_q != 0. The regularised barrier
+    equals it exactly wherever |phi_v phi_q| >= eps, stays within it
+    (|force| <= omega |phi_q|) inside the band, and its energy density is
+    within eps/2 of |phi_v phi_q| everywhere."""
+    rng = np.random.default_rng(11)
+    phi = np.zeros((3, 2000))
+    phi[0] = rng.uniform(-0.3, 1.3, 2000)
+    phi[1] = rng.uniform(-0.3, 1.3, 2000)  # only the (1, 2) pair is active
+    w = params["omega_pair"][0]
+    for eps in (0.02, 0.005):
+        f = _pair_part(params, phi, eps)
+        prod = phi[0] * phi[1]
+        out = np.abs(prod) >= eps
+        assert out.sum() > 1000 and (~out).sum() > 20
+        lit0 = w * np.sign(phi[0]) * np.abs(phi[1])
+        lit1 = w * np.sign(phi[1]) * np.abs(phi[0])
+        assert np.max(np.abs(f[0][out] - lit0[out])) <= 1e-15
+        assert np.max(np.abs(f[1][out] - lit1[out])) <= 1e-15
+        assert np.all(np.abs(f[0][~out]) <= w * np.abs(phi[1][~out]) * (1 + 1e-15))
+        assert np.all(f[2] == 0.0)
+        m = oracle.Model((2, 2, 2), synth.load_params(pair_eps=eps))
+        assert np.max(np.abs(m.pair_abs(prod) - np.abs(prod))) <= eps / 2 * (1 + 1e-15)
+
+
+def test_pair_barrier_converges_to_the_literal_term(params):
+    """On a fixed state the regularised force tends to the literal one as
+    eps -> 0: the largest deviation shrinks with eps and vanishes once eps
+    is below min |phi_v phi_q|."""
+    rng = np.random.default_rng(12)
+    phi = np.zeros((3, 500))
+    phi[0] = rng.uniform(0.01, 1.0, 500) * rng.choice([-1, 1], 500)
+    phi[1] = rng.uniform(0.01, 1.0, 500)
+    lit = params["omega_pair"][0] * np.sign(phi[0]) * np.abs(phi[1])
+    dev = [np.max(np.abs(_pair_part(params, phi, e)[0] - lit)) for e in (0.02, 0.005, 0.001, 1e-5)]
+    assert dev[0] > dev[1] > dev[2] > 0.0
+    assert np.min(np.abs(phi[0] * phi[1])) > 1e-5 and dev[3] <= 1e-15
+
+
+def test_pair_width_keeps_the_band_explicitly_stable(params):
+    """Inside the band |phi_v phi_q| < eps the regularised pairwise force is
+    linear in phi_v with rate L omega phi_q^2 / eps, at most L omega / eps
+    (inside a variant-q precipitate), and it is treated explicitly. The
+    explicit ARK4 part is stable on [-x*, 0] of the negative real axis
+    (from the stability function with zI = 0). At the paper's largest stable
+    fourth-order step (2.25 s, Sec. 2.3) the band's rate stays inside that
+    interval for the library's width eps = 0.02 and leaves it for widths
+    of 0.005 and below, which is why the width is not taken smaller."""
+    t = oracle.ark436l2sa()
+    xs = np.linspace(0.01, 10.0, 2000)
+    stable = [abs(_R(t, 0.0, -x)) <= 1.0 + 1e-12 for x in xs]
+    xstar = xs[stable.index(False) - 1]
+    rate = params["L"] * params["omega_pair"][0]
+    assert 2.25 * rate / params["pair_eps"] <= xstar
+    assert 2.25 * rate / 0.005 > xstar
+
+
+def test_trajectory_converges_as_pair_width_shrinks():
+    """Two touching nuclei of different variants (the pairwise barrier acts
+    on their overlap), 20 fixed ARK4 steps of 0.1 s (inside the explicit
+    limit of every width used): the states obtained with eps = 0.02, 0.01,
+    0.005, 0.0025 form a Cauchy sequence whose successive differences
+    shrink, so the regularised model tends to a limit as eps -> 0."""
+    base = synth.load_params()
+    nuc = [(0, (6.5, 10.0, 10.0), (4.0,) * 3), (1, (13.5, 10.0, 10.0), (4.0,) * 3)]
+    y0 = synth.nuclei_ic((20, 20, 20), base, nuc, x_inside=base["B_v"])
+    res = []
+    for eps in (0.02, 0.01, 0.005, 0.0025):
+        m = oracle.Model(y0.shape[1:], synth.load_params(pair_eps=eps))
+        yh = m.to_k(y0)
+        for _ in range(20):
+            yh, _, _ = oracle.ark_step(m, yh, 0.1, oracle.ark436l2sa(), want_lte=False)
+        res.append(m.to_r(yh))
+    for f in range(3):
+        d = [np.linalg.norm(res[i][f] - res[i + 1][f]) / np.linalg.norm(res[i + 1][f]) for i in range(3)]
+        assert d[0] > d[1] > d[2] > 0.0, (f, d)
+        assert d[0] < 1e-2
 
 
 # --------------------------------------------------------------------------
@@ -381,6 +538,23 @@ def test_controller_formula(params):
     assert c.accept(1.0, 1e-12) == pytest.approx(1.0)  # growth capped at 1 after a rejection
 
 
+def test_controller_fixed_point(params):
+    """A property of the PI rule rather than its formula retyped: on a
+    problem whose error is exactly e(h) = (h / h1)^q the accepted steps
+    settle where e = e_prev = e*, i.e. safety e*^{-(k1 - k2)/q} = 1, so
+    e* = safety^{q/(k1 - k2)}; a wrong exponent moves e*. The controller
+    constants are proposed (the paper uses ARKODE's and states none), so
+    this pins the rule as specified, not a value from the paper."""
+    q = 4
+    c = oracle.Controller(params, q)
+    h = 0.01
+    for _ in range(200):
+        e = (h / 1.0) ** q
+        h = c.accept(h, e)
+    want = params["safety"] ** (q / (params["k1"] - params["k2"]))
+    assert (h / 1.0) ** q == pytest.approx(want, rel=1e-6)
+
+
 # --------------------------------------------------------------------------
 # temporal order (Sec. 2.3, Fig. 4a): first order for ImEx Euler, fourth order
 # for ARK4(3)6L[2]SA, measured on a smooth, non-stiff nonlinear state (coarse
@@ -423,3 +597,23 @@ def test_temporal_order_euler_and_ark4():
         assert 0.9 <= s <= 1.1
     for s in slopes(oracle.ark436l2sa(), [1.0, 0.5, 0.25]):
         assert s >= 3.5
+
+
+def test_temporal_order_ark2_ark3():
+    """Measured orders of the second- and third-order members (Sec. 2.3 /
+    Fig. 4a reports the same family): slopes near 2 and at least 2.7."""
+    p = synth.load_params(dx=2.0, omega_vq=0.0)
+    y0 = _smooth_state()
+    m = oracle.Model(y0.shape[1:], p)
+    yh0 = m.to_k(y0)
+    T = 8.0
+    ref = _run(m, yh0, oracle.ark436l2sa(), 1.0 / 32, T)
+
+    def slopes(tab, dts):
+        e = [np.sqrt(np.mean((_run(m, yh0, tab, dt, T) - ref) ** 2)) for dt in dts]
+        return [math.log(e[i] / e[i + 1]) / math.log(dts[i] / dts[i + 1]) for i in range(len(dts) - 1)]
+
+    for s in slopes(oracle.ark2_giraldo(), [0.5, 0.25, 0.125]):
+        assert 1.8 <= s <= 2.3
+    for s in slopes(oracle.ark324l2sa(), [1.0, 0.5, 0.25]):
+        assert s >= 2.7
