@@ -227,9 +227,10 @@ const char* pf_kernel_name(int kind);
 /* Launch schedule of a context: tuned tile widths of the z stage-assembly
  * and completion / y / elastic passes, rows per CTA of the x passes (0 =
  * built-in heuristic), the radix order of each axis (count + up to 10 radices
- * in {2,3,4,5,8,16}, for x, y, z: ints 4-36), and the tile width of the
- * forward z pass (int 37).  PF_TUNE_LEN ints. */
-#define PF_TUNE_LEN 38
+ * in {2,3,4,5,8,16}, for x, y, z: ints 4-36), the tile width of the forward
+ * z pass (int 37) and the compiled radix plan of the elastic pass (int 38;
+ * 0 = the z axis's own plan).  PF_TUNE_LEN ints. */
+#define PF_TUNE_LEN 39
 int pf_get_tuning(pf_ctx* ctx, int* cfg, int n);
 int pf_set_tuning(pf_ctx* ctx, const int* cfg, int n);
 /* Autotuner: times `reps` step attempts per candidate schedule on the

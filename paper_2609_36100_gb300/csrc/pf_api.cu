@@ -1406,6 +1406,7 @@ int pf_get_tuning(pf_ctx* c, int* cfg, int n) {
     cfg[2] = c->g.tx_el;
     cfg[3] = c->g.rp;
     cfg[37] = c->g.tx_zf;
+    cfg[38] = c->g.el_pid;
     plan_to_cfg(c->g.px, cfg + 4);
     plan_to_cfg(c->g.py, cfg + 4 + 11);
     plan_to_cfg(c->g.pz, cfg + 4 + 22);
@@ -1420,6 +1421,9 @@ int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
     g.tx_el = cfg[2];
     g.rp = cfg[3];
     g.tx_zf = cfg[37];
+    if (cfg[38] != 0 && compiled_plan_len(cfg[38]) != g.nz)
+        return fail(c, PF_EINVAL, "pf_set_tuning: elastic plan %d does not have length nz", cfg[38]);
+    g.el_pid = cfg[38];
     AxisPlan* pl[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
@@ -1529,6 +1533,13 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
                 cfg[slot] = v;
                 trial(cfg);
             }
+        }
+        // compiled plans of length nz for the fused elastic pass
+        for (int pid = 0; pid <= compiled_plan_count(); ++pid) {
+            if (pid > 0 && compiled_plan_len(pid) != c->g.nz) continue;
+            std::memcpy(cfg, best, sizeof cfg);
+            cfg[38] = pid;
+            trial(cfg);
         }
         const int ns[3] = {c->g.nx, c->g.ny, c->g.nz};
         for (int a = 0; a < 3; ++a) {

@@ -560,6 +560,16 @@ inline bool plan_is(const AxisPlan& p, int n, Radices<Rs...>) {
     return true;
 }
 
+// length of compiled plan PID (0 for an unknown PID)
+template <int PID = 1>
+inline int fixed_plan_len(int pid) {
+    if constexpr (PID > kFixedPlans) {
+        return 0;
+    } else {
+        return pid == PID ? FixedPlan<PID>::N : fixed_plan_len<PID + 1>(pid);
+    }
+}
+
 // PID of a plan (0: not compiled)
 template <int PID = 1>
 inline int fixed_plan_id(const AxisPlan& p) {
@@ -630,6 +640,44 @@ template <int R, int... Rs>
 struct RadInfo<Radices<R, Rs...>> {
     static constexpr int count = 1 + (int)sizeof...(Rs);
     static constexpr int first = R;
+    static constexpr int last = RadInfo<Radices<Rs...>>::count == 0 ? R : RadInfo<Radices<Rs...>>::last;
+};
+template <>
+struct RadInfo<Radices<>> {
+    static constexpr int count = 0;
+    static constexpr int first = 1;
+    static constexpr int last = 1;
+};
+
+// the radix order reversed: the inverse transform of a tile whose forward
+// transform ended with radix R starts with radix R, so that the last forward
+// stage and the first inverse stage see the same element positions
+template <class A, class B>
+struct RevCat;
+template <int... Bs>
+struct RevCat<Radices<>, Radices<Bs...>> {
+    using type = Radices<Bs...>;
+};
+template <int A, int... As, int... Bs>
+struct RevCat<Radices<A, As...>, Radices<Bs...>> {
+    using type = typename RevCat<Radices<As...>, Radices<A, Bs...>>::type;
+};
+template <class R>
+using Reversed = typename RevCat<R, Radices<>>::type;
+// the radices strictly between the first and the last of a list
+template <class R>
+struct DropFirst;
+template <int A, int... Rs>
+struct DropFirst<Radices<A, Rs...>> {
+    using type = Radices<Rs...>;
+};
+template <class R>
+struct PlanInner {
+    using type = Reversed<typename DropFirst<Reversed<typename DropFirst<R>::type>>::type>;
+};
+template <int A>
+struct PlanInner<Radices<A>> {
+    using type = Radices<>;
 };
 
 // fft_cols with the compile-time plan PID (same contract)

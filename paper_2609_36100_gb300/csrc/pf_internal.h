@@ -27,6 +27,9 @@ inline unsigned magic_u32(unsigned d) { return d <= 1 ? 0u : (unsigned)((0xfffff
 // radix schedule (8s first, then 4/2, 3s, 5s) and division magic of one axis
 bool make_axis_plan(int n, AxisPlan& p, bool prefer16 = false);
 bool make_axis_plan_radices(int n, const int* rad, int nr, AxisPlan& p);
+// length of compiled (compile-time) plan `pid` (0 if unknown), and how many there are
+int compiled_plan_len(int pid);
+int compiled_plan_count();
 
 // Grid geometry and the per-axis wave-number tables k_m = 2 pi m / (n d)
 // (FP64, Nyquist index taken as +pi/d).
@@ -52,6 +55,7 @@ struct Geo {
     int tx_y, tx_z, tx_el;  // tuned tile widths (kx columns) of the strided passes, 0 = heuristic
     int rp;                  // tuned row pairs per CTA in the x passes, 0 = heuristic
     int tx_zf;               // tuned tile width of the forward z pass, 0 = heuristic
+    int el_pid;              // compiled plan of the fused elastic pass (length nz), 0 = the z-axis plan
 };
 
 // Model constants of the real-space and elastic terms in one compute type,

@@ -2,6 +2,9 @@
 #include "pf_xpass.cuh"
 
 namespace pf {
+int compiled_plan_len(int pid) { return fixed_plan_len(pid); }
+int compiled_plan_count() { return kFixedPlans; }
+
 // plan from an explicit radix order (each radix in {2,3,4,5,8,16}, product n)
 bool make_axis_plan_radices(int n, const int* rad, int nr, AxisPlan& p) {
     if (nr < 1 || nr > kMaxRadices) return false;

@@ -207,9 +207,229 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
     }
 }
 
+// ---------------------------------------------------------------------------
+// Elastic pass with a compile-time plan, one shared tile per CTA: the three
+// h fields of TX kx columns stay in one [field][kz][col] tile, transformed in
+// place.  The last forward stage (radix R), the Green's contraction and the
+// first inverse stage (radix R again: the inverse runs the forward radix
+// order reversed, so both stages see the element positions j + (N/R) t) run
+// in the registers of one thread per (column, j), which holds all three
+// fields of its R wave numbers: no shared-memory round trip and no barrier
+// between the forward transform, the contraction and the inverse.  Middle
+// stages of longer plans run in place through registers (every load of a
+// stage, a barrier, then the stores).  NT = TX N / R threads, one per
+// (column, j) of the fused stage.
+// ---------------------------------------------------------------------------
+// one radix-R stage of NF fields of the [f][pos][TX] tile S, in place: each
+// thread first loads every butterfly it owns, the CTA synchronises, then the
+// butterflies are computed and stored (and the CTA synchronises again)
+template <int R, int SIGN, int TX, int N, int NS, int NF, int NT, typename T2>
+__device__ __forceinline__ void tile_stage_inplace(T2* S, const T2* __restrict__ tw) {
+    constexpr int M = N / R, JOBS = NF * TX * M, JPT = (JOBS + NT - 1) / NT, TWS = N / (NS * R);
+    T2 v[JPT][R];
+#pragma unroll
+    for (int u = 0; u < JPT; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        if (JOBS % NT == 0 || idx < JOBS) {
+            const int f = idx / (TX * M), r = idx - f * (TX * M), col = r % TX, j = r / TX;
+            const T2* src = S + f * (N * TX) + j * TX + col;
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[u][t] = src[t * M * TX];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < JPT; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        if (JOBS % NT == 0 || idx < JOBS) {
+            const int f = idx / (TX * M), r = idx - f * (TX * M), col = r % TX, j = r / TX;
+            const int jq = j / NS, k = j - jq * NS;
+            if constexpr (NS > 1) apply_twiddles<R, SIGN>(v[u], tw, k * TWS);
+            Bfly<R, SIGN, T2>::run(v[u]);
+            T2* dst = S + f * (N * TX) + (jq * NS * R + k) * TX + col;
+#pragma unroll
+            for (int t = 0; t < R; ++t) dst[t * NS * TX] = v[u][t];
+        }
+    }
+    __syncthreads();
+}
+
+// stage from global (first forward stage) or to global (last inverse stage):
+// no staging, the tile is written only by loads from global or read only
+template <int R, int SIGN, int TX, int N, int NS, int NF, int NT, typename T2, class Ld, class St>
+__device__ __forceinline__ void tile_stage_io(const T2* __restrict__ tw, Ld ld, St st) {
+    constexpr int M = N / R, JOBS = NF * TX * M, TWS = N / (NS * R);
+    for (int idx = threadIdx.x; idx < JOBS; idx += NT) {
+        const int f = idx / (TX * M), r = idx - f * (TX * M), col = r % TX, j = r / TX;
+        T2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = ld(f, j + t * M, col);
+        const int jq = j / NS, k = j - jq * NS;
+        if constexpr (NS > 1) apply_twiddles<R, SIGN>(v, tw, k * TWS);
+        Bfly<R, SIGN, T2>::run(v);
+        const int base = jq * NS * R + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) st(f, base + t * NS, col, v[t]);
+    }
+}
+
+// in-place stages of a radix list between the first and the last, NS growing
+template <int SIGN, int TX, int N, int NS, int NF, int NT, typename T2>
+__device__ __forceinline__ void tile_stages_inplace(T2*, const T2*, Radices<>) {}
+template <int SIGN, int TX, int N, int NS, int NF, int NT, typename T2, int R, int... Rest>
+__device__ __forceinline__ void tile_stages_inplace(T2* S, const T2* tw, Radices<R, Rest...>) {
+    tile_stage_inplace<R, SIGN, TX, N, NS, NF, NT>(S, tw);
+    tile_stages_inplace<SIGN, TX, N, NS * R, NF, NT>(S, tw, Radices<Rest...>{});
+}
+
+// CTAs per SM the register budget is planned for: 128 registers a thread
+// where the fused stage holds few values, the full file for one CTA where it
+// holds 3 x 16 complex values (FP32) or any FP64 tile
+template <typename T, int PID, int NT>
+constexpr int elastic_min_blocks() {
+    constexpr int RL = RadInfo<typename FixedPlan<PID>::Rad>::last;
+    constexpr int regs = (RL >= 16 || sizeof(T) == 8) ? 255 : 128;
+    return NT * regs <= 65536 ? 65536 / (NT * regs) : 1;
+}
+
+template <typename T, int TX, int PID, int NT>
+__global__ void __launch_bounds__(NT, elastic_min_blocks<T, PID, NT>())
+    k_z_elastic_fused(Geo g, Phys ph, typename Cx<T>::t* __restrict__ H) {
+    PF_SKIP_INACTIVE(g);
+    using T2 = typename Cx<T>::t;
+    using Fwd = typename FixedPlan<PID>::Rad;
+    using Inv = Reversed<Fwd>;
+    constexpr int N = FixedPlan<PID>::N;
+    constexpr int RF = RadInfo<Fwd>::first, RL = RadInfo<Fwd>::last;
+    constexpr int M = N / RL;  // the fused stage's butterflies per column
+    static_assert(NT == TX * M, "one thread per (column, j) of the fused stage");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* S = reinterpret_cast<T2*>(smraw);  // [3][N][TX]
+    const int ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    const int ncol = min(TX, g.nxh - kx0);
+    const long long rowoff = (long long)ky * g.nxh + kx0;
+    const long long zs = (long long)g.ny * g.nxh;
+    const T2* tw = twiddles<T2>(g.pz);
+    // forward stage 1: global -> tile
+    {
+        auto ld = [&](int f, int kz, int col) -> T2 {
+            return col < ncol ? H[(long long)f * g.NK + rowoff + kz * zs + col] : T2{0, 0};
+        };
+        auto st = [&](int f, int kz, int col, T2 v) { S[f * (N * TX) + kz * TX + col] = v; };
+        tile_stage_io<RF, -1, TX, N, 1, 3, NT>(tw, ld, st);
+    }
+    __syncthreads();
+    // forward middle stages (in place)
+    tile_stages_inplace<-1, TX, N, RF, 3, NT>(S, tw, typename PlanInner<Fwd>::type{});
+    // fused: last forward stage, contraction, first inverse stage
+    {
+        const int col = threadIdx.x % TX, j = threadIdx.x / TX;
+        T2 h[3][RL];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const T2* src = S + f * (N * TX) + j * TX + col;
+#pragma unroll
+            for (int t = 0; t < RL; ++t) h[f][t] = src[t * M * TX];
+            apply_twiddles<RL, -1>(h[f], tw, j);  // NS = N / RL: k = j, table stride 1
+            Bfly<RL, -1, T2>::run(h[f]);
+        }
+        __syncthreads();
+        const T invN = std::is_same<T, float>::value ? (T)g.invN32 : (T)g.invN;
+        const PhysT<T>& pt = phys_t<T>(ph);
+        const T kxv = kval<T>(g, 0, kx0 + (col < ncol ? col : 0)), kyv = kval<T>(g, 1, ky);
+#pragma unroll
+        for (int t = 0; t < RL; ++t) {
+            T Bm[3][3];
+            elastic_kernel<T>(pt, kxv, kyv, kval<T>(g, 2, j + t * M), Bm);
+            const T2 a = h[0][t], b = h[1][t], c = h[2][t];
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+                h[v][t] = T2{(Bm[v][0] * a.x + Bm[v][1] * b.x + Bm[v][2] * c.x) * invN,
+                             (Bm[v][0] * a.y + Bm[v][1] * b.y + Bm[v][2] * c.y) * invN};
+        }
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            Bfly<RL, +1, T2>::run(h[f]);  // first inverse stage: NS = 1, no twiddles
+            T2* dst = S + f * (N * TX) + (j * RL) * TX + col;
+#pragma unroll
+            for (int t = 0; t < RL; ++t) dst[t * TX] = h[f][t];
+        }
+    }
+    __syncthreads();
+    // inverse middle stages (in place), then the last inverse stage: tile -> global
+    tile_stages_inplace<+1, TX, N, RL, 3, NT>(S, tw, typename PlanInner<Inv>::type{});
+    {
+        auto ld = [&](int f, int kz, int col) -> T2 { return S[f * (N * TX) + kz * TX + col]; };
+        auto st = [&](int f, int kz, int col, T2 v) {
+            if (col < ncol) H[(long long)f * g.NK + rowoff + kz * zs + col] = v;
+        };
+        tile_stage_io<RF, +1, TX, N, N / RF, 3, NT>(tw, ld, st);
+    }
+}
+
+// compiled plans of two or more stages run the fused elastic pass
+template <int PID>
+constexpr bool fused_elastic_ok() {
+    return PID > 0 && RadInfo<typename FixedPlan<PID>::Rad>::count >= 2;
+}
+
+template <typename T, int PID>
+static bool launch_z_elastic_fused(const Geo& g, const Phys& ph, void* H, int tuned, cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    if constexpr (!fused_elastic_ok<PID>()) {
+        return false;
+    } else {
+        constexpr int N = FixedPlan<PID>::N;
+        constexpr int M = N / RadInfo<typename FixedPlan<PID>::Rad>::last;
+        // widest tile (16, 8, 4, 2 columns) with NT <= 1024 threads and at most
+        // ~100 KB of shared memory, or the tuned width if it fits
+        auto fits = [&](int tx) { return tx * M <= 1024 && 3 * (size_t)tx * N * sizeof(T2) <= 100 * 1024; };
+        int TX = 0;
+        for (int tx : {16, 8, 4, 2})
+            if (fits(tx) && (TX == 0 || (tuned > 0 && tx == tuned))) TX = tx;
+        if (tuned <= 0)
+            for (int tx : {16, 8, 4, 2})
+                if (fits(tx) && tx / 2 < g.nxh) {
+                    TX = tx;
+                    break;
+                }
+        if (TX == 0) return false;
+        const size_t sm = 3 * (size_t)TX * N * sizeof(T2);
+        dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);
+#define PF_ELF(TXC)                                                                                       if constexpr ((TXC) * M <= 1024) {                                                                        set_smem(k_z_elastic_fused<T, TXC, PID, (TXC) * M>, sm);                                              k_z_elastic_fused<T, TXC, PID, (TXC) * M><<<grid, (TXC) * M, sm, s>>>(g, ph, reinterpret_cast<T2*>(H));     }
+        switch (TX) {
+            case 16: PF_ELF(16); break;
+            case 8: PF_ELF(8); break;
+            case 4: PF_ELF(4); break;
+            default: PF_ELF(2); break;
+        }
+#undef PF_ELF
+        return true;
+    }
+}
+
 template <typename T>
 void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
+    bool done = false;
+    if (g.pz.n == g.nz && g.nz >= 32) {
+        const int pid = (g.el_pid > 0 && fixed_plan_len(g.el_pid) == g.nz) ? g.el_pid : fixed_plan_id(g.pz);
+        switch (pid) {
+            case 1: done = launch_z_elastic_fused<T, 1>(g, ph, H, g.tx_el, s); break;
+            case 2: done = launch_z_elastic_fused<T, 2>(g, ph, H, g.tx_el, s); break;
+            case 3: done = launch_z_elastic_fused<T, 3>(g, ph, H, g.tx_el, s); break;
+            case 4: done = launch_z_elastic_fused<T, 4>(g, ph, H, g.tx_el, s); break;
+            case 5: done = launch_z_elastic_fused<T, 5>(g, ph, H, g.tx_el, s); break;
+            case 6: done = launch_z_elastic_fused<T, 6>(g, ph, H, g.tx_el, s); break;
+            case 7: done = launch_z_elastic_fused<T, 7>(g, ph, H, g.tx_el, s); break;
+            case 8: done = launch_z_elastic_fused<T, 8>(g, ph, H, g.tx_el, s); break;
+            case 9: done = launch_z_elastic_fused<T, 9>(g, ph, H, g.tx_el, s); break;
+            case 10: done = launch_z_elastic_fused<T, 10>(g, ph, H, g.tx_el, s); break;
+            case 11: done = launch_z_elastic_fused<T, 11>(g, ph, H, g.tx_el, s); break;
+            default: break;
+        }
+    }
+    if (done) return;
     const int TX = tuned_cols<T>(g, g.tx_el, g.nz, 4, 128 * 1024);
     const size_t sm = 4 * (size_t)TX * g.nz * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);

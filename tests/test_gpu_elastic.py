@@ -1,0 +1,60 @@
+"""The fused elastic pass (last forward z stage, Green's contraction of
+Eq. u_gov and first inverse stage in registers; the inverse runs the forward
+radix order reversed) against the FP64 oracle's explicit right-hand side,
+for every compiled radix plan of each length and every tile width, on grids
+whose half-spectrum rows leave a ragged last tile."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+# compiled plans (id: length) of the library
+PLANS = {1: 256, 2: 256, 3: 128, 4: 128, 5: 64, 6: 64, 7: 160, 8: 96, 9: 120, 10: 192, 11: 640}
+
+
+@pytest.fixture(scope="module")
+def pfg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_36100_gb300 as m
+    m.build()
+    return m
+
+
+def relerr(a, b):
+    return np.array([np.linalg.norm((a[f] - b[f]).ravel()) / np.linalg.norm(b[f].ravel()) for f in range(4)])
+
+
+@pytest.mark.parametrize("pid", sorted(PLANS))
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32bulk", 2e-5)])
+def test_fused_elastic_plan_matches_oracle(pfg, params, pid, prec, tol):
+    import torch
+    n = PLANS[pid]
+    shape = (n, 6, 10)  # nz = n; nx/2 + 1 = 6 columns: every tile width leaves a ragged tail
+    y = synth.random_state(shape, 40 + pid)
+    m = oracle.Model(shape, params)
+    yh = m.to_k(y)
+    ref = m.rhs_explicit(yh)
+    dev = torch.from_numpy(yh).to("cuda")
+    with pfg.Simulation(shape, params, "ark4", prec) as s:
+        for tx in (2, 4, 8, 16):
+            cfg = s.tuning()
+            cfg[2] = tx
+            cfg[38] = pid
+            s.set_tuning(cfg)
+            assert s.tuning()[38] == pid
+            got = s.rhs_explicit(dev).cpu().numpy()
+            err = relerr(got, ref)
+            assert np.all(err <= tol), (tx, err)
+
+
+def test_elastic_plan_of_wrong_length_refused(pfg, params):
+    with pfg.Simulation((64, 8, 8), params, "ark4", "fp64") as s:
+        cfg = s.tuning()
+        cfg[38] = 1  # length 256
+        with pytest.raises(pfg.PFError):
+            s.set_tuning(cfg)
