@@ -106,7 +106,7 @@ SIGNATURES = {
                                     C.POINTER(C.c_double)]),
 }
 NKERNELS = 11
-TUNE_LEN = 39
+TUNE_LEN = 40
 _DPTR_ARGS = {"pf_method_tableau"}
 
 _lib = None

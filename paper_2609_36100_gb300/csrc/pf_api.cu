@@ -574,13 +574,13 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef 
             ProfScope p(c, PF_K_Y, 4 * NK * 2 * cb);
             launch_y_pass<T>(g, c->W, 4, +1, s);
         }
+        int nb = 0;
         {
             ProfScope p(c, PF_K_X_WRMS, 4 * NK * cb + 4 * N * rb);
-            launch_x_pass<T>(g, ph, XM_WRMS, c->W, nullptr, nullptr, c->R1, c->partials, c->prm.rtol, c->prm.atol,
-                             nullptr, nullptr, s);
+            nb = launch_x_pass<T>(g, ph, XM_WRMS, c->W, nullptr, nullptr, c->R1, c->partials, c->prm.rtol,
+                                  c->prm.atol, nullptr, nullptr, s);
         }
         {
-            const int nb = x_pass_blocks(g, sizeof(T) == 8);
             ProfScope p(c, PF_K_REDUCE, nb * 8.0);
             launch_reduce(c->partials, nb, 1.0 / (4.0 * (double)g.N), c->d_scalar, s);
         }
@@ -1407,6 +1407,7 @@ int pf_get_tuning(pf_ctx* c, int* cfg, int n) {
     cfg[3] = c->g.rp;
     cfg[37] = c->g.tx_zf;
     cfg[38] = c->g.el_pid;
+    cfg[39] = c->g.xf_off;
     plan_to_cfg(c->g.px, cfg + 4);
     plan_to_cfg(c->g.py, cfg + 4 + 11);
     plan_to_cfg(c->g.pz, cfg + 4 + 22);
@@ -1424,6 +1425,7 @@ int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
     if (cfg[38] != 0 && compiled_plan_len(cfg[38]) != g.nz)
         return fail(c, PF_EINVAL, "pf_set_tuning: elastic plan %d does not have length nz", cfg[38]);
     g.el_pid = cfg[38];
+    g.xf_off = cfg[39] != 0;
     AxisPlan* pl[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
@@ -1533,6 +1535,12 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
                 cfg[slot] = v;
                 trial(cfg);
             }
+        }
+        // fused or staged FP32 x passes
+        for (int v : {0, 1}) {
+            std::memcpy(cfg, best, sizeof cfg);
+            cfg[39] = v;
+            trial(cfg);
         }
         // compiled plans of length nz for the fused elastic pass
         for (int pid = 0; pid <= compiled_plan_count(); ++pid) {

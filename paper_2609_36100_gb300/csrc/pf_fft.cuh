@@ -664,6 +664,14 @@ struct RevCat<Radices<A, As...>, Radices<Bs...>> {
 };
 template <class R>
 using Reversed = typename RevCat<R, Radices<>>::type;
+// product of a radix list (the transform length)
+template <class R>
+struct RadProd;
+template <int... Rs>
+struct RadProd<Radices<Rs...>> {
+    static constexpr int value = (Rs * ... * 1);
+};
+
 // the radices strictly between the first and the last of a list
 template <class R>
 struct DropFirst;

@@ -56,6 +56,7 @@ struct Geo {
     int rp;                  // tuned row pairs per CTA in the x passes, 0 = heuristic
     int tx_zf;               // tuned tile width of the forward z pass, 0 = heuristic
     int el_pid;              // compiled plan of the fused elastic pass (length nz), 0 = the z-axis plan
+    int xf_off;              // 1: the FP32 x passes use the staged kernel instead of the fused one
 };
 
 // Model constants of the real-space and elastic terms in one compute type,
@@ -161,10 +162,11 @@ void launch_z_stage(const Geo& g, const Phys& ph, const double2* y, const StageT
                     void* W, cudaStream_t s);
 template <typename T>
 void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s);
+// returns the number of CTAs launched (the WRMS mode writes one partial sum each)
 template <typename T>
-void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
-                   double* partials, double rtol, double atol, const double* real_in, double* real_out,
-                   cudaStream_t s);
+int launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
+                  double* partials, double rtol, double atol, const double* real_in, double* real_out,
+                  cudaStream_t s);
 template <typename T>
 void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s);
 // forward z FFT; scale_mode 0: y = W/N to FP64 (set_state); 1: f^E scaling

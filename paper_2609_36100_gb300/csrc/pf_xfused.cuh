@@ -1,0 +1,324 @@
+// Fused x passes (FP32 compute type): packed real transforms along x with the
+// real-space physics between them, organised so that the physics runs in the
+// registers of the threads that finish the inverse transform and start the
+// forward one.
+//
+// The forward transform of a line uses the radix order Fwd = (RM, ...); the
+// inverse runs it reversed, so its last stage (radix RM, sub-transform size
+// M = N/RM) leaves butterfly j holding the elements x = j + M t (t < RM) --
+// exactly the inputs of butterfly j of the forward first stage.  One thread
+// per (row pair, j) therefore takes the last inverse stage of every input
+// field, evaluates the physics at its RM positions of both rows, and applies
+// the first forward stage to every output field without a shared-memory
+// round trip.  The C2R packing of two real rows into one complex line is
+// folded into the first inverse stage (read straight from the staged
+// half-spectrum rows), the R2C unpacking into the store.  Stages ping-pong
+// between two shared-memory tiles of skewed lines.
+#pragma once
+#include "pf_xpass.cuh"
+
+namespace pf {
+
+enum XFMode { XF_PHYS1_H = 0, XF_PHYS1_RHS = 1, XF_PHYS2 = 2, XF_WRMS = 3 };
+template <int MODE>
+struct XFIO {
+    static constexpr int FIN = MODE == XF_PHYS2 ? 3 : 4;  // input lines per row pair
+    static constexpr int FOUT = MODE == XF_WRMS ? 0 : (MODE == XF_PHYS1_H ? 3 : 4);
+};
+
+// stages of a radix list, sub-transform size growing from NS: cur -> oth,
+// then the pointers swap (the result is in cur)
+template <int SIGN, int N, int NS, typename T2>
+__device__ __forceinline__ void xf_run(T2*&, T2*&, int, const T2*, Radices<>) {}
+template <int SIGN, int N, int NS, typename T2, int R, int... Rest>
+__device__ __forceinline__ void xf_run(T2*& cur, T2*& oth, int nl, const T2* tw, Radices<R, Rest...>) {
+    fft_stage_fixed<R, SIGN, N, NS>(cur, oth, nl, skewed_len(N), tw);
+    __syncthreads();
+    T2* t = cur;
+    cur = oth;
+    oth = t;
+    xf_run<SIGN, N, NS * R>(cur, oth, nl, tw, Radices<Rest...>{});
+}
+
+template <class Fwd, int P>
+struct XFShape {
+    static constexpr int N = RadProd<Fwd>::value;
+    static constexpr int RM = RadInfo<Fwd>::first;  // radix of the fused stages
+    static constexpr int M = N / RM;                 // butterflies per line in the fused stages
+    static constexpr int NT = P * M;                 // one thread per (row pair, butterfly)
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps, at most 1024 threads");
+    static constexpr int LS = N + N / 16;            // skewed line stride
+};
+
+template <typename T, class Fwd, int P, int MODE>
+__global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph, const float2* __restrict__ in,
+                                                                  float2* __restrict__ out, float* __restrict__ R,
+                                                                  const float* __restrict__ Rin,
+                                                                  double* __restrict__ partials, float rt, float at) {
+    PF_SKIP_INACTIVE(g);
+    using T2 = float2;
+    using Sh = XFShape<Fwd, P>;
+    constexpr int N = Sh::N, RM = Sh::RM, M = Sh::M, NT = Sh::NT, LS = Sh::LS, NXH = N / 2 + 1;
+    constexpr int FIN = XFIO<MODE>::FIN, FOUT = XFIO<MODE>::FOUT;
+    using Inv = Reversed<Fwd>;
+    constexpr int R1 = RadInfo<Inv>::first;  // first inverse stage
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* A = reinterpret_cast<T2*>(smraw);
+    T2* B = A + P * 4 * LS;
+    const int npairs = g.nz * g.ny / 2;
+    const int rp0 = blockIdx.x * P;
+    const long long NK = g.NK, N3 = g.N;
+    const T2* tw = g.px.tw32;
+    __shared__ double red[NT / 32 + 1];
+
+    // 1. the raw half-spectrum rows of the input fields -> B (cp.async)
+    for (int e = threadIdx.x; e < P * FIN * 2 * NXH; e += NT) {
+        const int r = e / NXH, k = e - r * NXH;  // raw row r = (rp FIN + f) 2 + (0: row y, 1: row y+1)
+        const int pf = r >> 1, rp = pf / FIN, f = pf - rp * FIN;
+        if (rp0 + rp < npairs)
+            cp_async<8>(B + e, in + (long long)f * NK + (2LL * (rp0 + rp) + (r & 1)) * NXH + k);
+        else
+            B[e] = T2{0.f, 0.f};
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // 2. first inverse stage (radix R1, no twiddles), packing Z = a + i b of
+    //    the two rows' half spectra (Hermitian extension, imaginary parts of
+    //    DC and Nyquist dropped): B -> A
+    {
+        constexpr int M1 = N / R1;
+        for (int idx = threadIdx.x; idx < P * FIN * M1; idx += NT) {
+            const int line = idx / M1, j = idx - line * M1;
+            const T2* ra = B + line * 2 * NXH;
+            const T2* rb = ra + NXH;
+            T2 v[R1];
+#pragma unroll
+            for (int t = 0; t < R1; ++t) {
+                const int x = j + t * M1;
+                const bool lo = x <= N / 2;
+                const int k = lo ? x : N - x;
+                T2 a = ra[k], b = rb[k];
+                if (k == 0 || k == N / 2) {
+                    a.y = 0.f;
+                    b.y = 0.f;
+                }
+                v[t] = lo ? T2{a.x - b.y, a.y + b.x} : T2{a.x + b.y, b.x - a.y};
+            }
+            Bfly<R1, +1, T2>::run(v);
+            T2* d = A + line * LS;
+#pragma unroll
+            for (int t = 0; t < R1; ++t) d[skew<true>(j * R1 + t)] = v[t];
+        }
+    }
+    __syncthreads();
+    T2* cur = A;
+    T2* oth = B;
+    // 3. inverse stages between the first and the last
+    xf_run<+1, N, R1>(cur, oth, P * FIN, tw, typename PlanInner<Inv>::type{});
+    // 4. fused: last inverse stage, physics, first forward stage
+    const int rp = threadIdx.x / M, j = threadIdx.x - (threadIdx.x / M) * M;
+    const bool valid = rp0 + rp < npairs;
+    const long long row = 2LL * (rp0 + rp);
+    T2 vin[FIN][RM];
+#pragma unroll
+    for (int f = 0; f < FIN; ++f) {
+        const T2* src = cur + (rp * FIN + f) * LS;
+#pragma unroll
+        for (int t = 0; t < RM; ++t) vin[f][t] = src[skew<true>(j + t * M)];
+        apply_twiddles<RM, +1>(vin[f], tw, j);  // NS = M: twiddle exponent j t
+        Bfly<RM, +1, T2>::run(vin[f]);
+    }
+    if constexpr (MODE == XF_WRMS) {
+        // sum of squares of the weighted error w_i LTE_i (weights from the
+        // stored real-space y_{n-1}); compensated FP32 sum per thread, FP64
+        // across threads and CTAs
+        float sh = 0.f, sl = 0.f;
+        if (valid) {
+#pragma unroll
+            for (int t = 0; t < RM; ++t) {
+                const int x = j + t * M;
+#pragma unroll
+                for (int f = 0; f < FIN; ++f) {
+                    const float* yr = Rin + f * N3 + row * N + x;
+                    const float a = __fdividef(vin[f][t].x, __fmaf_rn(rt, fabsf(yr[0]), at));
+                    const float b = __fdividef(vin[f][t].y, __fmaf_rn(rt, fabsf(yr[N]), at));
+                    const DF s1 = df_two_sum(sh, __fmul_rn(a, a));
+                    const DF s2 = df_two_sum(s1.h, __fmul_rn(b, b));
+                    sh = s2.h;
+                    sl = __fadd_rn(sl, __fadd_rn(s1.l, s2.l));
+                }
+            }
+        }
+        double acc = f2d_bits(sh) + f2d_bits(sl);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int i = 0; i < (NT + 31) / 32; ++i) s += red[i];
+            partials[blockIdx.x] = s;
+        }
+        return;
+    } else {
+        const PhysT<float>& pt = ph.t32;
+        T2 vout[FOUT][RM];
+#pragma unroll
+        for (int t = 0; t < RM; ++t) {
+            const int x = j + t * M;
+            float Xr[2], pr[2][3], er[2][3];
+            if constexpr (MODE == XF_PHYS2) {
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const float* b = Rin + f * N3 + row * N + x;
+                    const float u0 = valid ? b[0] : 0.f, u1 = valid ? b[N] : 0.f;
+                    if (f == 0) {
+                        Xr[0] = u0;
+                        Xr[1] = u1;
+                    } else {
+                        pr[0][f - 1] = u0;
+                        pr[1][f - 1] = u1;
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    er[0][v] = vin[v][t].x;
+                    er[1][v] = vin[v][t].y;
+                }
+            } else {
+                Xr[0] = vin[0][t].x;
+                Xr[1] = vin[0][t].y;
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    pr[0][v] = vin[1 + v][t].x;
+                    pr[1][v] = vin[1 + v][t].y;
+                    er[0][v] = 0.f;
+                    er[1][v] = 0.f;
+                }
+                if (R && valid) {
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        float* b = R + f * N3 + row * N + x;
+                        b[0] = vin[f][t].x;
+                        b[N] = vin[f][t].y;
+                    }
+                }
+            }
+            if constexpr (MODE == XF_PHYS1_H) {
+#pragma unroll
+                for (int v = 0; v < 3; ++v) vout[v][t] = T2{hfun(pr[0][v]), hfun(pr[1][v])};
+            } else {
+                float q[2], gv[2][3];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) Pt::rhs<float>(pt, Xr[r], pr[r], er[r], q[r], gv[r]);
+                vout[0][t] = T2{q[0], q[1]};
+#pragma unroll
+                for (int v = 0; v < 3; ++v) vout[1 + v][t] = T2{gv[0][v], gv[1][v]};
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < FOUT; ++f) {
+            Bfly<RM, -1, T2>::run(vout[f]);  // first forward stage: NS = 1, no twiddles
+            T2* d = oth + (rp * FOUT + f) * LS;
+#pragma unroll
+            for (int t = 0; t < RM; ++t) d[skew<true>(j * RM + t)] = vout[f][t];
+        }
+        __syncthreads();
+        {
+            T2* t = cur;
+            cur = oth;
+            oth = t;
+        }
+        // 5. the remaining forward stages
+        xf_run<-1, N, RM>(cur, oth, P * FOUT, tw, typename DropFirst<Fwd>::type{});
+        // 6. R2C unpacking of the two rows of each line and the store
+        for (int e = threadIdx.x; e < P * FOUT * NXH; e += NT) {
+            const int line = e / NXH, k = e - line * NXH, lrp = line / FOUT, f = line - lrp * FOUT;
+            if (rp0 + lrp >= npairs) continue;
+            const T2 Zk = cur[line * LS + skew<true>(k)];
+            const T2 Zm = cur[line * LS + skew<true>(k == 0 ? 0 : N - k)];
+            const T2 a = T2{(Zk.x + Zm.x) * 0.5f, (Zk.y - Zm.y) * 0.5f};
+            const T2 b = T2{(Zk.y + Zm.y) * 0.5f, (Zm.x - Zk.x) * 0.5f};
+            T2* base = out + (long long)f * NK + (2LL * (rp0 + lrp)) * NXH + k;
+            base[0] = a;
+            base[NXH] = b;
+        }
+    }
+}
+
+// fused plans by line length (FP32): the first forward radix is small so the
+// fused stage holds few values per field; P row pairs per CTA, chosen so that
+// the CTA is a whole number of warps
+template <int N>
+struct XFPlan {
+    static constexpr bool ok = false;
+};
+#define PF_XF_PLAN(N_, P_, ...)              \
+    template <>                              \
+    struct XFPlan<N_> {                      \
+        static constexpr bool ok = true;     \
+        static constexpr int P = P_;         \
+        using Fwd = Radices<__VA_ARGS__>;    \
+    };
+PF_XF_PLAN(64, 16, 4, 16)
+PF_XF_PLAN(96, 8, 4, 8, 3)
+PF_XF_PLAN(120, 4, 3, 8, 5)
+PF_XF_PLAN(128, 8, 4, 8, 4)
+PF_XF_PLAN(160, 4, 4, 8, 5)
+PF_XF_PLAN(192, 4, 4, 16, 3)
+PF_XF_PLAN(256, 4, 4, 16, 4)
+PF_XF_PLAN(640, 2, 5, 16, 8)
+#undef PF_XF_PLAN
+
+template <int N, int MODE>
+static int launch_x_fused_n(const Geo& g, const Phys& ph, const void* in, void* out, void* R, const void* Rin,
+                            double* partials, double rtol, double atol, cudaStream_t s) {
+    using Pl = XFPlan<N>;
+    using Sh = XFShape<typename Pl::Fwd, Pl::P>;
+    const size_t sm = 2 * (size_t)Pl::P * 4 * Sh::LS * sizeof(float2);
+    const int npairs = g.nz * g.ny / 2;
+    const int nb = (npairs + Pl::P - 1) / Pl::P;
+    auto k = k_x_fused<float, typename Pl::Fwd, Pl::P, MODE>;
+    set_smem(k, sm);
+    k<<<nb, Sh::NT, sm, s>>>(g, ph, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out),
+                             reinterpret_cast<float*>(R), reinterpret_cast<const float*>(Rin), partials, (float)rtol,
+                             (float)atol);
+    return nb;
+}
+
+template <int N>
+static int launch_x_fused_modes(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R,
+                                const void* Rin, double* partials, double rtol, double atol, cudaStream_t s) {
+    if constexpr (!XFPlan<N>::ok) {
+        return 0;
+    } else {
+        switch (mode) {
+            case XM_PHYS1:
+                return ph.elastic ? launch_x_fused_n<N, XF_PHYS1_H>(g, ph, in, out, R, Rin, partials, rtol, atol, s)
+                                  : launch_x_fused_n<N, XF_PHYS1_RHS>(g, ph, in, out, R, Rin, partials, rtol, atol, s);
+            case XM_PHYS2:
+                return ph.elastic ? launch_x_fused_n<N, XF_PHYS2>(g, ph, in, out, R, Rin, partials, rtol, atol, s) : 0;
+            case XM_WRMS: return launch_x_fused_n<N, XF_WRMS>(g, ph, in, out, R, Rin, partials, rtol, atol, s);
+            default: return 0;
+        }
+    }
+}
+
+// the fused x pass for FP32 contexts where the line length has a fused plan;
+// returns the number of CTAs launched, 0 if it does not apply
+int launch_x_fused(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
+                          double* partials, double rtol, double atol, cudaStream_t s) {
+    if (g.xf_off) return 0;
+    switch (g.nx) {
+        case 64: return launch_x_fused_modes<64>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        case 96: return launch_x_fused_modes<96>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        case 120: return launch_x_fused_modes<120>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        case 128: return launch_x_fused_modes<128>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        case 160: return launch_x_fused_modes<160>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        case 192: return launch_x_fused_modes<192>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        case 256: return launch_x_fused_modes<256>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        case 640: return launch_x_fused_modes<640>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        default: return 0;
+    }
+}
+
+}  // namespace pf

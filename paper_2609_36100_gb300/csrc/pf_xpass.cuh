@@ -12,6 +12,16 @@ namespace pf {
 // imaginary parts of DC and Nyquist dropped), R2C unpacks
 // A_k = (Z_k + conj Z_{n-k})/2, B_k = (Z_k - conj Z_{n-k})/(2i).
 // ---------------------------------------------------------------------------
+// a / b: the FP32 form divides through the hardware reciprocal (about two
+// ulp, far inside the FP32 transforms' rounding); FP64 divides exactly
+template <typename T>
+__device__ __forceinline__ T xdiv(T a, T b) {
+    if constexpr (sizeof(T) == 4)
+        return __fdividef(a, b);
+    else
+        return a / b;
+}
+
 struct Pt {
     // real-space physics at one point (Sec. 4.1); returns q and g_v
     template <typename T>
@@ -26,7 +36,7 @@ struct Pt {
         const T H = h[0] + h[1] + h[2];
         const T Bv = pt.Bv, Bm = pt.Bm;
         const T denom = H * pt.inv2Av + ((T)1 - H) * pt.inv2Am;
-        const T mu = (X - H * Bv - ((T)1 - H) * Bm) / denom;
+        const T mu = xdiv<T>(X - H * Bv - ((T)1 - H) * Bm, denom);
         const T Xm = mu * pt.inv2Am + Bm;
         const T Xv = mu * pt.inv2Av + Bv;
         const T fm = pt.A0m + pt.Am * (Xm - Bm) * (Xm - Bm);
@@ -390,11 +400,18 @@ static int x_rows(const Geo& g) {
     return P;
 }
 
+int launch_x_fused(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
+                   double* partials, double rtol, double atol, cudaStream_t s);
+
 template <typename T>
-void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
-                   double* partials, double rtol, double atol, const double* real_in, double* real_out,
-                   cudaStream_t s) {
+int launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
+                  double* partials, double rtol, double atol, const double* real_in, double* real_out,
+                  cudaStream_t s) {
     using T2 = typename Cx<T>::t;
+    if constexpr (sizeof(T) == 4) {
+        const int nbf = launch_x_fused(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
+        if (nbf > 0) return nbf;
+    }
     const int P = x_rows<T>(g);
     const size_t sm = 2 * 4 * (size_t)P * skewed_len(g.nx) * sizeof(T2);
     const int npairs = g.nz * g.ny / 2;
@@ -420,6 +437,7 @@ void launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void*
         default: PF_R16_SWITCH(g.px.has16, PF_XLAUNCH(R16C, 0)); break;
     }
 #undef PF_XLAUNCH
+    return nb;
 }
 
 }  // namespace pf

@@ -3,6 +3,6 @@
 #include "pf_xpass.cuh"
 
 namespace pf {
-template void launch_x_pass<double>(const Geo&, const Phys&, int, const void*, void*, void*, const void*, double*,
+template int launch_x_pass<double>(const Geo&, const Phys&, int, const void*, void*, void*, const void*, double*,
                                 double, double, const double*, double*, cudaStream_t);
 }  // namespace pf

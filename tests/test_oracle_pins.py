@@ -246,10 +246,11 @@ def test_pair_width_keeps_the_band_explicitly_stable(params):
     linear in phi_v with rate L omega phi_q^2 / eps, at most L omega / eps
     (inside a variant-q precipitate), and it is treated explicitly. The
     explicit ARK4 part is stable on [-x*, 0] of the negative real axis
-    (from the stability function with zI = 0). At the paper's largest stable
-    fourth-order step (2.25 s, Sec. 2.3) the band's rate stays inside that
-    interval for the library's width eps = 0.02 and leaves it for widths
-    of 0.005 and below, which is why the width is not taken smaller."""
+    (from the stability function with zI = 0; x* = 4.23). At the paper's
+    largest stable fourth-order step (2.25 s, Sec. 2.3) the band's rate stays
+    inside that interval for the library's width eps = 0.01 and leaves it
+    for widths of 0.005 and below (the bound is eps >= 2.25 L omega / x* =
+    0.008), which is why the width is not taken smaller."""
     t = oracle.ark436l2sa()
     xs = np.linspace(0.01, 10.0, 2000)
     stable = [abs(_R(t, 0.0, -x)) <= 1.0 + 1e-12 for x in xs]
@@ -360,7 +361,7 @@ def test_free_energy_uniform_states(params):
     # uniform h has only a DC mode, where B = 0
     assert m.free_energy(m.to_k(y)) == pytest.approx(V * (fch + fb), rel=1e-12)
     # quadratic branch of the regularised pairwise barrier: |x| -> x^2/(2 eps)
-    a, b = 0.1, 0.15
+    a, b = 0.05, 0.15
     y[1], y[2] = a, b
     H = h(a) + h(b)
     mu = (0.07 - H * p["B_v"] - (1 - H) * p["B_m0"]) * 2 * A
