@@ -275,15 +275,31 @@ int pf_fno_forward(pf_fno* f, const float* x_dev, float* out_dev); /* out_dev ma
 int pf_fno_backward(pf_fno* f, const float* target_dev, double* loss_out);
 int pf_fno_adam(pf_fno* f, float lr, float b1, float b2, float eps);
 int pf_fno_train_step(pf_fno* f, const float* x_dev, const float* target_dev, float lr, double* loss_out);
+/* Normalisation statistics from solver snapshots (device FP32
+ * [n_traj][n_snap][4][nz][ny][nx], n_snap >= 2): per-channel mean and
+ * standard deviation of the inputs s_t and standard deviation of the
+ * increments s_{t+1} - s_t over all consecutive pairs (sums in FP64), set as
+ * by pf_fno_set_norm. */
+int pf_fno_fit_norm(pf_fno* f, const float* snaps_dev, int n_traj, int n_snap);
+/* One training step (forward, MSE backward, Adam with b1 0.9, b2 0.999,
+ * eps 1e-8) on the pair (s_t, s_{t+tau}) of device FP32 [4][nz][ny][nx]
+ * states: the input (s_t - mean)/std and the target (s_{t+tau} - s_t)/out_std
+ * are formed on the device from the normalisation set before. */
+int pf_fno_train_pair(pf_fno* f, const float* s0_dev, const float* s1_dev, float lr, double* loss_out);
 const char* pf_fno_last_error(const pf_fno* f);
-/* One surrogate proposal with the integrator as judge: the network proposes
- * y(t + tau) from y(t); the composition mean is reset to y(t)'s exactly; one
- * ARK step of size h is taken from the proposal, and the proposal is accepted
- * (state and clock advance to t + tau + h) if that step's ||LTE||_WRMS <= 1,
- * else y(t) and the clock are restored.  *accepted and *lte report the
- * decision.  Same grid for the network and the simulation. */
+/* One surrogate proposal judged by the integrator (the method's own step
+ * control is the judge).  The network proposes y(t + tau) = y(t) +
+ * out_std * net((y(t) - mean)/std) in real space; the context then
+ * integrates the same interval adaptively (pf_advance to t + tau at
+ * rtol/atol, first step h), and *dist = ||y^ - y_tau||_WRMS with weights
+ * w = 1/(rtol |y_tau| + atol) over all four real fields.  The proposal is
+ * accepted (*accepted = 1) when *dist <= 1, i.e. when it lies within the
+ * integrator's own tolerance of the verified state.  Either way the
+ * context ends at the verified state y_tau and time t + tau (a proposal's
+ * own error is bounded only by comparing it with an integration of the same
+ * interval).  Same grid for the network and the simulation. */
 int pf_surrogate_step(pf_ctx* ctx, pf_fno* f, double tau, double h, double rtol, double atol, int* accepted,
-                      double* lte);
+                      double* dist);
 
 /* Allocation-free inverse transform (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory -- e.g. applications

@@ -102,6 +102,8 @@ SIGNATURES = {
     "pf_fno_adam": (C.c_int, [_P, C.c_float, C.c_float, C.c_float, C.c_float]),
     "pf_fno_train_step": (C.c_int, [_P, _P, _P, C.c_float, C.POINTER(C.c_double)]),
     "pf_fno_last_error": (C.c_char_p, [_P]),
+    "pf_fno_fit_norm": (C.c_int, [_P, _P, C.c_int, C.c_int]),
+    "pf_fno_train_pair": (C.c_int, [_P, _P, _P, C.c_float, C.POINTER(C.c_double)]),
     "pf_surrogate_step": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int),
                                     C.POINTER(C.c_double)]),
 }
@@ -497,12 +499,25 @@ class FNO:
                                           float(lr), _byref(l)))
         return l.value
 
+    def fit_norm(self, snaps):
+        """Normalisation from a CUDA float32 tensor [n_traj][n_snap][4][nz][ny][nx]."""
+        assert snaps.is_cuda and snaps.dtype == _torch().float32 and snaps.is_contiguous()
+        self._chk(lib().pf_fno_fit_norm(self.f, _ctypes_void_p(snaps.data_ptr()), int(snaps.shape[0]),
+                                        int(snaps.shape[1])))
+
+    def train_pair(self, s0, s1, lr):
+        l = C_double()
+        self._chk(lib().pf_fno_train_pair(self.f, _ctypes_void_p(s0.data_ptr()), _ctypes_void_p(s1.data_ptr()),
+                                          float(lr), _byref(l)))
+        return l.value
+
     def surrogate_step(self, sim, tau, h, rtol=1e-4, atol=1e-8):
+        """(accepted, WRMS distance of the proposal to the verified integration)."""
         acc = C_int()
-        lte = C_double()
+        dist = C_double()
         self._chk(lib().pf_surrogate_step(sim.ctx, self.f, float(tau), float(h), float(rtol), float(atol),
-                                          _byref(acc), _byref(lte)))
-        return bool(acc.value), lte.value
+                                          _byref(acc), _byref(dist)))
+        return bool(acc.value), dist.value
 
 
 _ctypes_void_p = C.c_void_p

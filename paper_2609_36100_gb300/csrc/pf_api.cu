@@ -666,15 +666,6 @@ int pf_ctx_grid(pf_ctx* c, pf_grid* g) {
     return PF_OK;
 }
 
-// overwrite the composition-mean entry X^(k = 0) of the state with src's
-int pf_copy_dc(pf_ctx* c, const void* src) {
-    if (!c || !src) return PF_EINVAL;
-    cudaSetDevice(c->dev);
-    PF_CUDA(c, cudaMemcpyAsync(c->y, src, sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-    PF_CUDA(c, cudaStreamSynchronize(c->stream));
-    return PF_OK;
-}
-
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

@@ -28,7 +28,6 @@
 using namespace pf;
 
 int pf_ctx_grid(pf_ctx* c, pf_grid* g);
-int pf_copy_dc(pf_ctx* c, const void* src);
 
 namespace {
 
@@ -283,6 +282,80 @@ __global__ void k_apply_delta(double* __restrict__ y, const float* __restrict__ 
     }
 }
 
+// per-channel sums over the snapshot pairs (s_t, s_{t+1}) of n_traj
+// trajectories of n_snap snapshots [traj][snap][4][N]: sums of x, x^2 of the
+// inputs s_t and of d, d^2 of the increments d = s_{t+1} - s_t, in FP64,
+// per block (part[block][16])
+__global__ void k_pair_stats(const float* __restrict__ snaps, int n_traj, int n_snap, long long N,
+                             double* __restrict__ part) {
+    __shared__ double red[16][kT / 32];
+    double acc[16];
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    const long long per_pair = 4 * N;
+    const long long total = (long long)n_traj * (n_snap - 1) * per_pair;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long pr = i / per_pair, r = i - pr * per_pair;
+        const long long tr = pr / (n_snap - 1), t = pr - tr * (n_snap - 1);
+        const int f = (int)(r / N);
+        const float* a = snaps + (tr * n_snap + t) * per_pair;
+        const double x = a[r], d = (double)(a[r + per_pair] - a[r]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c == f) {
+                acc[4 * c + 0] += x;
+                acc[4 * c + 1] += x * x;
+                acc[4 * c + 2] += d;
+                acc[4 * c + 3] += d * d;
+            }
+    }
+    for (int q = 0; q < 16; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        part[(long long)blockIdx.x * 16 + threadIdx.x] = v;
+    }
+}
+
+// network input x = (s_t - mean) / std and target (s_{t+tau} - s_t) / out_std
+__global__ void k_pair_prep(const float* __restrict__ s0, const float* __restrict__ s1, float* __restrict__ x,
+                            float* __restrict__ tgt, long long N, float4 mean, float4 istd, float4 iostd) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 4 * N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i / N);
+        const float mu = f == 0 ? mean.x : f == 1 ? mean.y : f == 2 ? mean.z : mean.w;
+        const float is = f == 0 ? istd.x : f == 1 ? istd.y : f == 2 ? istd.z : istd.w;
+        const float io = f == 0 ? iostd.x : f == 1 ? iostd.y : f == 2 ? iostd.z : iostd.w;
+        const float a = s0[i];
+        x[i] = (a - mu) * is;
+        tgt[i] = (s1[i] - a) * io;
+    }
+}
+
+// per-block sums of ((a - b) w)^2 with w = 1/(rtol |b| + atol) (FP64)
+__global__ void k_wrms_dist(const double* __restrict__ a, const double* __restrict__ b, long long n, double rtol,
+                            double atol, double* __restrict__ part) {
+    __shared__ double red[kT / 32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double d = (a[i] - b[i]) / (rtol * fabs(b[i]) + atol);
+        acc += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
 inline int grid_for(long long n) {
     long long g = (n + kT - 1) / kT;
     if (g > 152 * 16) g = 152 * 16;
@@ -320,9 +393,9 @@ struct pf_fno {
     double* dpart = nullptr;
     double* hsum = nullptr;  // pinned
     float4 in_mean{0, 0, 0, 0}, in_istd{1, 1, 1, 1}, out_std{1, 1, 1, 1};
-    double2* backup = nullptr;  // state copy for a rejected proposal
-    double* realbuf = nullptr;  // real-space FP64 state [4][N]
-    long long backup_nk = 0;
+    double* realbuf = nullptr;  // real-space FP64 state [4][N]: the proposal
+    double* realbuf2 = nullptr; // real-space FP64 state [4][N]: the verified integration
+    float* tgt = nullptr;       // training target [4][N]
     char err[256] = "no error";
 };
 
@@ -349,7 +422,7 @@ cudaError_t falloc(P** p, size_t bytes) {
 void fno_free(pf_fno* f) {
     void* ps[] = {f->theta, f->grad, f->am, f->av, f->wbf, f->Mx, f->Mxw, f->My, f->Mz, f->IXw, f->IX1, f->IY,
                   f->IZ, f->x, f->act, f->zs, f->hpre, f->hh, f->out, f->Ak, f->T1, f->T2, f->Ok, f->Gk,
-                  f->sbuf, f->da, f->dz, f->dh, f->dout, f->part, f->dpart, f->backup, f->realbuf};
+                  f->sbuf, f->da, f->dz, f->dh, f->dout, f->part, f->dpart, f->realbuf, f->realbuf2, f->tgt};
     for (void* p : ps) cudaFree(p);
     if (f->hsum) cudaFreeHost(f->hsum);
 }
@@ -595,8 +668,9 @@ int pf_fno_create(int nx, int ny, int nz, int C, int modes, int H, int L, int bf
     A(&f->dz, sizeof(float) * (size_t)C * N);
     A(&f->dh, sizeof(float) * (size_t)H * N);
     A(&f->dout, sizeof(float) * 4 * N);
+    A(&f->tgt, sizeof(float) * 4 * N);
     A(&f->part, sizeof(float) * (size_t)f->npart_blk * (size_t)(H * C > C * C ? H * C : C * C));
-    A(&f->dpart, sizeof(double) * (152 * 4 + 2));
+    A(&f->dpart, sizeof(double) * (152 * 4 * 16 + 32));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&f->hsum, sizeof(double) * 2);
     std::vector<float2> Mx, Mxw, My, Mz, IXw, IX1, IY, IZ;
     build_matrices(f, Mx, Mxw, My, Mz, IXw, IX1, IY, IZ);
@@ -721,10 +795,56 @@ int pf_fno_train_step(pf_fno* f, const float* x_dev, const float* target_dev, fl
 
 const char* pf_fno_last_error(const pf_fno* f) { return f ? f->err : g_fno_err; }
 
-// Surrogate proposal + judge (one call = one proposal).
+// Normalisation statistics from solver snapshots (device FP32
+// [n_traj][n_snap][4][N]): per-channel mean and standard deviation of the
+// inputs and standard deviation of the increments over consecutive pairs.
+int pf_fno_fit_norm(pf_fno* f, const float* snaps_dev, int n_traj, int n_snap) {
+    if (!f || !snaps_dev || n_traj < 1 || n_snap < 2) return ffail(f, PF_EINVAL, "pf_fno_fit_norm: bad argument");
+    cudaSetDevice(f->dev);
+    const int nb = 152 * 4;
+    k_pair_stats<<<nb, kT, 0, f->s>>>(snaps_dev, n_traj, n_snap, f->d.N, f->dpart);
+    std::vector<double> part((size_t)nb * 16);
+    cudaError_t e = cudaMemcpyAsync(part.data(), f->dpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, f->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->s);
+    if (e != cudaSuccess) return ffail(f, PF_ECUDA, "pf_fno_fit_norm", e);
+    double sum[16] = {};
+    for (int b = 0; b < nb; ++b)
+        for (int q = 0; q < 16; ++q) sum[q] += part[(size_t)b * 16 + q];
+    const double cnt = (double)n_traj * (n_snap - 1) * (double)f->d.N;
+    float mean[4], sd[4], dsd[4];
+    for (int c = 0; c < 4; ++c) {
+        const double m = sum[4 * c] / cnt, v = sum[4 * c + 1] / cnt - m * m;
+        const double dm = sum[4 * c + 2] / cnt, dv = sum[4 * c + 3] / cnt - dm * dm;
+        mean[c] = (float)m;
+        sd[c] = (float)std::fmax(std::sqrt(std::fmax(v, 0.0)), 1e-6);
+        dsd[c] = (float)std::fmax(std::sqrt(std::fmax(dv, 0.0)), 1e-9);
+    }
+    return pf_fno_set_norm(f, mean, sd, dsd);
+}
+
+// One Adam step on the pair (s_t, s_{t+tau}) (device FP32 [4][N] each): the
+// normalised input and increment target are formed on the device.
+int pf_fno_train_pair(pf_fno* f, const float* s0_dev, const float* s1_dev, float lr, double* loss_out) {
+    if (!f || !s0_dev || !s1_dev) return ffail(f, PF_EINVAL, "pf_fno_train_pair: NULL argument");
+    cudaSetDevice(f->dev);
+    const float4 io = make_float4(1.f / f->out_std.x, 1.f / f->out_std.y, 1.f / f->out_std.z, 1.f / f->out_std.w);
+    k_pair_prep<<<grid_for(4 * f->d.N), kT, 0, f->s>>>(s0_dev, s1_dev, f->x, f->tgt, f->d.N, f->in_mean, f->in_istd,
+                                                      io);
+    int rc = fno_forward(f, f->x);
+    if (!rc) rc = pf_fno_backward(f, f->tgt, loss_out);
+    if (!rc) rc = pf_fno_adam(f, lr, 0.9f, 0.999f, 1e-8f);
+    return rc;
+}
+
+// Surrogate proposal judged by the integrator (one call = one proposal over
+// tau): the network proposes y(t + tau) from y(t); the context then
+// integrates the same interval with its adaptive controller (first step h),
+// and the proposal is reported as accepted when its WRMS distance to that
+// verified integration is <= 1.  The context ends at the verified state.
 int pf_surrogate_step(pf_ctx* ctx, pf_fno* f, double tau, double h, double rtol, double atol, int* accepted,
-                      double* lte) {
-    if (!ctx || !f || !accepted || !(tau > 0) || !(h > 0)) return ffail(f, PF_EINVAL, "pf_surrogate_step: bad argument");
+                      double* dist) {
+    if (!ctx || !f || !accepted || !(tau > 0) || !(h > 0) || !(rtol >= 0) || !(atol > 0))
+        return ffail(f, PF_EINVAL, "pf_surrogate_step: bad argument");
     pf_grid g{};
     double t0 = 0, h0 = 0;
     pf_get_time(ctx, &t0, &h0);
@@ -734,17 +854,14 @@ int pf_surrogate_step(pf_ctx* ctx, pf_fno* f, double tau, double h, double rtol,
     if (g.nx != f->d.nx || g.ny != f->d.ny || g.nz != f->d.nz)
         return ffail(f, PF_EINVAL, "pf_surrogate_step: network and simulation grids differ");
     const long long N = f->d.N;
-    const long long nk4 = 4LL * g.nz * g.ny * (g.nx / 2 + 1);
     cudaError_t e = cudaSuccess;
-    if (!f->backup) {
-        e = falloc(&f->backup, sizeof(double2) * nk4);
-        if (e == cudaSuccess) e = falloc(&f->realbuf, sizeof(double) * 4 * N);
+    if (!f->realbuf) {
+        e = falloc(&f->realbuf, sizeof(double) * 4 * N);
+        if (e == cudaSuccess) e = falloc(&f->realbuf2, sizeof(double) * 4 * N);
         if (e != cudaSuccess) return ffail(f, PF_ENOMEM, "pf_surrogate_step: allocation", e);
-        f->backup_nk = nk4;
     }
-    // y(t) -> backup (k space) and real space
-    rc = pf_get_state_hat(ctx, f->backup, 1);
-    if (!rc) rc = pf_get_state(ctx, f->realbuf, 1);
+    // proposal y^(t + tau) = y(t) + net(y(t)) in real space (FP64)
+    rc = pf_get_state(ctx, f->realbuf, 1);
     if (rc) return rc;
     k_norm_in<<<grid_for(4 * N), kT, 0, f->s>>>(f->realbuf, f->x, N, f->in_mean, f->in_istd);
     rc = fno_forward(f, f->x);
@@ -752,25 +869,24 @@ int pf_surrogate_step(pf_ctx* ctx, pf_fno* f, double tau, double h, double rtol,
     k_apply_delta<<<grid_for(4 * N), kT, 0, f->s>>>(f->realbuf, f->out, N, f->out_std);
     e = cudaStreamSynchronize(f->s);
     if (e != cudaSuccess) return ffail(f, PF_ECUDA, "pf_surrogate_step: proposal", e);
-    // proposal y^ in k space, with the composition mean of y(t) kept exactly
-    rc = pf_set_state(ctx, f->realbuf, 1);
-    if (!rc) rc = pf_copy_dc(ctx, f->backup);
+    // the verified integration of the same interval
+    pf_set_time(ctx, t0, h);
+    pf_stats st{};
+    rc = pf_advance(ctx, t0 + tau, rtol, atol, &st);
     if (rc) return rc;
-    pf_set_time(ctx, t0 + tau, h);
-    double e_j = 0.0;
-    rc = pf_step(ctx, h, &e_j);
+    rc = pf_get_state(ctx, f->realbuf2, 1);
     if (rc) return rc;
-    if (lte) *lte = e_j;
-    if (std::isfinite(e_j) && e_j <= 1.0) {
-        *accepted = 1;
-        pf_set_time(ctx, t0 + tau + h, h0);
-        return PF_OK;
-    }
-    // rejected: restore y(t)
-    *accepted = 0;
-    rc = pf_set_state_hat(ctx, f->backup, 1);
-    pf_set_time(ctx, t0, h0);
-    return rc;
+    const int nb = 152 * 4;
+    k_wrms_dist<<<nb, kT, 0, f->s>>>(f->realbuf, f->realbuf2, 4 * N, rtol, atol, f->dpart);
+    double* tot = f->dpart + nb;
+    launch_reduce(f->dpart, nb, 1.0 / (4.0 * (double)N), tot, f->s);
+    e = cudaMemcpyAsync(f->hsum, tot, sizeof(double), cudaMemcpyDeviceToHost, f->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->s);
+    if (e != cudaSuccess) return ffail(f, PF_ECUDA, "pf_surrogate_step: distance", e);
+    const double d = std::sqrt(f->hsum[0]);
+    if (dist) *dist = d;
+    *accepted = (std::isfinite(d) && d <= 1.0) ? 1 : 0;
+    return PF_OK;
 }
 
 }  // extern "C"

@@ -3,8 +3,8 @@ library's kernels, and surrogate-assisted integration with the integrator as
 judge.
 
 Everything numerical runs in libpf.so; this module only orchestrates calls.
-Training data are pairs (y(t), y(t + tau) - y(t)) of real-space states taken
-every tau along trajectories integrated with fixed ARK4 steps of size dt
+Training data are pairs (y(t), y(t + tau)) of real-space states taken every
+tau along trajectories integrated with fixed ARK4 steps of size dt
 (tau = 8 dt).
 """
 from __future__ import annotations
@@ -38,26 +38,13 @@ def trajectories(ics, params, dt, n_snap, steps_per_snap=8, precision="fp32bulk"
     return torch.stack(out)
 
 
-def normalisation(traj):
-    """Per-channel input mean/std and output (increment) std of a trajectory
-    tensor [n, T, 4, ...]."""
-    x = traj[:, :-1].transpose(0, 2).reshape(4, -1)
-    dlt = (traj[:, 1:] - traj[:, :-1]).transpose(0, 2).reshape(4, -1)
-    mean = x.mean(dim=1)
-    std = x.std(dim=1).clamp_min(1e-6)
-    dstd = dlt.std(dim=1).clamp_min(1e-9)
-    return mean.cpu().numpy(), std.cpu().numpy(), dstd.cpu().numpy()
-
-
 def train(net, traj, epochs, lr, seed=0, log=None):
-    """Adam on the MSE of normalised increments over all consecutive snapshot
-    pairs; returns the per-epoch mean losses."""
-    import torch
-    mean, std, dstd = normalisation(traj)
-    net.set_norm(mean, std, dstd)
-    m = torch.as_tensor(mean, device="cuda").view(4, 1, 1, 1)
-    sd = torch.as_tensor(std, device="cuda").view(4, 1, 1, 1)
-    ds = torch.as_tensor(dstd, device="cuda").view(4, 1, 1, 1)
+    """Adam, one snapshot pair per step, on the MSE of normalised increments
+    over all consecutive snapshot pairs of a CUDA float32 trajectory tensor
+    [n, T, 4, ...]; the normalisation statistics and every per-pair
+    transformation are computed by the library.  Returns the per-epoch mean
+    losses."""
+    net.fit_norm(traj)
     n, T = traj.shape[0], traj.shape[1] - 1
     pairs = [(i, t) for i in range(n) for t in range(T)]
     rng = np.random.default_rng(seed)
@@ -67,46 +54,45 @@ def train(net, traj, epochs, lr, seed=0, log=None):
         tot = 0.0
         for k in order:
             i, t = pairs[k]
-            x = ((traj[i, t] - m) / sd).contiguous()
-            y = ((traj[i, t + 1] - traj[i, t]) / ds).contiguous()
-            tot += net.train_step(x, y, lr)
+            tot += net.train_pair(traj[i, t], traj[i, t + 1], lr)
         losses.append(tot / len(pairs))
         if log:
             log("epoch %d loss %.4e" % (ep, losses[-1]))
     return losses
 
 
-def rollout(y0, params, t_end, dt, net=None, steps_per_snap=8, precision="fp32bulk", rtol=1e-4, atol=1e-8):
-    """Integrate to t_end with fixed ARK4 steps of size dt; with a network,
-    each block of steps_per_snap steps is first offered to the surrogate
-    (proposal over tau = steps_per_snap * dt plus one judged step of size dt).
-    Returns (final real-space state, wall seconds, accepted, offered)."""
+def rollout(y0, params, t_end, tau, net=None, precision="fp32bulk", rtol=1e-4, atol=1e-8, h0=1.0):
+    """Integrate to t_end adaptively (ARK4, rtol/atol).  Without a network:
+    one pf_advance.  With a network: window by window of length tau, each
+    window first proposed by the network and then integrated by the method,
+    which judges the proposal (accepted when its WRMS distance to the
+    verified state is <= 1); the state always continues from the verified
+    integration.  Returns (final real-space state, wall seconds, accepted,
+    offered, proposal distances)."""
     import torch
     shape = y0.shape[1:]
-    tau = steps_per_snap * dt
     acc = off = 0
+    dists = []
     with Simulation(shape, params, "ark4", precision) as s:
         s.set_state(y0)
+        s.set_time(0.0, h0)
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        t = 0.0
-        while t < t_end - 1e-9:
-            left = t_end - t
-            if net is not None and left >= tau + dt - 1e-9:
+        if net is None:
+            s.advance(t_end, rtol, atol)
+        else:
+            t = 0.0
+            while t < t_end - 1e-9:
+                w = min(tau, t_end - t)
                 off += 1
-                ok, _ = net.surrogate_step(s, tau, dt, rtol, atol)
-                if ok:
-                    acc += 1
-                    t += tau + dt
-                    continue
-            k = min(steps_per_snap, int(round(left / dt)))
-            for _ in range(max(k, 1)):
-                s.step(dt, want_lte=False)
-            t += max(k, 1) * dt
+                ok, d = net.surrogate_step(s, w, h0, rtol, atol)
+                acc += int(ok)
+                dists.append(d)
+                t = s.time()[0]
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
         out = s.get_state()
-    return out, wall, acc, off
+    return out, wall, acc, off, dists
 
 
 def new_network(shape, C=32, modes=12, H=128, L=4, bf16=True, seed=0):

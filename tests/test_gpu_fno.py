@@ -1,7 +1,8 @@
 """FNO surrogate kernels against the FP64 oracle (oracle/fno.py), through the
 C ABI: forward outputs and every parameter gradient, in the FP32-weight
 checking mode (tight) and with BF16 spectral weights (BF16-level), plus the
-Adam training loop and the proposal/judge logic of pf_surrogate_step."""
+Adam training loop, the library-side normalisation and pair training, and
+the judge of pf_surrogate_step."""
 import numpy as np
 import pytest
 
@@ -105,35 +106,78 @@ def test_adam_training_reduces_loss(pfg):
         net.close()
 
 
-def test_surrogate_step_accept_and_restore(pfg, params):
+def test_fit_norm_and_train_pair(pfg, params):
+    """The library's normalisation statistics equal numpy's over all
+    consecutive snapshot pairs, and a training step on a raw pair equals a
+    training step on the pair normalised by hand."""
+    import torch
+    rng = np.random.default_rng(9)
+    snaps = rng.standard_normal((2, 3, 4) + SHAPE).astype(np.float32) * np.array([0.01, 0.3, 0.2, 0.1],
+                                                                              dtype=np.float32)[None, None, :, None,
+                                                                                                 None, None]
+    snaps += np.array([0.05, 0.2, 0.1, 0.0], dtype=np.float32)[None, None, :, None, None, None]
+    x = snaps[:, :-1].transpose(2, 0, 1, 3, 4, 5).reshape(4, -1).astype(np.float64)
+    d = (snaps[:, 1:] - snaps[:, :-1]).transpose(2, 0, 1, 3, 4, 5).reshape(4, -1).astype(np.float64)
+    mean, sd, dsd = x.mean(axis=1), x.std(axis=1), d.std(axis=1)
+    dev = torch.from_numpy(snaps).to("cuda").contiguous()
+    a = pfg.FNO(SHAPE, bf16=False, **DIMS)
+    b = pfg.FNO(SHAPE, bf16=False, **DIMS)
+    try:
+        th = (np.random.default_rng(4).standard_normal(a.n) * 0.05).astype(np.float32)
+        a.set_params(th)
+        b.set_params(th)
+        a.fit_norm(dev)
+        la = a.train_pair(dev[0, 0], dev[0, 1], 1e-3)
+        b.set_norm(mean, sd, dsd)
+        xin = torch.from_numpy(((snaps[0, 0] - mean[:, None, None, None]) / sd[:, None, None, None])
+                               .astype(np.float32)).to("cuda").contiguous()
+        tgt = torch.from_numpy(((snaps[0, 1] - snaps[0, 0]) / dsd[:, None, None, None])
+                               .astype(np.float32)).to("cuda").contiguous()
+        lb = b.train_step(xin, tgt, 1e-3)
+        assert la == pytest.approx(lb, rel=1e-4)
+        assert np.max(np.abs(a.params() - b.params())) <= 1e-6
+    finally:
+        a.close()
+        b.close()
+
+
+def test_surrogate_step_judged_by_verified_integration(pfg, params):
+    """The judge integrates the proposal's interval with the method itself:
+    the call ends at the state and time of a plain adaptive integration of
+    the same interval (bitwise), and reports the proposal's WRMS distance to
+    it (weights from the verified state), accepting only within 1."""
+    import torch  # noqa: F401
     p = params
     y0 = synth.ic_spheres(16, 2, 3.0, 4.0, 3, p)
+    tau, h, rtol, atol = 8.0, 0.5, 1e-4, 1e-8
+    with pfg.Simulation(SHAPE, p, "ark4", "fp64") as ref:
+        ref.set_state(y0)
+        ref.set_time(0.0, h)
+        ref.advance(tau, rtol, atol)
+        y_tau = ref.get_state()
+        yh_tau = ref.state_hat().cpu().numpy()
     net = pfg.FNO(SHAPE, bf16=True, **DIMS)
     sim = pfg.Simulation(SHAPE, p, "ark4", "fp64")
     try:
         net.set_norm([0.05, 0.0, 0.0, 0.0], [0.05, 1.0, 1.0, 1.0], [1e-3, 1e-2, 1e-2, 1e-2])
-        # zero network: the proposal is y(t) itself, so the judge step is an
-        # ordinary step and is accepted; the clock advances by tau + h
+        # zero network: the proposal is y(t) itself
         net.set_params(np.zeros(net.n, dtype=np.float32))
         sim.set_state(y0)
-        ok, e = net.surrogate_step(sim, 8.0, 0.5)
-        assert ok and e <= 1.0
-        t, _ = sim.time()
-        assert t == pytest.approx(8.5)
-        with pfg.Simulation(SHAPE, p, "ark4", "fp64") as ref:
-            ref.set_state(y0)
-            ref.step(0.5)
-            a = ref.state_hat().cpu().numpy()
-        b = sim.state_hat().cpu().numpy()
-        assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))
-        # a noisy network: rejected, state and clock restored exactly
+        ok, dist = net.surrogate_step(sim, tau, h, rtol, atol)
+        want = np.sqrt(np.mean(((y0 - y_tau) / (rtol * np.abs(y_tau) + atol)) ** 2))
+        assert dist == pytest.approx(want, rel=1e-9)
+        assert ok == (want <= 1.0)
+        assert sim.time()[0] == pytest.approx(tau, rel=1e-14)
+        assert np.array_equal(sim.state_hat().cpu().numpy(), yh_tau)
+        # a noisy network: far outside the tolerance, rejected; the state is
+        # still the verified integration
         rng = np.random.default_rng(3)
         net.set_params((rng.standard_normal(net.n) * 3.0).astype(np.float32))
-        before = sim.state_hat().cpu().numpy()
-        ok, e = net.surrogate_step(sim, 8.0, 0.5)
-        assert not ok and not (e <= 1.0)  # large or non-finite error estimate
-        assert sim.time()[0] == pytest.approx(8.5)
-        assert np.array_equal(sim.state_hat().cpu().numpy(), before)
+        sim.set_state(y0)
+        sim.set_time(0.0, h)
+        ok, dist = net.surrogate_step(sim, tau, h, rtol, atol)
+        assert not ok and not (dist <= 1.0)
+        assert np.array_equal(sim.state_hat().cpu().numpy(), yh_tau)
     finally:
         sim.close()
         net.close()
