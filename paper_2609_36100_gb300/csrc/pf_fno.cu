@@ -356,6 +356,177 @@ __global__ void k_wrms_dist(const double* __restrict__ a, const double* __restri
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core forms of the pointwise channel contractions (BF16 mode): the
+// dense layers y = W x (+ bias, + add, GELU), their transposes dx = W^T dy,
+// and the weight gradients G = U V^T summed over the grid points, as BF16
+// mma.sync m16n8k16 with FP32 accumulation.  Each FP32 operand v is split
+// into v_hi = bf16(v) and v_lo = bf16(v - v_hi), and the product is formed
+// as hi*hi + hi*lo + lo*hi, which keeps about 16 significant bits of both
+// operands (the dropped lo*lo term is ~2^-16 relative), so the contractions
+// cost the weights' and activations' FP32 copies no accuracy beyond the BF16
+// spectral weights of this mode.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// two FP32 values -> their BF16 leading parts packed (first value in the low
+// half) and the BF16 roundings of their remainders
+__device__ __forceinline__ void split2(float x0, float x1, unsigned& hi, unsigned& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __bfloat162float(h.x), x1 - __bfloat162float(h.y));
+    hi = *reinterpret_cast<const unsigned*>(&h);
+    lo = *reinterpret_cast<const unsigned*>(&l);
+}
+__device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4], unsigned bh0,
+                                     unsigned bh1, unsigned bl0, unsigned bl1) {
+    mma_bf16_16816(d, ah, bh0, bh1);
+    mma_bf16_16816(d, ah, bl0, bl1);
+    mma_bf16_16816(d, al, bh0, bh1);
+}
+
+constexpr int kMmaWarps = 4;
+
+// y[m][p] = act(sum_k W'[m][k] x[k][p] + bias[m] (+ add[m][p])), W' = W (M x K
+// = A x B) or, with TRANS, W^T (M x K = B x A; out = accum ? out + . : .).
+// MT m-tiles of 16 rows; one warp per 8 consecutive points at a time.
+template <int MT, bool TRANS>
+__global__ void __launch_bounds__(32 * kMmaWarps) k_dense_mma(const float* __restrict__ x, float* __restrict__ y,
+                                                              float* __restrict__ zout, const float* __restrict__ W,
+                                                              const float* __restrict__ bias,
+                                                              const float* __restrict__ add, int A, int B, long long N,
+                                                              int act, int accum) {
+    const int M = TRANS ? B : A, K = TRANS ? A : B;
+    const int KT = (K + 15) / 16;  // k-tiles of 16 (zero padded)
+    extern __shared__ unsigned wsm[];  // per (m-tile, k-tile): 32 lanes x 4 regs, hi then lo
+    for (int e = threadIdx.x; e < MT * KT * 32; e += blockDim.x) {
+        const int lane = e & 31, tile = e >> 5, mt = tile / KT, kt = tile - mt * KT;
+        const int g = lane >> 2, t = lane & 3;
+        unsigned* dh = wsm + (size_t)tile * 256 + lane * 4;
+        unsigned* dl = dh + 128;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int m = mt * 16 + g + ((r & 1) ? 8 : 0), k = kt * 16 + 2 * t + ((r & 2) ? 8 : 0);
+            auto wv = [&](int mm, int kk) -> float {
+                if (mm >= M || kk >= K) return 0.f;
+                return TRANS ? W[(long long)kk * B + mm] : W[(long long)mm * B + kk];
+            };
+            split2(wv(m, k), wv(m, k + 1), dh[r], dl[r]);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const long long ntiles = (N + 7) / 8;
+    for (long long nt = blockIdx.x * (long long)kMmaWarps + warp; nt < ntiles; nt += (long long)gridDim.x * kMmaWarps) {
+        const long long p = nt * 8 + g;  // this lane's point in the B fragment
+        float acc[MT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
+        for (int kt = 0; kt < KT; ++kt) {
+            float xv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int k = kt * 16 + 2 * t + (r & 1) + ((r & 2) ? 8 : 0);
+                xv[r] = (k < K && p < N) ? x[(long long)k * N + p] : 0.f;
+            }
+            unsigned bh0, bl0, bh1, bl1;
+            split2(xv[0], xv[1], bh0, bl0);
+            split2(xv[2], xv[3], bh1, bl1);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const unsigned* sh = wsm + (size_t)(mt * KT + kt) * 256 + lane * 4;
+                const unsigned ah[4] = {sh[0], sh[1], sh[2], sh[3]};
+                const unsigned al[4] = {sh[128], sh[129], sh[130], sh[131]};
+                mma3(acc[mt], ah, al, bh0, bh1, bl0, bl1);
+            }
+        }
+        // epilogue: acc[mt][0..1] -> rows mt*16 + g, points nt*8 + 2t + {0,1};
+        // acc[mt][2..3] -> rows + 8
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = mt * 16 + g + ((r & 2) ? 8 : 0);
+                const long long q = nt * 8 + 2 * t + (r & 1);
+                if (m >= M || q >= N) continue;
+                const long long i = (long long)m * N + q;
+                float v = acc[mt][r];
+                if (TRANS) {
+                    y[i] = accum ? y[i] + v : v;
+                } else {
+                    v += bias[m];
+                    if (add) v += add[i];
+                    if (zout) zout[i] = v;
+                    y[i] = act ? gelu_f(v) : v;
+                }
+            }
+    }
+}
+
+// per-block partial sums of G[a][b] = sum_p U[a][p] V[b][p] (U: A x N, V: B x
+// N), K = the grid points; warps split the m-tiles, each holding all NT
+// n-tiles of its rows; CTAs split the points.
+template <int MTW, int NT>
+__global__ void __launch_bounds__(32 * kMmaWarps) k_outer_mma(const float* __restrict__ U, const float* __restrict__ V,
+                                                              int A, int B, long long N, float* __restrict__ part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int MT = (A + 15) / 16;
+    float acc[MTW][NT][4];
+#pragma unroll
+    for (int i = 0; i < MTW; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+    const long long ks = (N + 15) / 16;
+    const long long per = (ks + gridDim.x - 1) / gridDim.x;
+    const long long k0 = blockIdx.x * per, k1 = min(ks, k0 + per);
+    for (long long kk = k0; kk < k1; ++kk) {
+        const long long p = kk * 16 + 2 * t;
+        auto ld2 = [&](const float* X, int row, int rows, long long q) -> float2 {
+            if (row >= rows) return make_float2(0.f, 0.f);
+            const float* r = X + (long long)row * N + q;
+            return make_float2(q < N ? r[0] : 0.f, q + 1 < N ? r[1] : 0.f);
+        };
+        unsigned bh[NT][2], bl[NT][2];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const float2 v0 = ld2(V, j * 8 + g, B, p), v1 = ld2(V, j * 8 + g, B, p + 8);
+            split2(v0.x, v0.y, bh[j][0], bl[j][0]);
+            split2(v1.x, v1.y, bh[j][1], bl[j][1]);
+        }
+#pragma unroll
+        for (int i = 0; i < MTW; ++i) {
+            const int mt = warp + i * kMmaWarps;
+            if (mt >= MT) break;
+            const float2 u0 = ld2(U, mt * 16 + g, A, p), u1 = ld2(U, mt * 16 + g + 8, A, p);
+            const float2 u2 = ld2(U, mt * 16 + g, A, p + 8), u3 = ld2(U, mt * 16 + g + 8, A, p + 8);
+            unsigned ah[4], al[4];
+            split2(u0.x, u0.y, ah[0], al[0]);
+            split2(u1.x, u1.y, ah[1], al[1]);
+            split2(u2.x, u2.y, ah[2], al[2]);
+            split2(u3.x, u3.y, ah[3], al[3]);
+#pragma unroll
+            for (int j = 0; j < NT; ++j) mma3(acc[i][j], ah, al, bh[j][0], bh[j][1], bl[j][0], bl[j][1]);
+        }
+    }
+    const int E = A * B;
+#pragma unroll
+    for (int i = 0; i < MTW; ++i) {
+        const int mt = warp + i * kMmaWarps;
+        if (mt >= MT) break;
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int a = mt * 16 + g + ((r & 2) ? 8 : 0), b = j * 8 + 2 * t + (r & 1);
+                if (a < A && b < B) part[(long long)blockIdx.x * E + (long long)a * B + b] = acc[i][j][r];
+            }
+    }
+}
+
 inline int grid_for(long long n) {
     long long g = (n + kT - 1) / kT;
     if (g > 152 * 16) g = 152 * 16;
@@ -458,20 +629,71 @@ void trunc_inv(pf_fno* f, const float2* O, float* r, const float2* IX, bool accu
 }
 
 // G[A][B] = sum_p U[a][p] V[b][p] into dst (V null: sums of U rows)
+// tensor-core launch of the outer-product reduction (BF16 mode, V present)
+template <int MTW, int NT>
+void outer_mma_launch(pf_fno* f, const float* U, const float* V, int A, int B) {
+    k_outer_mma<MTW, NT><<<f->npart_blk, 32 * kMmaWarps, 0, f->s>>>(U, V, A, B, f->d.N, f->part);
+}
+
+bool outer_mma(pf_fno* f, const float* U, const float* V, int A, int B) {
+    if (!f->bf16 || !V) return false;
+    const int MT = (A + 15) / 16, NT = (B + 7) / 8, MTW = (MT + kMmaWarps - 1) / kMmaWarps;
+    // register budget: MTW * NT * 4 accumulators per lane
+    if (MTW == 1 && NT == 1) outer_mma_launch<1, 1>(f, U, V, A, B);
+    else if (MTW == 1 && NT <= 4) outer_mma_launch<1, 4>(f, U, V, A, B);
+    else if (MTW == 1 && NT <= 8) outer_mma_launch<1, 8>(f, U, V, A, B);
+    else if (MTW == 1 && NT <= 16) outer_mma_launch<1, 16>(f, U, V, A, B);
+    else if (MTW == 2 && NT <= 4) outer_mma_launch<2, 4>(f, U, V, A, B);
+    else if (MTW == 2 && NT <= 8) outer_mma_launch<2, 8>(f, U, V, A, B);
+    else return false;
+    return true;
+}
+
 void outer_reduce(pf_fno* f, const float* U, const float* V, int A, int B, float* dst) {
     const int nb = f->npart_blk;
-    const size_t sm = (size_t)(A + B) * kCh * sizeof(float);
-    k_outer_partial<<<nb, kT, sm, f->s>>>(U, V, A, B, f->d.N, f->part);
+    if (!outer_mma(f, U, V, A, B)) {
+        const size_t sm = (size_t)(A + B) * kCh * sizeof(float);
+        k_outer_partial<<<nb, kT, sm, f->s>>>(U, V, A, B, f->d.N, f->part);
+    }
     k_sum_partials<<<grid_for(A * B), kT, 0, f->s>>>(f->part, nb, A * B, dst);
+}
+
+template <int MT, bool TRANS>
+void dense_mma_launch(pf_fno* f, const float* x, float* y, float* zout, const float* Mw, const float* b,
+                      const float* add, int A, int B, int act, int accum) {
+    const int K = TRANS ? A : B, KT = (K + 15) / 16;
+    const size_t sm = (size_t)MT * KT * 256 * sizeof(unsigned);
+    long long nt = (f->d.N + 7) / 8;
+    long long grid = (nt + kMmaWarps - 1) / kMmaWarps;
+    if (grid > 152 * 8) grid = 152 * 8;
+    auto k = k_dense_mma<MT, TRANS>;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<(int)grid, 32 * kMmaWarps, sm, f->s>>>(x, y, zout, Mw, b, add, A, B, f->d.N, act, accum);
+}
+
+template <bool TRANS>
+bool dense_mma(pf_fno* f, const float* x, float* y, float* zout, const float* Mw, const float* b, const float* add,
+               int A, int B, int act, int accum) {
+    if (!f->bf16) return false;
+    const int M = TRANS ? B : A;
+    switch ((M + 15) / 16) {
+        case 1: dense_mma_launch<1, TRANS>(f, x, y, zout, Mw, b, add, A, B, act, accum); return true;
+        case 2: dense_mma_launch<2, TRANS>(f, x, y, zout, Mw, b, add, A, B, act, accum); return true;
+        case 4: dense_mma_launch<4, TRANS>(f, x, y, zout, Mw, b, add, A, B, act, accum); return true;
+        case 8: dense_mma_launch<8, TRANS>(f, x, y, zout, Mw, b, add, A, B, act, accum); return true;
+        default: return false;
+    }
 }
 
 void dense(pf_fno* f, const float* x, float* y, float* zout, const float* Mw, const float* b, const float* add, int A,
            int B, int act) {
+    if (dense_mma<false>(f, x, y, zout, Mw, b, add, A, B, act, 0)) return;
     const size_t sm = (size_t)(A * B + A) * sizeof(float);
     k_dense<<<grid_for(f->d.N), kT, sm, f->s>>>(x, y, zout, Mw, b, add, A, B, f->d.N, act);
 }
 
 void dense_t(pf_fno* f, const float* dy, float* dx, const float* Mw, int A, int B, int accum) {
+    if (dense_mma<true>(f, dy, dx, nullptr, Mw, nullptr, nullptr, A, B, 0, accum)) return;
     const size_t sm = (size_t)(A * B) * sizeof(float);
     k_dense_t<<<grid_for(f->d.N), kT, sm, f->s>>>(dy, dx, Mw, A, B, f->d.N, accum);
 }

@@ -23,29 +23,16 @@ __device__ __forceinline__ T xdiv(T a, T b) {
 }
 
 struct Pt {
-    // real-space physics at one point (Sec. 4.1); returns q and g_v.  With
-    // u = phi (1 - phi): h' = 30 u^2 and the double-well slope
-    // 2 omega_bar u (1 - 2 phi); each pairwise term omega_vq |phi_v phi_q|
-    // (Huber-regularised) is evaluated once per pair and feeds both g_v and g_q.
+    // real-space physics at one point (Sec. 4.1); returns q and g_v
     template <typename T>
     __device__ __forceinline__ static void rhs(const PhysT<T>& pt, T X, const T* p, const T* e, T& q, T* gv) {
-        T h[3], hp[3], d[3];
+        T h[3], hp[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-            const T f = p[v], f2 = f * f, u = f - f2;
-            h[v] = f2 * f * (f * ((T)6 * f - (T)15) + (T)10);
-            hp[v] = (T)30 * u * u;
-            d[v] = pt.wb2 * u * ((T)1 - (T)2 * f);
+            const T f = p[v];
+            h[v] = f * f * f * ((T)6 * f * f - (T)15 * f + (T)10);
+            hp[v] = (T)30 * f * f * ((T)1 - f) * ((T)1 - f);
         }
-#pragma unroll
-        for (int v = 0; v < 3; ++v)
-#pragma unroll
-            for (int qq = v + 1; qq < 3; ++qq) {
-                // d/dphi_v omega |phi_v phi_q| = omega clip(phi_v phi_q / eps, -1, 1) phi_q
-                const T sl = pt.w[v][qq] * fmin((T)1, fmax((T)-1, p[v] * p[qq] * pt.ie));
-                d[v] += sl * p[qq];
-                d[qq] += sl * p[v];
-            }
         const T H = h[0] + h[1] + h[2];
         const T Bv = pt.Bv, Bm = pt.Bm;
         const T denom = H * pt.inv2Av + ((T)1 - H) * pt.inv2Am;
@@ -56,7 +43,17 @@ struct Pt {
         const T fv = pt.A0v + pt.Av * (Xv - Bv) * (Xv - Bv);
         const T drive = fv - fm - mu * (Xv - Xm);
 #pragma unroll
-        for (int v = 0; v < 3; ++v) gv[v] = d[v] + hp[v] * (drive + e[v]);
+        for (int v = 0; v < 3; ++v) {
+            const T f = p[v];
+            T d = pt.wb2 * f * ((T)1 - f) * ((T)1 - (T)2 * f);
+#pragma unroll
+            for (int qq = 0; qq < 3; ++qq)
+                if (qq != v) {
+                    const T sl = fmin((T)1, fmax((T)-1, f * p[qq] * pt.ie));
+                    d += pt.w[v][qq] * sl * p[qq];
+                }
+            gv[v] = d + hp[v] * drive + hp[v] * e[v];
+        }
         q = mu - pt.twoAm * X;
     }
 };
