@@ -11,6 +11,8 @@
 
 namespace pf {
 
+constexpr int kColThreads = 256;  // threads of a column-pass CTA
+
 template <typename T>
 struct Cx;
 template <>
@@ -688,6 +690,57 @@ struct PlanInner<Radices<A>> {
     using type = Radices<>;
 };
 
+// one radix-R stage of NF fields of the [f][pos][TX] tile S, in place: each
+// thread first loads every butterfly it owns, the CTA synchronises, then the
+// butterflies are computed and stored (and the CTA synchronises again)
+template <int R, int SIGN, int TX, int N, int NS, int NF, int NT, typename T2>
+__device__ __forceinline__ void tile_stage_inplace(T2* S, const T2* __restrict__ tw) {
+    constexpr int M = N / R, JOBS = NF * TX * M, JPT = (JOBS + NT - 1) / NT, TWS = N / (NS * R);
+    T2 v[JPT][R];
+#pragma unroll
+    for (int u = 0; u < JPT; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        if (JOBS % NT == 0 || idx < JOBS) {
+            const int f = idx / (TX * M), r = idx - f * (TX * M), col = r % TX, j = r / TX;
+            const T2* src = S + f * (N * TX) + j * TX + col;
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[u][t] = src[t * M * TX];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < JPT; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        if (JOBS % NT == 0 || idx < JOBS) {
+            const int f = idx / (TX * M), r = idx - f * (TX * M), col = r % TX, j = r / TX;
+            const int jq = j / NS, k = j - jq * NS;
+            if constexpr (NS > 1) apply_twiddles<R, SIGN>(v[u], tw, k * TWS);
+            Bfly<R, SIGN, T2>::run(v[u]);
+            T2* dst = S + f * (N * TX) + (jq * NS * R + k) * TX + col;
+#pragma unroll
+            for (int t = 0; t < R; ++t) dst[t * NS * TX] = v[u][t];
+        }
+    }
+    __syncthreads();
+}
+
+// Column transform of a compile-time plan with one shared buffer: stage 0
+// reads global memory (src) into S, the middle stages run in place through
+// registers (tile_stage_inplace), the last stage hands results to dst.
+template <int SIGN, int TX, int N, int NS, bool FIRST, typename T2, class Src, class Dst>
+__device__ __forceinline__ void cols_fixed_run_1buf(T2*, const T2*, Src&, Dst&, Radices<>) {}
+template <int SIGN, int TX, int N, int NS, bool FIRST, typename T2, class Src, class Dst, int R, int... Rest>
+__device__ __forceinline__ void cols_fixed_run_1buf(T2* S, const T2* tw, Src& src, Dst& dst, Radices<R, Rest...>) {
+    constexpr bool LAST = sizeof...(Rest) == 0;
+    if constexpr (FIRST || LAST) {
+        col_stage_fixed<R, SIGN, TX, N, NS, FIRST, LAST>(S, S, tw, src, dst);
+        if constexpr (!LAST) __syncthreads();
+    } else {
+        tile_stage_inplace<R, SIGN, TX, N, NS, 1, kColThreads>(S, tw);
+    }
+    cols_fixed_run_1buf<SIGN, TX, N, NS * R, false>(S, tw, src, dst, Radices<Rest...>{});
+}
+
 // fft_cols with the compile-time plan PID (same contract)
 template <int SIGN, int TX, bool IN_PLACE, int PRELOAD, int PID, typename T2, class Src, class Dst>
 __device__ void fft_cols_fixed(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
@@ -711,13 +764,32 @@ __device__ void fft_cols_fixed(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst
     }
 }
 
-// column transform with the compile-time plan PID, or the generic stages
-template <int SIGN, int TX, bool IN_PLACE, int PRELOAD, bool R16, int PID, typename T2, class Src, class Dst>
+// column transform with the compile-time plan PID, or the generic stages;
+// ONEBUF: a compiled plan of three or more stages uses only P (its middle
+// stages in place; the caller allocates one buffer, see col_buffers)
+template <int SIGN, int TX, bool IN_PLACE, int PRELOAD, bool R16, int PID, bool ONEBUF = false, typename T2,
+          class Src, class Dst>
 __device__ __forceinline__ void cols_fft(const AxisPlan& p, T2* P, T2* Q, Src src, Dst dst) {
-    if constexpr (PID > 0)
-        fft_cols_fixed<SIGN, TX, IN_PLACE, PRELOAD, PID>(p, P, Q, src, dst);
-    else
+    if constexpr (PID > 0) {
+        if constexpr (ONEBUF && PRELOAD == 0 && RadInfo<typename FixedPlan<PID>::Rad>::count >= 3) {
+            cols_fixed_run_1buf<SIGN, TX, FixedPlan<PID>::N, 1, true>(P, twiddles<T2>(p), src, dst,
+                                                                      typename FixedPlan<PID>::Rad{});
+        } else {
+            fft_cols_fixed<SIGN, TX, IN_PLACE, PRELOAD, PID>(p, P, Q, src, dst);
+        }
+    } else {
         fft_cols<SIGN, TX, IN_PLACE, PRELOAD, R16>(p, P, Q, src, dst);
+    }
+}
+
+// shared-memory buffers of a column pass of the compute type T at tile
+// width tx: one when the transform has at most two stages or runs a compiled
+// plan (FP32, tile width 8 or 16), else two
+template <typename T>
+inline int col_buffers(const AxisPlan& p, int tx) {
+    if (p.nst <= 2) return 1;
+    const bool compiled = sizeof(T) == 4 && (tx == 8 || tx == 16) && fixed_plan_id(p) > 0;
+    return compiled ? 1 : 2;
 }
 
 }  // namespace pf

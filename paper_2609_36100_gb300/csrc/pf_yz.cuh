@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kThreads) k_y_pass(Geo g, typename Cx<T>::t* _
     auto dst = [&](int ky, int col, T2 v) {
         if (col < ncol) base[ky * ys + col] = v;
     };
-    cols_fft<SIGN, TX, true, 0, R16, PID>(g.py, A, B, src, dst);
+    cols_fft<SIGN, TX, true, 0, R16, PID, true>(g.py, A, B, src, dst);
 }
 
 template <typename T>
@@ -31,9 +31,10 @@ void launch_y_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
     const int TX = tuned_cols<T>(g, g.tx_y, g.ny, 2, 128 * 1024);
     // a transform of at most two stages never touches its second buffer
-    // (stage 0 reads global, the last stage writes global): half the shared
-    // memory, more CTAs per SM
-    const size_t sm = (g.py.nst <= 2 ? 1 : 2) * (size_t)TX * g.ny * sizeof(T2);
+    // (stage 0 reads global, the last stage writes global), and a compiled
+    // plan runs its middle stages in place: half the shared memory, more
+    // CTAs per SM
+    const size_t sm = col_buffers<T>(g.py, TX) * (size_t)TX * g.ny * sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.nz, nf);
     if (sign > 0) {
         PF_COL_SWITCH(T, g.py, TX, set_smem(k_y_pass<T, 1, TXC, R16C, PIDC>, sm);
@@ -63,14 +64,14 @@ __global__ void __launch_bounds__(kThreads) k_z_pass(Geo g, typename Cx<T>::t* _
     auto dst = [&](int kz, int col, T2 v) {
         if (col < ncol) base[kz * zs + col] = v;
     };
-    cols_fft<SIGN, TX, true, 0, R16, PID>(g.pz, A, B, src, dst);
+    cols_fft<SIGN, TX, true, 0, R16, PID, true>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
 void launch_z_pass(const Geo& g, void* buf, int nf, int sign, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
     const int TX = tuned_cols<T>(g, g.tx_zf, g.nz, 2, 128 * 1024);
-    const size_t sm = (g.pz.nst <= 2 ? 1 : 2) * (size_t)TX * g.nz * sizeof(T2);  // as in the y pass
+    const size_t sm = col_buffers<T>(g.pz, TX) * (size_t)TX * g.nz * sizeof(T2);  // as in the y pass
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
     if (sign > 0) {
         PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_pass<T, 1, TXC, R16C, PIDC>, sm);
@@ -120,14 +121,16 @@ __global__ void __launch_bounds__(kThreads) k_z_fwd(Geo g, Phys ph, const typena
             out[gi] = OT2{(OT)(v.x * sc), (OT)(v.y * sc)};
         }
     };
-    cols_fft<-1, TX, false, 0, R16, PID>(g.pz, A, B, src, dst);
+    cols_fft<-1, TX, false, 0, R16, PID, true>(g.pz, A, B, src, dst);
 }
 
 template <typename T>
 void launch_z_fwd(const Geo& g, const Phys& ph, const void* W, void* out, int scale_mode, cudaStream_t s, int nf) {
     using T2 = typename Cx<T>::t;
     const int TX = tuned_cols<T>(g, g.tx_zf, g.nz, 2, 128 * 1024);
-    const size_t sm = (g.pz.nst <= 2 ? 1 : 2) * (size_t)TX * g.nz * sizeof(T2);  // as in the y pass
+    // modes 0/2 run the generic stages (two buffers for three or more stages)
+    const size_t sm = (scale_mode == 1 ? col_buffers<T>(g.pz, TX) : (g.pz.nst <= 2 ? 1 : 2)) * (size_t)TX * g.nz *
+                      sizeof(T2);
     dim3 grid((g.nxh + TX - 1) / TX, g.ny, nf);
     if (scale_mode == 1) {
         PF_COL_SWITCH(T, g.pz, TX, set_smem(k_z_fwd<T, T2, TXC, R16C, PIDC>, sm);
@@ -220,40 +223,6 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
 // stage, a barrier, then the stores).  NT = TX N / R threads, one per
 // (column, j) of the fused stage.
 // ---------------------------------------------------------------------------
-// one radix-R stage of NF fields of the [f][pos][TX] tile S, in place: each
-// thread first loads every butterfly it owns, the CTA synchronises, then the
-// butterflies are computed and stored (and the CTA synchronises again)
-template <int R, int SIGN, int TX, int N, int NS, int NF, int NT, typename T2>
-__device__ __forceinline__ void tile_stage_inplace(T2* S, const T2* __restrict__ tw) {
-    constexpr int M = N / R, JOBS = NF * TX * M, JPT = (JOBS + NT - 1) / NT, TWS = N / (NS * R);
-    T2 v[JPT][R];
-#pragma unroll
-    for (int u = 0; u < JPT; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (JOBS % NT == 0 || idx < JOBS) {
-            const int f = idx / (TX * M), r = idx - f * (TX * M), col = r % TX, j = r / TX;
-            const T2* src = S + f * (N * TX) + j * TX + col;
-#pragma unroll
-            for (int t = 0; t < R; ++t) v[u][t] = src[t * M * TX];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < JPT; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (JOBS % NT == 0 || idx < JOBS) {
-            const int f = idx / (TX * M), r = idx - f * (TX * M), col = r % TX, j = r / TX;
-            const int jq = j / NS, k = j - jq * NS;
-            if constexpr (NS > 1) apply_twiddles<R, SIGN>(v[u], tw, k * TWS);
-            Bfly<R, SIGN, T2>::run(v[u]);
-            T2* dst = S + f * (N * TX) + (jq * NS * R + k) * TX + col;
-#pragma unroll
-            for (int t = 0; t < R; ++t) dst[t * NS * TX] = v[u][t];
-        }
-    }
-    __syncthreads();
-}
-
 // stage from global (first forward stage) or to global (last inverse stage):
 // no staging, the tile is written only by loads from global or read only
 template <int R, int SIGN, int TX, int N, int NS, int NF, int NT, typename T2, class Ld, class St>

@@ -58,3 +58,29 @@ def test_elastic_plan_of_wrong_length_refused(pfg, params):
         cfg[38] = 1  # length 256
         with pytest.raises(pfg.PFError):
             s.set_tuning(cfg)
+
+
+@pytest.mark.parametrize("n", [96, 120, 160, 192, 640])
+@pytest.mark.parametrize("axis", ["y", "z"])
+def test_column_passes_three_stage_plans(pfg, params, n, axis):
+    """y and z column transforms of three-stage compiled plans, whose middle
+    stage runs in place in one shared buffer: one FP32-bulk RHS evaluation
+    against the oracle's, for every tile width the autotuner can choose."""
+    import torch
+    shape = (6, n, 10) if axis == "y" else (n, 6, 10)
+    y = synth.random_state(shape, 80 + n)
+    m = oracle.Model(shape, params)
+    yh = m.to_k(y)
+    ref = m.rhs_explicit(yh)
+    dev = torch.from_numpy(yh).to("cuda")
+    order = {96: [8, 4, 3], 120: [8, 3, 5], 160: [8, 4, 5], 192: [16, 4, 3], 640: [16, 8, 5]}[n]
+    a = 1 if axis == "y" else 2
+    with pfg.Simulation(shape, params, "ark4", "fp32bulk") as s:
+        for tx in (4, 8, 16):
+            cfg = s.tuning()
+            cfg[0] = cfg[1] = cfg[37] = tx
+            cfg[4 + 11 * a:4 + 11 * (a + 1)] = [3] + order + [0] * 7
+            s.set_tuning(cfg)
+            got = s.rhs_explicit(dev).cpu().numpy()
+            err = relerr(got, ref)
+            assert np.all(err <= 2e-5), (tx, err)
