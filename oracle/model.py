@@ -20,7 +20,9 @@ the readings:
   d/dphi_v = omega_vq clip(phi_v phi_q / eps, -1, 1) phi_q is continuous;
 * one solute (Nb);
 * homogeneous modulus (iteration 0 of the Hu-Chen scheme), stress-free mean
-  strain so that B(k = 0) = 0;
+  strain so that B(k = 0) = 0; with el_inhom set, a phase-dependent
+  (Reuss-mixed) stiffness solved by the Hu-Chen iterations of
+  oracle/elastic.py;
 * Nyquist wave numbers taken as +pi/dx.
 """
 from __future__ import annotations
@@ -121,6 +123,11 @@ class Model:
             self.lam[1 + v] = -self.L * self.kk[v]
         self.elastic_on = any(abs(x) > 0 for e in p["eps_star"] for x in e)
         self.B = elastic_B(self.kvec, p) if self.elastic_on else None
+        # phase-dependent stiffness: Hu-Chen iterations (oracle/elastic.py)
+        self.inhom = bool(p.get("el_inhom", 0)) and self.elastic_on
+        if self.inhom:
+            from .elastic import HuChen
+            self.hc = HuChen(self, p)
 
     # --- transforms -------------------------------------------------------
     def to_k(self, real: np.ndarray) -> np.ndarray:
@@ -163,6 +170,8 @@ class Model:
         of Eq. u_gov; functional derivative of the elastic energy w.r.t. h_v)."""
         if not self.elastic_on:
             return np.zeros_like(h)
+        if self.inhom:
+            return self.hc.solve(h)[0]
         hk = self.to_k(h)
         ek = np.einsum("vq...,q...->v...", self.B, hk)
         return self.to_r(ek)
@@ -213,7 +222,10 @@ class Model:
         V = self.N * self.dV
         for v in range(3):
             F += 0.5 * V * np.sum(w * self.kk[v] * np.abs(yhat[1 + v]) ** 2)
-        if self.elastic_on:
+        if self.inhom:
+            _, sig, el, _, _ = self.hc.solve(h)
+            F += 0.5 * float(np.sum(sig * el)) * self.dV
+        elif self.elastic_on:
             hk = self.to_k(h)
             for v in range(3):
                 for q in range(3):
