@@ -91,6 +91,17 @@ typedef struct {
     double h0, h_min, h_max;
     int max_rejects;
     double safety, k1, k2, eta_max, eta_min, eta_reject_min;
+    /* phase-dependent stiffness (Eq. u_gov with C(r) the Reuss mix of the
+       matrix constants C11/C12/C44 above and the precipitate constants
+       below), solved by Hu-Chen fixed-point iterations in FP64 around the
+       reference medium (C^m + C^v)/2 with a stress-free mean strain; stop
+       when max |eps(u)_n - eps(u)_{n-1}| <= el_tol max |eps0| or after
+       el_max_iter solves.  el_inhom = 0: homogeneous modulus (closed-form
+       Green kernel, one solve). */
+    int el_inhom;
+    double C11_v, C12_v, C44_v;
+    double el_tol;
+    int el_max_iter;
 } pf_params;
 
 typedef struct {
@@ -160,7 +171,8 @@ int pf_advance_attempts(pf_ctx* ctx, double t_final, double rtol, double atol, i
  * a single launch of a device-looped graph (a conditional WHILE node over the
  * rounds, a conditional IF node per member that skips finished members) and
  * the host waits once; where the driver lacks conditional nodes, or in
- * PF_BATCH_POLLED mode, the round graph is relaunched under a host poll.  At
+ * PF_BATCH_POLLED mode, the round graph is relaunched under a host poll.
+ * Members with el_inhom set are refused (PF_EUNSUPPORTED).  At
  * most pf_batch_round_cap() rounds (PF_ETIMEOUT beyond).  `out` has n entries or is NULL. */
 int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, double atol, pf_stats* out);
 
@@ -188,6 +200,9 @@ int pf_free_energy(pf_ctx* ctx, double* F_out);
  * controller history (e_prev = 1, no pending rejection). */
 int pf_get_time(pf_ctx* ctx, double* t, double* h);
 int pf_set_time(pf_ctx* ctx, double t, double h);
+/* Elastic solves of the last right-hand-side evaluation (the Hu-Chen
+ * iteration count with el_inhom set, else 1), or a negative error. */
+int pf_elastic_iterations(pf_ctx* ctx);
 /* Controller history for an exact resume: the last accepted ||LTE||_WRMS
  * (e_prev of the PI rule) and whether the last attempt was rejected (growth
  * capped at 1 next).  A checkpoint is pf_get_state_hat + pf_get_time +

@@ -42,6 +42,8 @@ class PFParams(C.Structure):
         ("max_rejects", C.c_int),
         ("safety", C.c_double), ("k1", C.c_double), ("k2", C.c_double),
         ("eta_max", C.c_double), ("eta_min", C.c_double), ("eta_reject_min", C.c_double),
+        ("el_inhom", C.c_int), ("C11_v", C.c_double), ("C12_v", C.c_double), ("C44_v", C.c_double),
+        ("el_tol", C.c_double), ("el_max_iter", C.c_int),
     ]
 
 
@@ -77,6 +79,7 @@ SIGNATURES = {
     "pf_set_time": (C.c_int, [_P, C.c_double, C.c_double]),
     "pf_get_stats": (C.c_int, [_P, C.POINTER(PFStats)]),
     "pf_get_controller": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "pf_elastic_iterations": (C.c_int, [_P]),
     "pf_set_controller": (C.c_int, [_P, C.c_double, C.c_int]),
     "pf_batch_round_cap": (C.c_longlong, [C.c_longlong]),
     "pf_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
@@ -158,6 +161,12 @@ def make_params(p: dict, method="ark4", precision="fp64") -> PFParams:
             q.eps_star[v][i] = float(p["eps_star"][v][i])
         q.omega_pair[v] = float(p["omega_pair"][v])
     q.max_rejects = int(p["max_rejects"])
+    q.el_inhom = int(p.get("el_inhom", 0))
+    q.C11_v = float(p.get("C11_v", p["C11"]))
+    q.C12_v = float(p.get("C12_v", p["C12"]))
+    q.C44_v = float(p.get("C44_v", p["C44"]))
+    q.el_tol = float(p.get("el_tol", 1e-6))
+    q.el_max_iter = int(p.get("el_max_iter", 20))
     q.method = METHODS[method] if isinstance(method, str) else int(method)
     q.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return q
@@ -318,6 +327,12 @@ class Simulation:
 
     def set_time(self, t, h):
         _check(lib().pf_set_time(self.ctx, float(t), float(h)), self.ctx)
+
+    def elastic_iterations(self):
+        """Hu-Chen solves of the last right-hand-side evaluation (1 without phase contrast)."""
+        n = lib().pf_elastic_iterations(self.ctx)
+        _check(n if n < 0 else PF_OK, self.ctx)
+        return n
 
     def controller(self):
         """(e_prev, after_reject) of the PI controller (checkpoint/resume)."""

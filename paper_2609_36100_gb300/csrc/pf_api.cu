@@ -218,6 +218,17 @@ struct pf_ctx {
     double gdiag = 0.0;      // common nonzero implicit diagonal entry, or 0
     double* partials = nullptr;
     int npartials = 0;
+    // phase-dependent stiffness (Hu-Chen iterations, FP64)
+    bool inhom = false;
+    HCConst hck{};
+    double* hc_tau = nullptr;      // eigenstress, real [8][N] (xx yy zz yz | xz xy, two padding fields)
+    double* hc_eu[2] = {};         // eps(u), real [8][N]: current and previous iterate
+    double2* hc_k = nullptr;       // k-space [8][NK] (tau^, then eps^(u))
+    double2* hc_ks = nullptr;      // partial-transform scratch [4][NK]
+    double* hc_part = nullptr;     // per-block statistics [blocks][11]
+    double* hc_ebar = nullptr;     // eps_bar on the device [6]
+    double* hc_host = nullptr;     // pinned: statistics [blocks][11] and eps_bar [6]
+    int hc_iters = 0;              // iterations of the last solve
     double* d_scalar = nullptr;
     double* h_scalar = nullptr;  // pinned
     // integrator state
@@ -368,6 +379,14 @@ void free_all(pf_ctx* c) {
     cudaFree(c->lamdf);
     cudaFree(c->qtab);
     cudaFree(c->partials);
+    cudaFree(c->hc_tau);
+    cudaFree(c->hc_eu[0]);
+    cudaFree(c->hc_eu[1]);
+    cudaFree(c->hc_k);
+    cudaFree(c->hc_ks);
+    cudaFree(c->hc_part);
+    cudaFree(c->hc_ebar);
+    if (c->hc_host) cudaFreeHost(c->hc_host);
     cudaFree(c->d_scalar);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
@@ -425,6 +444,93 @@ struct ProfScope {
         c->prof_recs.push_back({kind, e0, e1, bytes});
     }
 };
+
+// Hu-Chen solve of the phase-dependent elasticity for the real fields R
+// ([4][N] of type TR: X, phi_1..3) on the context's stream: iteration 0 with
+// tau = C0:eps0, then tau from the previous iterate until the change of
+// eps(u) is <= el_tol max |eps0| or el_max_iter solves; writes the driving
+// forces e_v into E ([3][N] of type TR, if not null) and the elastic energy
+// sum_r sigma:eps_el/2 (without the volume element) into *energy (if not
+// null).  Each transform is the FP64 four-field pipeline of set/get state.
+template <typename TR>
+int hc_solve(pf_ctx* c, const void* R, void* E, double* energy) {
+    const Geo& g = c->g;
+    const Phys& ph = c->ph;
+    cudaStream_t s = c->stream;
+    const HCConst& k = c->hck;
+    const int nb = hc_blocks();
+    const long long N = g.N, NK = g.NK;
+    double* host = c->hc_host;
+    double* ebar_h = host + (size_t)nb * 11;
+    auto forward = [&](const double* real, double2* out) {  // 4 real fields -> normalised k-space
+        launch_x_pass<double>(g, ph, XM_R2C_REAL, nullptr, c->hc_ks, nullptr, nullptr, nullptr, 0, 0, real, nullptr, s);
+        launch_y_pass<double>(g, c->hc_ks, 4, -1, s);
+        launch_z_fwd<double>(g, ph, c->hc_ks, out, 0, s);
+    };
+    auto inverse = [&](const double2* in, double* real) {  // 4 k-space fields -> real
+        StageTerms none{};
+        launch_z_stage<double>(g, ph, in, none, nullptr, c->hc_ks, s);
+        launch_y_pass<double>(g, c->hc_ks, 4, +1, s);
+        launch_x_pass<double>(g, ph, XM_C2R_REAL, c->hc_ks, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr, real, s);
+    };
+    auto green = [&](double* eu) {
+        forward(c->hc_tau, c->hc_k);
+        forward(c->hc_tau + 4 * N, c->hc_k + 4 * NK);
+        launch_hc_green(g, k, c->hc_k, s);
+        inverse(c->hc_k, eu);
+        inverse(c->hc_k + 4 * NK, eu + 4 * N);
+    };
+    // statistics -> eps_bar (host) and the change / scale
+    auto stats = [&](const double* eu, const double* prev, double& change, double& scale) -> int {
+        launch_hc_stats<TR>(g, k, R, eu, prev, c->hc_part, s);
+        PF_CUDA(c, cudaMemcpyAsync(host, c->hc_part, (size_t)nb * 11 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PF_CUDA(c, cudaStreamSynchronize(s));
+        double sum[11] = {};
+        for (int b = 0; b < nb; ++b)
+            for (int q = 0; q < 11; ++q) sum[q] = q < 9 ? sum[q] + host[b * 11 + q] : std::fmax(sum[q], host[b * 11 + q]);
+        double cav[3], sav[3], r[6];
+        for (int a = 0; a < 3; ++a) cav[a] = sum[a] / (double)N;
+        for (int a = 0; a < 6; ++a) r[a] = sum[3 + a] / (double)N;
+        // <C> is cubic: eps_bar = <C>^-1 r with the cubic compliance of <C>
+        const double d = (cav[0] - cav[1]) * (cav[0] + 2.0 * cav[1]);
+        sav[0] = (cav[0] + cav[1]) / d;
+        sav[1] = -cav[1] / d;
+        sav[2] = 1.0 / (2.0 * cav[2]);
+        const double tr = r[0] + r[1] + r[2];
+        for (int a = 0; a < 3; ++a) ebar_h[a] = (sav[0] - sav[1]) * r[a] + sav[1] * tr;
+        for (int a = 3; a < 6; ++a) ebar_h[a] = sav[2] * r[a];
+        PF_CUDA(c, cudaMemcpyAsync(c->hc_ebar, ebar_h, 6 * sizeof(double), cudaMemcpyHostToDevice, s));
+        change = sum[9];
+        scale = sum[10];
+        return PF_OK;
+    };
+    int cur = 0;
+    launch_hc_tau<TR>(g, k, R, nullptr, nullptr, c->hc_tau, s);
+    green(c->hc_eu[cur]);
+    double change = 0.0, scale = 0.0;
+    if (int rc = stats(c->hc_eu[cur], nullptr, change, scale)) return rc;
+    int it = 1;
+    const double tol = c->prm.el_tol * (scale > 0.0 ? scale : 1e-300);
+    while (it < c->prm.el_max_iter) {
+        const int prev = cur;
+        cur ^= 1;
+        launch_hc_tau<TR>(g, k, R, c->hc_eu[prev], c->hc_ebar, c->hc_tau, s);
+        green(c->hc_eu[cur]);
+        if (int rc = stats(c->hc_eu[cur], c->hc_eu[prev], change, scale)) return rc;
+        ++it;
+        if (!(change > tol)) break;  // also stops on a non-finite change
+    }
+    c->hc_iters = it;
+    if (E) launch_hc_force<TR>(g, k, R, c->hc_eu[cur], c->hc_ebar, E, s);
+    if (energy) {
+        launch_hc_energy<TR>(g, k, R, c->hc_eu[cur], c->hc_ebar, c->hc_part, s);
+        launch_reduce(c->hc_part, nb, 1.0, c->d_scalar + 2, s);
+        PF_CUDA(c, cudaMemcpyAsync(c->h_scalar + 2, c->d_scalar + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        PF_CUDA(c, cudaStreamSynchronize(s));
+        *energy = c->h_scalar[2];
+    }
+    return check_launch(c, "Hu-Chen elastic solve");
+}
 
 template <typename T>
 int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef = nullptr) {
@@ -493,7 +599,23 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef 
             ProfScope p(c, PF_K_Y, 4 * NK * 2 * cb);
             launch_y_pass<T>(g, c->W, 4, +1, s);
         }
-        if (ph.elastic) {
+        if (c->inhom) {
+            // phase-dependent stiffness: the real fields of the stage, then
+            // the Hu-Chen solve (driving forces into H as real fields), then
+            // the right-hand side from them
+            {
+                ProfScope p(c, PF_K_X_PHYS1, 4 * NK * cb + 4 * N * rb + 3 * NK * cb);
+                launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->H, Ri, nullptr, nullptr, 0, 0, nullptr, nullptr, s);
+            }
+            {
+                ProfScope p(c, PF_K_Z_ELASTIC, 0.0);
+                if (int rc = hc_solve<T>(c, Ri, c->H, nullptr)) return rc;
+            }
+            {
+                ProfScope p(c, PF_K_X_PHYS2, 3 * N * rb + 4 * N * rb + 4 * NK * cb);
+                launch_x_pass<T>(g, ph, XM_PHYS2R, c->H, c->W, nullptr, Ri, nullptr, 0, 0, nullptr, nullptr, s);
+            }
+        } else if (ph.elastic) {
             {
                 ProfScope p(c, PF_K_X_PHYS1, 4 * NK * cb + 4 * N * rb + 3 * NK * cb);
                 launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->H, Ri, nullptr, nullptr, 0, 0, nullptr, nullptr, s);
@@ -642,7 +764,11 @@ int rhs_explicit_t(pf_ctx* c, const double2* yh, double2* out) {
         launch_z_stage<T>(g, ph, yh, none, nullptr, c->W, s);
     }
     launch_y_pass<T>(g, c->W, 4, +1, s);
-    if (ph.elastic) {
+    if (c->inhom) {
+        launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->H, c->R, nullptr, nullptr, 0, 0, nullptr, nullptr, s);
+        if (int rc = hc_solve<T>(c, c->R, c->H, nullptr)) return rc;
+        launch_x_pass<T>(g, ph, XM_PHYS2R, c->H, c->W, nullptr, c->R, nullptr, 0, 0, nullptr, nullptr, s);
+    } else if (ph.elastic) {
         launch_x_pass<T>(g, ph, XM_PHYS1, c->W, c->H, c->R, nullptr, nullptr, 0, 0, nullptr, nullptr, s);
         launch_y_pass<T>(g, c->H, 3, -1, s);
         launch_z_elastic<T>(g, ph, c->H, s);
@@ -714,6 +840,16 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     c->prm = *params;
     c->fp32 = params->precision == PF_FP32BULK;
     derive_phys(*params, c->ph);
+    c->inhom = params->el_inhom != 0 && c->ph.elastic;
+    if (c->inhom) {
+        if (!(params->C11_v > params->C12_v) || !(params->C11_v + 2 * params->C12_v > 0) || !(params->C44_v > 0) ||
+            !(params->el_tol >= 0) || params->el_max_iter < 1) {
+            delete c;
+            return fail(nullptr, PF_EINVAL, "invalid precipitate stiffness or elastic-solver settings");
+        }
+        hc_constants(params->C11, params->C12, params->C44, params->C11_v, params->C12_v, params->C44_v,
+                     params->eps_star, c->hck);
+    }
     const Tableau& tb = c->tab;
     for (int i = 0; i < tb.s; ++i) {
         bool nf = tb.bE[i] != 0.0 || (tb.embedded && tb.btE[i] != 0.0);
@@ -794,6 +930,22 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     c->npartials = g.nz * g.ny / 2;
     if (energy_k_blocks(g) > c->npartials) c->npartials = energy_k_blocks(g);
     rc = rc ? rc : dalloc(c, &c->partials, (size_t)c->npartials * sizeof(double));
+    if (c->inhom) {
+        const size_t n8 = 8 * (size_t)g.N * sizeof(double);
+        rc = rc ? rc : dalloc(c, &c->hc_tau, n8);
+        rc = rc ? rc : dalloc(c, &c->hc_eu[0], n8);
+        rc = rc ? rc : dalloc(c, &c->hc_eu[1], n8);
+        rc = rc ? rc : dalloc(c, &c->hc_k, 8 * (size_t)g.NK * sizeof(double2));
+        rc = rc ? rc : dalloc(c, &c->hc_ks, 4 * (size_t)g.NK * sizeof(double2));
+        rc = rc ? rc : dalloc(c, &c->hc_part, (size_t)hc_blocks() * 11 * sizeof(double));
+        rc = rc ? rc : dalloc(c, &c->hc_ebar, 6 * sizeof(double));
+        if (!rc && cudaMallocHost((void**)&c->hc_host, ((size_t)hc_blocks() * 11 + 8) * sizeof(double)) != cudaSuccess)
+            rc = fail(c, PF_ENOMEM, "pinned host allocation failed");
+        // the padding fields of the second four-field group stay zero
+        if (!rc && (cudaMemset(c->hc_tau, 0, n8) != cudaSuccess || cudaMemset(c->hc_eu[0], 0, n8) != cudaSuccess ||
+                    cudaMemset(c->hc_eu[1], 0, n8) != cudaSuccess))
+            rc = fail(c, PF_ECUDA, "cudaMemset failed");
+    }
     rc = rc ? rc : dalloc(c, &c->d_scalar, 4 * sizeof(double));
     if (!rc && cudaMallocHost((void**)&c->h_scalar, 4 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -1068,6 +1220,10 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
         if (!ctxs[i]) return fail(nullptr, PF_EINVAL, "pf_batch_advance: NULL context %d", i);
         if (ctxs[i]->prm.method != ctxs[0]->prm.method || ctxs[i]->fp32 != ctxs[0]->fp32)
             return fail(ctxs[i], PF_EINVAL, "pf_batch_advance: members differ in method or precision");
+        if (ctxs[i]->inhom)
+            return fail(ctxs[i], PF_EUNSUPPORTED,
+                        "pf_batch_advance: the Hu-Chen elastic solve reads its convergence on the host per iteration "
+                        "and cannot run inside the batch graph");
         if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->dev != ctxs[0]->dev)
             return fail(ctxs[i], PF_EINVAL, "pf_batch_advance: members must share the device and stream");
     }
@@ -1322,6 +1478,18 @@ int pf_free_energy(pf_ctx* c, double* F_out) {
     double2* S1 = c->ynew;
     double2* S2 = fp64_scratch(c);
     StageTerms none{};
+    double Fel = 0.0;
+    Phys phk = c->ph;
+    if (c->inhom) {
+        // elastic energy of the Hu-Chen equilibrium of the current state, in
+        // real space; the closed-form k-space kernel term is left out below
+        double* real = reinterpret_cast<double*>(S2);
+        launch_z_stage<double>(g, c->ph, c->y, none, nullptr, S1, s);
+        launch_y_pass<double>(g, S1, 4, +1, s);
+        launch_x_pass<double>(g, c->ph, XM_C2R_REAL, S1, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr, real, s);
+        if (int rc = hc_solve<double>(c, real, nullptr, &Fel)) return rc;
+        phk.elastic = 0;
+    }
     launch_z_stage<double>(g, c->ph, c->y, none, nullptr, S1, s);
     launch_y_pass<double>(g, S1, 4, +1, s);
     launch_x_pass<double>(g, c->ph, XM_ENERGY, S1, S2, nullptr, nullptr, c->partials, 0, 0, nullptr, nullptr, s);
@@ -1330,7 +1498,7 @@ int pf_free_energy(pf_ctx* c, double* F_out) {
     launch_reduce(c->partials, x_pass_blocks(g, 1), 1.0, c->d_scalar, s);  // local densities
     launch_y_pass<double>(g, S2, 3, -1, s);
     launch_z_fwd<double>(g, c->ph, S2, S1, 0, s, 3);  // h^ (normalised) into S1
-    launch_energy_k(g, c->ph, c->y, S1, c->partials, s);
+    launch_energy_k(g, phk, c->y, S1, c->partials, s);
     launch_reduce(c->partials, energy_k_blocks(g), 1.0, c->d_scalar + 1, s);
     rc = check_launch(c, "pf_free_energy");
     if (rc) return rc;
@@ -1338,7 +1506,7 @@ int pf_free_energy(pf_ctx* c, double* F_out) {
     PF_CUDA(c, cudaStreamSynchronize(s));
     const double dV = c->grid.dx * c->grid.dy * c->grid.dz;
     const double V = (double)g.N * dV;
-    *F_out = c->h_scalar[0] * dV + 0.5 * V * c->h_scalar[1];
+    *F_out = c->h_scalar[0] * dV + 0.5 * V * c->h_scalar[1] + Fel * dV;
     return PF_OK;
 }
 
@@ -1356,6 +1524,11 @@ int pf_set_time(pf_ctx* c, double t, double h) {
     c->e_prev = 1.0;
     c->after_reject = false;
     return PF_OK;
+}
+
+int pf_elastic_iterations(pf_ctx* c) {
+    if (!c) return fail(c, PF_EINVAL, "pf_elastic_iterations: NULL context");
+    return c->inhom ? c->hc_iters : 1;
 }
 
 int pf_get_controller(pf_ctx* c, double* e_prev, int* after_reject) {

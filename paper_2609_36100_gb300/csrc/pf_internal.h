@@ -147,13 +147,39 @@ struct BatchConst {
     int max_rejects, q;
 };
 
+// Constants of the phase-dependent stiffness (Hu-Chen iterations): cubic
+// reference medium, matrix and precipitate compliances, eigenstrains
+// (Voigt order xx yy zz yz xz xy, tensor shears)
+struct HCConst {
+    double c0[3];         // reference medium c11, c12, c44 (sigma_xy = 2 c44 eps_xy)
+    double sm[3], sv[3];  // compliances s11, s12, s44 (eps_xy = s44 sigma_xy)
+    double eps[3][6];
+};
+void hc_constants(double C11, double C12, double C44, double C11v, double C12v, double C44v,
+                  const double eps[3][6], HCConst& k);
+int hc_blocks();
+template <typename T>
+void launch_hc_tau(const Geo& g, const HCConst& k, const void* R, const double* eu, const double* ebar, double* tau,
+                   cudaStream_t s);
+void launch_hc_green(const Geo& g, const HCConst& k, double2* hk, cudaStream_t s);
+template <typename T>
+void launch_hc_stats(const Geo& g, const HCConst& k, const void* R, const double* eu, const double* eu_prev,
+                     double* part, cudaStream_t s);
+template <typename T>
+void launch_hc_force(const Geo& g, const HCConst& k, const void* R, const double* eu, const double* ebar, void* E,
+                     cudaStream_t s);
+template <typename T>
+void launch_hc_energy(const Geo& g, const HCConst& k, const void* R, const double* eu, const double* ebar,
+                      double* part, cudaStream_t s);
+
 enum XMode {
     XM_PHYS1 = 0,      // C2R state -> real fields, h(phi) -> R2C (or the full RHS when elasticity is off)
     XM_PHYS2 = 1,      // C2R elastic potential + stored real fields -> RHS -> R2C
     XM_WRMS = 2,       // C2R local error + weights from stored real y -> partial sums
     XM_R2C_REAL = 3,   // real FP64 fields -> R2C (set_state)
     XM_C2R_REAL = 4,   // C2R -> real FP64 fields (get_state)
-    XM_ENERGY = 5      // C2R state -> local free-energy density partial sums + h -> R2C
+    XM_ENERGY = 5,     // C2R state -> local free-energy density partial sums + h -> R2C
+    XM_PHYS2R = 6      // real-space elastic potential (argument `in`, [3][N]) + stored real fields -> RHS -> R2C
 };
 
 // Host launchers (defined in pf_kernels.cu).  `T` = compute type.

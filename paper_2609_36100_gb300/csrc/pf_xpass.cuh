@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
     int Fin = 0;
     if (mode == XM_PHYS1 || mode == XM_WRMS || mode == XM_C2R_REAL || mode == XM_ENERGY) Fin = 4;
     if (mode == XM_PHYS2) Fin = ph.elastic ? 3 : 0;
+    const T* Ereal = mode == XM_PHYS2R ? reinterpret_cast<const T*>(in) : nullptr;
     T2* RS = S0;  // real-space lines (a + i b)
     if (mode == XM_R2C_REAL) {
 #pragma unroll 4
@@ -275,14 +276,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
     // ---- pointwise physics: 2 rows per line, all fields of a point together
     int Fout = 0;
     double eacc = 0.0;
-    const bool full_rhs = (mode == XM_PHYS2) || (mode == XM_PHYS1 && !ph.elastic);
+    const bool full_rhs = (mode == XM_PHYS2) || (mode == XM_PHYS2R) || (mode == XM_PHYS1 && !ph.elastic);
 #pragma unroll 2
     for (int e = threadIdx.x; e < P * nx; e += blockDim.x) {
         const int rp = L.divn(e), x = e - rp * nx;
         if (rp0 + rp >= npairs) continue;
         const long long row = 2LL * (rp0 + rp);
         T Xr[2], pr[2][3], er[2][3];
-        if (mode == XM_PHYS2) {
+        if (mode == XM_PHYS2 || mode == XM_PHYS2R) {
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 const T* b = Rin + (long long)f * g.N + row * nx + x;
@@ -296,7 +297,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
             }
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                if (ph.elastic) {
+                if (Ereal) {
+                    const T* b = Ereal + (long long)v * g.N + row * nx + x;
+                    er[0][v] = b[0];
+                    er[1][v] = b[nx];
+                } else if (ph.elastic) {
                     const T2 z = RS[(rp * 3 + v) * ls + skew<true>(x)];
                     er[0][v] = z.x;
                     er[1][v] = z.y;

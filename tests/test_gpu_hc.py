@@ -1,0 +1,96 @@
+"""Phase-dependent stiffness (Eq. u_gov with the Reuss-mixed C(r), solved by
+Hu-Chen iterations in FP64) through the C ABI against the oracle's
+independent formulation (oracle/elastic.py: full fourth-order tensors,
+Mandel inversion, numpy FFTs)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pfg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_36100_gb300 as m
+    m.build()
+    return m
+
+
+def relerr(a, b):
+    return np.array([np.linalg.norm((a[f] - b[f]).ravel()) / np.linalg.norm(b[f].ravel()) for f in range(a.shape[0])])
+
+
+def contrast(params, tol=1e-12, it=200):
+    return dict(params, el_inhom=1, C11_v=1.3 * params["C11"], C12_v=1.1 * params["C12"], C44_v=1.2 * params["C44"],
+                el_tol=tol, el_max_iter=it)
+
+
+def state(shape, seed):
+    """Precipitate-like fields with sum_v h(phi_v) <= 1 (a valid compliance mix)."""
+    y = synth.random_state(shape, seed)
+    y[1:] *= 0.4
+    return y
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 10, 20)])
+@pytest.mark.parametrize("tol", [1e-12, 1e-2])
+def test_rhs_fp64_matches_oracle(pfg, params, shape, tol):
+    """Converged (1e-12) and loose (1e-2: a few iterations) tolerances: the
+    same iteration count as the oracle and the explicit right-hand side to
+    1e-11 per field."""
+    import torch
+    p = contrast(params, tol)
+    y = state(shape, 31)
+    m = oracle.Model(shape, p)
+    yh = m.to_k(y)
+    ref = m.rhs_explicit(yh)
+    its = m.hc.solve(oracle.h_interp(m.to_r(yh)[1:]))[4]
+    with pfg.Simulation(shape, p, "ark4", "fp64") as s:
+        got = s.rhs_explicit(torch.from_numpy(yh).to("cuda")).cpu().numpy()
+        assert s.elastic_iterations() == its
+    assert its >= 2
+    assert np.all(relerr(got, ref) <= 1e-11), relerr(got, ref)
+
+
+def test_rhs_fp32bulk_matches_oracle(pfg, params):
+    import torch
+    p = contrast(params)
+    shape = (16, 16, 16)
+    y = state(shape, 32)
+    m = oracle.Model(shape, p)
+    yh = m.to_k(y)
+    ref = m.rhs_explicit(yh)
+    with pfg.Simulation(shape, p, "ark4", "fp32bulk") as s:
+        got = s.rhs_explicit(torch.from_numpy(yh).to("cuda")).cpu().numpy()
+    assert np.all(relerr(got, ref) <= 2e-5), relerr(got, ref)
+
+
+def test_ark4_step_and_free_energy(pfg, params):
+    p = contrast(params)
+    y0 = synth.ic_spheres(16, 2, 2.5, 3.5, 7, p)
+    m = oracle.Model(y0.shape[1:], p)
+    yh, e, _ = oracle.ark_step(m, m.to_k(y0), 0.5, oracle.ark436l2sa(), p["rtol"], p["atol"])
+    F0 = m.free_energy(m.to_k(y0))
+    with pfg.Simulation(y0.shape[1:], p, "ark4", "fp64") as s:
+        s.set_state(y0)
+        F = s.free_energy()
+        eg = s.step(0.5)
+        got = s.state_hat().cpu().numpy()
+    assert F == pytest.approx(F0, rel=1e-12)
+    assert np.all(relerr(got, yh) <= 1e-11), relerr(got, yh)
+    assert eg == pytest.approx(e, rel=1e-8)
+
+
+def test_batch_refuses_phase_contrast(pfg, params):
+    p = contrast(params)
+    y0 = synth.ic_spheres(16, 2, 2.5, 3.5, 7, p)
+    with pfg.Simulation(y0.shape[1:], p, "ark4", "fp32bulk") as s:
+        s.set_state(y0)
+        with pytest.raises(pfg.PFError) as ei:
+            pfg.batch_advance([s], 2.0)
+        assert ei.value.code == pfg.PF_EUNSUPPORTED
