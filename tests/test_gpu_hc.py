@@ -22,7 +22,12 @@ def pfg():
 
 
 def relerr(a, b):
-    return np.array([np.linalg.norm((a[f] - b[f]).ravel()) / np.linalg.norm(b[f].ravel()) for f in range(a.shape[0])])
+    """Relative L2 error per field (absolute where the reference field is zero)."""
+    out = []
+    for f in range(a.shape[0]):
+        den = np.linalg.norm(b[f].ravel())
+        out.append(np.linalg.norm((a[f] - b[f]).ravel()) / (den if den > 0 else 1.0))
+    return np.array(out)
 
 
 def contrast(params, tol=1e-12, it=200):
