@@ -213,8 +213,7 @@ struct pf_ctx {
     void* R = nullptr;
     void* R1 = nullptr;
     double* lam = nullptr;   // [4][NK] lambda(k), FP64
-    float2* lamdf = nullptr;  // [4][NK] lambda(k), double-float (FP32-bulk contexts, anisotropic gradients)
-    float2* k2df = nullptr;   // [NK] |k|^2, double-float (FP32-bulk contexts, isotropic gradients)
+    float2* lamdf = nullptr;  // [4][NK] lambda(k), double-float (FP32-bulk contexts)
     double* qtab = nullptr;  // [4][NK] 1/(1 - dt gamma lambda) of the current step (ESDIRK diagonal)
     double gdiag = 0.0;      // common nonzero implicit diagonal entry, or 0
     double* partials = nullptr;
@@ -378,7 +377,6 @@ void free_all(pf_ctx* c) {
     cudaFree(c->R1);
     cudaFree(c->lam);
     cudaFree(c->lamdf);
-    cudaFree(c->k2df);
     cudaFree(c->qtab);
     cudaFree(c->partials);
     cudaFree(c->hc_tau);
@@ -564,7 +562,7 @@ int enqueue_step(pf_ctx* c, double dt, bool want_lte, const StageCoefDev* dcoef 
         split_ds(st.gamma, st.gh, st.gl);
         set_masks(st);
         st.dc = dcoef ? dcoef + i : nullptr;
-        if (c->gdiag != 0.0 && !c->k2df) {
+        if (c->gdiag != 0.0) {
             if (i == 0) {
                 st.qout = c->qtab;
                 st.qgamma = dt * c->gdiag;
@@ -926,12 +924,7 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     rc = rc ? rc : dalloc(c, &c->R, 4 * (size_t)g.N * tsz);
     rc = rc ? rc : dalloc(c, &c->R1, 4 * (size_t)g.N * tsz);
     rc = rc ? rc : dalloc(c, &c->lam, nk4 * sizeof(double));
-    // FP32-bulk streams: lambda from a |k|^2 table where the gradient tensors
-    // are isotropic (8 B per k-point instead of 8 B per element, and no table
-    // of 1/(1 - gamma lambda)), else the per-element double-float table
-    const bool k2tab = c->fp32 && c->ph.kap_iso;
-    if (k2tab) rc = rc ? rc : dalloc(c, &c->k2df, (size_t)g.NK * sizeof(float2));
-    if (c->fp32 && !k2tab) rc = rc ? rc : dalloc(c, &c->lamdf, nk4 * sizeof(float2));
+    if (c->fp32) rc = rc ? rc : dalloc(c, &c->lamdf, nk4 * sizeof(float2));
     rc = rc ? rc : dalloc(c, &c->qtab, nk4 * sizeof(double));
     // worst case over any tuned rows-per-CTA setting (one row pair per CTA)
     c->npartials = g.nz * g.ny / 2;
@@ -991,17 +984,9 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
         g.ky = c->d_ky;
         g.kz = c->d_kz;
         launch_lambda_table(g, c->ph, c->lam, c->lamdf, c->stream);
-        if (c->k2df) {
-            launch_k2_table(g, c->k2df, c->stream);
-            for (int f = 0; f < 4; ++f) {
-                const float h = (float)c->ph.lamc[f];
-                g.lamcdf[f] = make_float2(h, (float)(c->ph.lamc[f] - (double)h));
-            }
-        }
         e = cudaGetLastError();
         g.lam = c->lam;
         g.lamdf = c->lamdf;
-        g.k2df = c->k2df;
     }
     e = e ? e : cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {

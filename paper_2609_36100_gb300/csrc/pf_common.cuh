@@ -441,32 +441,18 @@ struct CoefSrc {
     __device__ __forceinline__ DF qgamma() const { return dev() ? DF{st.dc->qgh, st.dc->qgl} : DF{st.qgh, st.qgl}; }
 };
 
-// lambda(k) of element (field f, k-point q) as double-float: from the |k|^2
-// table and the per-field factor where the gradient tensors are isotropic,
-// else from the per-element table
-template <typename Idx>
-__device__ __forceinline__ DF lambda_df(const Geo& g, Idx gi, int f, Idx q) {
-    if (g.k2df) {
-        const float2 k2 = __ldg(g.k2df + q);
-        const float2 c = f == 0 ? g.lamcdf[0] : f == 1 ? g.lamcdf[1] : f == 2 ? g.lamcdf[2] : g.lamcdf[3];
-        return df_mul(DF{c.x, c.y}, DF{k2.x, k2.y});
-    }
-    const float2 lt = __ldg(g.lamdf + gi);
-    return DF{lt.x, lt.y};
-}
-
 // at most MAXT earlier-stage terms (compile-time bound: fewer registers);
 // Idx: element index type (unsigned where 4 NK < 2^32: one-instruction
 // address arithmetic)
 template <int MAXT = kMaxStages, int DC = -1, typename Idx = long long>
 __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms& st, const double2* __restrict__ y,
-                                                 Idx gi, int f, Idx q, float4* __restrict__ zout) {
+                                                 Idx gi, float4* __restrict__ zout) {
     const CoefSrc<DC> cs{st};
     // every load first (independent, all in flight together), then the sums
     const bool need_lam = st.mI != 0u || st.qout || st.has_gamma;
     const bool load_q = st.has_gamma && st.qin;
     const double2 yv = __ldg(y + gi);
-    const DF lamv = need_lam ? lambda_df(g, gi, f, q) : DF{0.f, 0.f};
+    const float2 lt = need_lam ? __ldg(g.lamdf + gi) : make_float2(0.f, 0.f);
     const float2 qt = load_q ? __ldg(reinterpret_cast<const float2*>(st.qin) + gi) : make_float2(1.f, 0.f);
     const unsigned mz = st.mI & ~st.mY;
     float4 zv[MAXT > 0 ? MAXT : 1];
@@ -497,7 +483,7 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
     }
     DF rx = df_add(yx, E.x()), ry = df_add(yy, E.y());
     if (need_lam) {
-        const DF lam = lamv;
+        const DF lam{lt.x, lt.y};
         if (st.mI != 0u) {
             rx = df_add(rx, df_mul(lam, I.x()));
             ry = df_add(ry, df_mul(lam, I.y()));
@@ -523,14 +509,14 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
 // DC and Idx as in stage_value_df.
 template <int MAXT = kMaxStages, int DC = -1, typename Idx = long long>
 __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms& bt, const StageTerms& dt,
-                                                 int want_lte, const double2* __restrict__ y, Idx gi, int f, Idx q,
+                                                 int want_lte, const double2* __restrict__ y, Idx gi,
                                                  double2* __restrict__ ynew) {
     const CoefSrc<DC> cb{bt}, cd{dt};
     const unsigned lmI = want_lte ? dt.mI : 0u, lmE = want_lte ? dt.mE : 0u;
     const unsigned mI = bt.mI | lmI, mE = bt.mE | lmE, mz = mI & ~bt.mY;
     // every load first, then the sums
     const double2 yv = __ldg(y + gi);
-    const DF lamv = mI != 0u ? lambda_df(g, gi, f, q) : DF{0.f, 0.f};
+    const float2 lt = mI != 0u ? __ldg(g.lamdf + gi) : make_float2(0.f, 0.f);
     float4 zv[MAXT];
     float2 fv[MAXT];
 #pragma unroll
@@ -575,7 +561,7 @@ __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms&
             }
         }
     }
-    const DF lam = lamv;
+    const DF lam{lt.x, lt.y};
     const DF dx = df_add(df_mul(lam, Ib.x()), Eb.x()), dy = df_add(df_mul(lam, Ib.y()), Eb.y());
     ynew[gi] = make_double2(yv.x + df_to_d(dx), yv.y + df_to_d(dy));
     return make_float2(__fmaf_rn(lam.h, dIx, dEx), __fmaf_rn(lam.h, dIy, dEy));

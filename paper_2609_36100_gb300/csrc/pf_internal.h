@@ -43,10 +43,7 @@ struct Geo {
     const double* ky;  // [ny]
     const double* kz;  // [nz]
     const double* lam;  // [4][NK] lambda(k) per field (FP64), or null (computed on the fly)
-    const float2* lamdf;  // [4][NK] lambda(k) as double-float {h, l} (FP32-bulk contexts without k2df)
-    const float2* k2df;   // [NK] |k|^2 as double-float (FP32-bulk, isotropic gradient tensors): lambda
-                          // = lamcdf[f] |k|^2 and 1/(1 - gamma lambda) formed per element, no tables read
-    float2 lamcdf[4];     // lambda / |k|^2 per field, double-float
+    const float2* lamdf;  // [4][NK] lambda(k) as double-float {h, l} (FP32-bulk contexts)
     const float* kx32;  // FP32 copies of the wave-number tables (FP32-bulk kernels)
     const float* ky32;
     const float* kz32;
@@ -213,7 +210,6 @@ void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, cons
                             double2* zout, cudaStream_t s);
 void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s);
 void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamdf, cudaStream_t s);
-void launch_k2_table(const Geo& g, float2* k2df, cudaStream_t s);
 // FP32-bulk stage assembly as a streaming pass (double-float z_i out, FP32
 // transform input W out); the inverse z transform follows as launch_z_pass
 void launch_stage_assemble(const Geo& g, const double2* y, const StageTerms& st, double2* zout, void* W,

@@ -46,20 +46,8 @@ __global__ void k_stage_pointwise_df(Geo g, const double2* __restrict__ y, Stage
     if (y_swapped(g)) y = g.yother;
     const long long total = 4LL * g.NK;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
-         gi += (long long)gridDim.x * blockDim.x) {
-        const int f = (int)(gi / g.NK);
-        stage_value_df(g, st, y, gi, f, gi - f * g.NK, zout);
-    }
-}
-
-// (field, k-point) of element gi advanced by a stride (stride >= 0)
-template <typename Idx>
-__device__ __forceinline__ void advance_fq(const Geo& g, Idx stride, int& f, Idx& q) {
-    q += stride;
-    while (q >= (Idx)g.NK) {
-        q -= (Idx)g.NK;
-        ++f;
-    }
+         gi += (long long)gridDim.x * blockDim.x)
+        stage_value_df(g, st, y, gi, zout);
 }
 
 // FP32-bulk stage assembly, streaming: each element's loads all issued
@@ -75,20 +63,11 @@ __global__ void __launch_bounds__(256) k_stage_assemble_df(Geo g, const double2*
     if (y_swapped(g)) y = g.yother;
     const Idx total = (Idx)(4LL * g.NK);
     const Idx stride = (Idx)gridDim.x * blockDim.x;
-    const Idx gi0 = (Idx)blockIdx.x * blockDim.x + threadIdx.x;
-    int f = (int)(gi0 / (Idx)g.NK);
-    Idx q = gi0 - (Idx)f * (Idx)g.NK;
-    for (Idx gi = gi0; gi < total; gi += stride * U) {
+    for (Idx gi = (Idx)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += stride * U) {
         float2 r[U];
-        int fu = f;
-        Idx qu = q;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (gi + u * stride < total) r[u] = stage_value_df<MAXT, DC, Idx>(g, st, y, gi + u * stride, fu, qu, zout);
-            advance_fq(g, stride, fu, qu);
-        }
-        f = fu;
-        q = qu;
+        for (int u = 0; u < U; ++u)
+            if (gi + u * stride < total) r[u] = stage_value_df<MAXT, DC, Idx>(g, st, y, gi + u * stride, zout);
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (gi + u * stride < total) W[gi + u * stride] = r[u];
@@ -160,13 +139,9 @@ __global__ void __launch_bounds__(256) k_step_complete_df(Geo g, const double2* 
     }
     const Idx total = (Idx)(4LL * g.NK);
     const Idx stride = (Idx)gridDim.x * blockDim.x;
-    const Idx gi0 = (Idx)blockIdx.x * blockDim.x + threadIdx.x;
-    int f = (int)(gi0 / (Idx)g.NK);
-    Idx q = gi0 - (Idx)f * (Idx)g.NK;
-    for (Idx gi = gi0; gi < total; gi += stride) {
-        const float2 e = final_value_df<MAXT, DC, Idx>(g, bt, dt, want_lte, y, gi, f, q, ynew);
+    for (Idx gi = (Idx)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += stride) {
+        const float2 e = final_value_df<MAXT, DC, Idx>(g, bt, dt, want_lte, y, gi, ynew);
         if (want_lte) W[gi] = e;
-        advance_fq(g, stride, f, q);
     }
 }
 
@@ -248,21 +223,6 @@ __global__ void k_lambda_table(Geo g, Phys ph, double* __restrict__ lam, float2*
         }
     }
 }
-
-// |k|^2 per k-point as double-float (FP64 sum of the squares, then split)
-__global__ void k_k2_table(Geo g, float2* __restrict__ k2df) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.NK;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int kx = (int)(q % g.nxh);
-        const int ky = (int)((q / g.nxh) % g.ny);
-        const int kz = (int)(q / ((long long)g.nxh * g.ny));
-        const double k2 = g.kx[kx] * g.kx[kx] + g.ky[ky] * g.ky[ky] + g.kz[kz] * g.kz[kz];
-        const float h = (float)k2;
-        k2df[q] = make_float2(h, (float)(k2 - (double)h));
-    }
-}
-
-void launch_k2_table(const Geo& g, float2* k2df, cudaStream_t s) { k_k2_table<<<152 * 8, 256, 0, s>>>(g, k2df); }
 
 void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamdf, cudaStream_t s) {
     k_lambda_table<<<152 * 8, 256, 0, s>>>(g, ph, lam, lamdf);
