@@ -214,6 +214,7 @@ struct pf_ctx {
     void* R1 = nullptr;
     double* lam = nullptr;   // [4][NK] lambda(k), FP64
     float2* lamdf = nullptr;  // [4][NK] lambda(k), double-float (FP32-bulk contexts)
+    float* btab = nullptr;    // FP32 elastic-kernel table (FP32-bulk contexts with diagonal eigenstrains)
     double* qtab = nullptr;  // [4][NK] 1/(1 - dt gamma lambda) of the current step (ESDIRK diagonal)
     double gdiag = 0.0;      // common nonzero implicit diagonal entry, or 0
     double* partials = nullptr;
@@ -377,6 +378,7 @@ void free_all(pf_ctx* c) {
     cudaFree(c->R1);
     cudaFree(c->lam);
     cudaFree(c->lamdf);
+    cudaFree(c->btab);
     cudaFree(c->qtab);
     cudaFree(c->partials);
     cudaFree(c->hc_tau);
@@ -925,6 +927,14 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     rc = rc ? rc : dalloc(c, &c->R1, 4 * (size_t)g.N * tsz);
     rc = rc ? rc : dalloc(c, &c->lam, nk4 * sizeof(double));
     if (c->fp32) rc = rc ? rc : dalloc(c, &c->lamdf, nk4 * sizeof(float2));
+    // elastic-kernel table: FP32-bulk, homogeneous modulus, diagonal
+    // eigenstrains (B even in each wave-number component), at most 256 MB
+    bool diag = true;
+    for (int v = 0; v < 3; ++v)
+        for (int a = 3; a < 6; ++a) diag = diag && params->eps_star[v][a] == 0.0;
+    const long long tabn = (long long)(g.nz / 2 + 1) * (g.ny / 2 + 1) * g.nxh;
+    if (c->fp32 && c->ph.elastic && !c->inhom && diag && 6 * tabn * (long long)sizeof(float) <= (256LL << 20))
+        rc = rc ? rc : dalloc(c, &c->btab, 6 * (size_t)tabn * sizeof(float));
     rc = rc ? rc : dalloc(c, &c->qtab, nk4 * sizeof(double));
     // worst case over any tuned rows-per-CTA setting (one row pair per CTA)
     c->npartials = g.nz * g.ny / 2;
@@ -984,9 +994,11 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
         g.ky = c->d_ky;
         g.kz = c->d_kz;
         launch_lambda_table(g, c->ph, c->lam, c->lamdf, c->stream);
+        if (c->btab) launch_btab(g, c->ph, c->btab, c->stream);
         e = cudaGetLastError();
         g.lam = c->lam;
         g.lamdf = c->lamdf;
+        g.btab = c->btab;
     }
     e = e ? e : cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {

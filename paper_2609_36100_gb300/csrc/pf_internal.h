@@ -57,6 +57,8 @@ struct Geo {
     int tx_zf;               // tuned tile width of the forward z pass, 0 = heuristic
     int el_pid;              // compiled plan of the fused elastic pass (length nz), 0 = the z-axis plan
     int xf_off;              // 1: the FP32 x passes use the staged kernel instead of the fused one
+    const float* btab;       // FP32 elastic kernel B(k) / N over kx >= 0, |ky| <= ny/2, |kz| <= nz/2 (six
+                             // symmetric entries, [6][nz/2+1][ny/2+1][nx/2+1]), or null: computed per k
 };
 
 // Model constants of the real-space and elastic terms in one compute type,
@@ -210,6 +212,9 @@ void launch_stage_pointwise(const Geo& g, const Phys& ph, const double2* y, cons
                             double2* zout, cudaStream_t s);
 void launch_solve(const Geo& g, const Phys& ph, double gamma, const double2* r, double2* z, cudaStream_t s);
 void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamdf, cudaStream_t s);
+// FP32 table of the elastic kernel B_vq(k)/N (diagonal eigenstrains: B is
+// even in each wave-number component, so |ky| and |kz| index it)
+void launch_btab(const Geo& g, const Phys& ph, float* btab, cudaStream_t s);
 // FP32-bulk stage assembly as a streaming pass (double-float z_i out, FP32
 // transform input W out); the inverse z transform follows as launch_z_pass
 void launch_stage_assemble(const Geo& g, const double2* y, const StageTerms& st, double2* zout, void* W,

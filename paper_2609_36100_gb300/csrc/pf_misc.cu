@@ -224,6 +224,31 @@ __global__ void k_lambda_table(Geo g, Phys ph, double* __restrict__ lam, float2*
     }
 }
 
+// B_vq(k) / N in FP64, rounded to FP32, over kx in [0, nx/2], ky, kz in
+// [0, n/2] (the kernel is even in each component for diagonal eigenstrains)
+__global__ void k_btab(Geo g, Phys ph, float* __restrict__ tab) {
+    const int hy = g.ny / 2 + 1, hz = g.nz / 2 + 1;
+    const long long n = (long long)hz * hy * g.nxh;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % g.nxh);
+        const int ky = (int)((i / g.nxh) % hy);
+        const int kz = (int)(i / ((long long)g.nxh * hy));
+        double Bm[3][3];
+        elastic_kernel<double>(ph.t64, g.kx[kx], g.ky[ky], g.kz[kz], Bm);
+        const double s = g.invN;
+        tab[0 * n + i] = (float)(Bm[0][0] * s);
+        tab[1 * n + i] = (float)(Bm[0][1] * s);
+        tab[2 * n + i] = (float)(Bm[0][2] * s);
+        tab[3 * n + i] = (float)(Bm[1][1] * s);
+        tab[4 * n + i] = (float)(Bm[1][2] * s);
+        tab[5 * n + i] = (float)(Bm[2][2] * s);
+    }
+}
+
+void launch_btab(const Geo& g, const Phys& ph, float* btab, cudaStream_t s) {
+    k_btab<<<152 * 8, 256, 0, s>>>(g, ph, btab);
+}
+
 void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamdf, cudaStream_t s) {
     k_lambda_table<<<152 * 8, 256, 0, s>>>(g, ph, lam, lamdf);
 }

@@ -306,15 +306,34 @@ __global__ void __launch_bounds__(NT, elastic_min_blocks<T, PID, NT>())
         const T invN = std::is_same<T, float>::value ? (T)g.invN32 : (T)g.invN;
         const PhysT<T>& pt = phys_t<T>(ph);
         const T kxv = kval<T>(g, 0, kx0 + (col < ncol ? col : 0)), kyv = kval<T>(g, 1, ky);
+        // FP32 contexts with diagonal eigenstrains read B/N from the table
+        // (held in L2 across the tiles); otherwise B is formed per wave vector
+        const float* bt = sizeof(T) == 4 ? g.btab : nullptr;
+        const int hy = g.ny / 2 + 1, hz = g.nz / 2 + 1;
+        const long long tn = (long long)hz * hy * g.nxh;
+        const long long trow = (long long)(ky <= g.ny / 2 ? ky : g.ny - ky) * g.nxh + kx0 + (col < ncol ? col : 0);
 #pragma unroll
         for (int t = 0; t < RL; ++t) {
             T Bm[3][3];
-            elastic_kernel<T>(pt, kxv, kyv, kval<T>(g, 2, j + t * M), Bm);
+            T sc = invN;
+            if (bt) {
+                const int kz = j + t * M;
+                const long long ti = (long long)(kz <= g.nz / 2 ? kz : g.nz - kz) * hy * g.nxh + trow;
+                Bm[0][0] = (T)__ldg(bt + ti);
+                Bm[0][1] = Bm[1][0] = (T)__ldg(bt + tn + ti);
+                Bm[0][2] = Bm[2][0] = (T)__ldg(bt + 2 * tn + ti);
+                Bm[1][1] = (T)__ldg(bt + 3 * tn + ti);
+                Bm[1][2] = Bm[2][1] = (T)__ldg(bt + 4 * tn + ti);
+                Bm[2][2] = (T)__ldg(bt + 5 * tn + ti);
+                sc = (T)1;
+            } else {
+                elastic_kernel<T>(pt, kxv, kyv, kval<T>(g, 2, j + t * M), Bm);
+            }
             const T2 a = h[0][t], b = h[1][t], c = h[2][t];
 #pragma unroll
             for (int v = 0; v < 3; ++v)
-                h[v][t] = T2{(Bm[v][0] * a.x + Bm[v][1] * b.x + Bm[v][2] * c.x) * invN,
-                             (Bm[v][0] * a.y + Bm[v][1] * b.y + Bm[v][2] * c.y) * invN};
+                h[v][t] = T2{(Bm[v][0] * a.x + Bm[v][1] * b.x + Bm[v][2] * c.x) * sc,
+                             (Bm[v][0] * a.y + Bm[v][1] * b.y + Bm[v][2] * c.y) * sc};
         }
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
