@@ -120,3 +120,18 @@ def test_fp32bulk_error_estimate_tracks_fp64(pfg, params):
                 assert ok == (e64 <= 1.0)
             n += 1
         torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("meth,nrhs", [("euler", 1), ("ark2", 3), ("ark3", 4), ("ark4", 6)])
+def test_rhs_evaluations_per_step_match_paper(pfg, params, meth, nrhs):
+    """Sec. 2.3 prints 1, 3, 4 and 6 explicit RHS evaluations per step for the
+    first- through fourth-order methods (tests/golden/rhs_per_step.txt): the
+    library's counter over three fixed steps, both precisions."""
+    y0 = synth.ic_spheres(16, 2, 2.0, 3.0, 4, params)
+    for prec in ("fp64", "fp32bulk"):
+        with pfg.Simulation((16, 16, 16), params, meth, prec) as s:
+            s.set_state(y0)
+            r0 = s.stats()["rhs_evals"]
+            for _ in range(3):
+                s.step(0.25)
+            assert s.stats()["rhs_evals"] - r0 == 3 * nrhs
