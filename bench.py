@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--ensemble-t", type=float, default=60.0, help="simulated seconds of the ensemble measurement")
     ap.add_argument("--surrogate", type=int, default=24, help="training trajectories of the surrogate measurement (0: skip)")
     ap.add_argument("--sweep", action="store_true", help="add the work-precision sweep of the two-particle test")
+    ap.add_argument("--hc", type=int, default=128, help="side of the phase-dependent-stiffness leg (0: skip)")
     return ap.parse_args()
 
 
@@ -292,7 +293,7 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": r32["gpt_stage_s"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": r32["ms_per_integration"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 transforms/RHS, f64 state/norms", "data": "synthetic",
-        "config": {"workload": WORKLOAD2 if n == 256 else WORKLOAD2.replace("256^3", "%d^3" % n),
+        "config": {"workload": WORKLOAD2.replace("256^3", "%d^3" % n).replace("t_final=60 s", "t_final=%g s" % T),
                    "grid": [n, n, n], "fields": 4, "method": "ARK4(3)6L[2]SA", "precision": "fp32bulk",
                    "rtol": 1e-4, "atol": 1e-8, "t_final": T, "step": "one integration from t=0 to t_final",
                    "l2": "inputs larger than L2 (FP64 k-space state %.0f MiB; no flush needed)" % (
@@ -380,6 +381,61 @@ def run_big(n, t_final, rank=0, world=1):
         sim.close()
         torch.cuda.synchronize()
     res["gain_fp32bulk_vs_fp64_gpt_stage_s"] = res["fp32bulk"]["gpt_stage_s"] / res["fp64"]["gpt_stage_s"]
+    return res
+
+
+def run_hc(n=128, t_final=20.0):
+    """Phase-dependent stiffness (Hu-Chen iterations, FP64) on an n^3 state of
+    the 256^3 recipe scaled down (32 n^3/256^3 nuclei, at least 4), with a
+    precipitate stiffer than the matrix (C11, C12, C44 up 30, 10, 20 %):
+    ARK4 adaptive at rtol 1e-4 from t = 0 (h0 = 1 s) to t_final with the
+    loose elastic tolerance of Sec. 2.3 (1e-6) and a tight one (1e-12), and
+    the homogeneous modulus on the same state for the cost of the iterations.
+    Returns wall time, RHS evaluations and elastic solves per RHS evaluation
+    (each attempt's RHS evaluations counted at the solve count of its last
+    one, which the library reports)."""
+    import torch
+
+    import paper_2609_36100_gb300 as pfg
+    import synth
+
+    p = synth.load_params()
+    y0 = synth.ic_spheres(n, max(4, 32 * n ** 3 // 256 ** 3), 4.0, 10.0, 2, p)
+    y0d = torch.from_numpy(y0).to("cuda")
+    base = dict(p, C11_v=1.3 * p["C11"], C12_v=1.1 * p["C12"], C44_v=1.2 * p["C44"], el_max_iter=200)
+    res = {"grid": [n, n, n], "t_final": t_final, "contrast": "C11 +30 %, C12 +10 %, C44 +20 % in the precipitate",
+           "runs": []}
+    for prec in ("fp32bulk", "fp64"):
+        for label, extra in (("homogeneous", {"el_inhom": 0}), ("loose 1e-6", {"el_inhom": 1, "el_tol": 1e-6}),
+                             ("tight 1e-12", {"el_inhom": 1, "el_tol": 1e-12})):
+            q = dict(base, **extra)
+            with pfg.Simulation((n, n, n), q, "ark4", prec) as sim:
+                sim.set_state(y0d)
+                sim.set_time(0.0, 1.0)
+                sim.advance_attempts(1)  # warm-up
+                sim.set_state(y0d)
+                sim.set_time(0.0, 1.0)
+                torch.cuda.synchronize()
+                st0 = sim.stats()
+                w0 = time.perf_counter()
+                solves = 0
+                rhs = 0
+                # attempt by attempt, to count the elastic solves of every RHS
+                while sim.time()[0] < t_final - 1e-9:
+                    r0 = sim.stats()["rhs_evals"]
+                    sim.advance_attempts(1, t_final, 1e-4, 1e-8)
+                    d = sim.stats()["rhs_evals"] - r0
+                    rhs += d
+                    solves += d * sim.elastic_iterations()
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - w0
+                st1 = sim.stats()
+                res["runs"].append({"precision": prec, "elastic": label, "wall_s": wall,
+                                    "attempts": int(st1["steps_accepted"] + st1["steps_rejected"]
+                                                    - st0["steps_accepted"] - st0["steps_rejected"]),
+                                    "rhs_evals": rhs, "elastic_solves_per_rhs": solves / max(rhs, 1),
+                                    "ms_per_rhs": wall * 1e3 / max(rhs, 1),
+                                    "sim_s_per_wall_s": t_final / wall})
     return res
 
 
@@ -603,7 +659,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD2 if n == 256 else WORKLOAD2.replace("256^3", "%d^3" % n),
+            "config": {"workload": WORKLOAD2.replace("256^3", "%d^3" % n).replace("t_final=60 s", "t_final=%g s" % args.t_final),
                        "grid": [n, n, n], "implementation": "FP64 CPU oracle (numpy/scipy) on the host cores",
                        "step": "one explicit RHS evaluation (one ARK4 stage) of the initial state"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": om._WORKERS, "kind": "oracle", "sample": sample},
@@ -632,6 +688,8 @@ def main():
         line["ensemble"] = run_ensemble(args.ensemble, args.ensemble_t, rank, world)
     if args.sweep and rank == 0:
         line["work_precision"] = run_sweep()
+    if args.hc > 0 and rank == 0:
+        line["hu_chen"] = run_hc(args.hc)
     if args.surrogate > 0 and rank == 0:
         line["surrogate"] = run_surrogate(args.surrogate)
     if rank == 0:
