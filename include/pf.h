@@ -244,7 +244,9 @@ const char* pf_kernel_name(int kind);
  * built-in heuristic), the radix order of each axis (count + up to 10 radices
  * in {2,3,4,5,8,16}, for x, y, z: ints 4-36), the tile width of the forward
  * z pass (int 37), the compiled radix plan of the elastic pass (int 38;
- * 0 = the z axis's own plan) and whether the FP32 x passes run the staged
+ * 0 = the z axis's own plan, -1 = no fused stage: the forward transforms,
+ * the contraction and the inverse transforms as separate steps of one
+ * kernel) and whether the FP32 x passes run the staged
  * kernel instead of the fused one (int 39).  PF_TUNE_LEN ints. */
 #define PF_TUNE_LEN 40
 int pf_get_tuning(pf_ctx* ctx, int* cfg, int n);

@@ -1598,7 +1598,8 @@ int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
     g.tx_el = cfg[2];
     g.rp = cfg[3];
     g.tx_zf = cfg[37];
-    if (cfg[38] != 0 && compiled_plan_len(cfg[38]) != g.nz)
+    if (cfg[38] < -1) return fail(c, PF_EINVAL, "pf_set_tuning: bad elastic plan %d", cfg[38]);
+    if (cfg[38] > 0 && compiled_plan_len(cfg[38]) != g.nz)
         return fail(c, PF_EINVAL, "pf_set_tuning: elastic plan %d does not have length nz", cfg[38]);
     g.el_pid = cfg[38];
     g.xf_off = cfg[39] != 0;
@@ -1718,8 +1719,8 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
             cfg[39] = v;
             trial(cfg);
         }
-        // compiled plans of length nz for the fused elastic pass
-        for (int pid = 0; pid <= compiled_plan_count(); ++pid) {
+        // compiled plans of length nz for the fused elastic pass, or none (-1)
+        for (int pid = -1; pid <= compiled_plan_count(); ++pid) {
             if (pid > 0 && compiled_plan_len(pid) != c->g.nz) continue;
             std::memcpy(cfg, best, sizeof cfg);
             cfg[38] = pid;

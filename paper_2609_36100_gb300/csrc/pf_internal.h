@@ -55,7 +55,8 @@ struct Geo {
     int tx_y, tx_z, tx_el;  // tuned tile widths (kx columns) of the strided passes, 0 = heuristic
     int rp;                  // tuned row pairs per CTA in the x passes, 0 = heuristic
     int tx_zf;               // tuned tile width of the forward z pass, 0 = heuristic
-    int el_pid;              // compiled plan of the fused elastic pass (length nz), 0 = the z-axis plan
+    int el_pid;              // compiled plan of the fused elastic pass (length nz), 0 = the z-axis plan,
+                             // -1 = no fused stage (the one-kernel pass with the z-axis column transforms)
     int xf_off;              // 1: the FP32 x passes use the staged kernel instead of the fused one
     const float* btab;       // FP32 elastic kernel B(k) / N over kx >= 0, |ky| <= ny/2, |kz| <= nz/2 (six
                              // symmetric entries, [6][nz/2+1][ny/2+1][nx/2+1]), or null: computed per k

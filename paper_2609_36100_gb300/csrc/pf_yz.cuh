@@ -400,7 +400,9 @@ template <typename T>
 void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
     bool done = false;
-    if (g.pz.n == g.nz && g.nz >= 32) {
+    // el_pid < 0: the one-kernel pass with the column transforms of the z
+    // axis (no fused stage), also where a compiled plan exists
+    if (g.el_pid >= 0 && g.pz.n == g.nz && g.nz >= 32) {
         const int pid = (g.el_pid > 0 && fixed_plan_len(g.el_pid) == g.nz) ? g.el_pid : fixed_plan_id(g.pz);
         switch (pid) {
             case 1: done = launch_z_elastic_fused<T, 1>(g, ph, H, g.tx_el, s); break;

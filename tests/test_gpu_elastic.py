@@ -52,6 +52,27 @@ def test_fused_elastic_plan_matches_oracle(pfg, params, pid, prec, tol):
             assert np.all(err <= tol), (tx, err)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32bulk", 2e-5)])
+def test_generic_elastic_pass_selectable(pfg, params, prec, tol):
+    """Plan value -1 selects the elastic pass without a fused stage (forward
+    transforms, contraction, inverse transforms as separate steps of one
+    kernel), also where a compiled plan exists."""
+    import torch
+    shape = (256, 12, 30)
+    y = synth.random_state(shape, 91)
+    m = oracle.Model(shape, params)
+    yh = m.to_k(y)
+    ref = m.rhs_explicit(yh)
+    dev = torch.from_numpy(yh).to("cuda")
+    with pfg.Simulation(shape, params, "ark4", prec) as s:
+        cfg = s.tuning()
+        cfg[38] = -1
+        s.set_tuning(cfg)
+        assert s.tuning()[38] == -1
+        got = s.rhs_explicit(dev).cpu().numpy()
+        assert np.all(relerr(got, ref) <= tol)
+
+
 def test_elastic_plan_of_wrong_length_refused(pfg, params):
     with pfg.Simulation((64, 8, 8), params, "ark4", "fp64") as s:
         cfg = s.tuning()

@@ -57,3 +57,37 @@ def test_bench_workload_first_step(pfg, params, ref, prec, tol, etol):
         assert got[0, 0, 0, 0] == dc  # the composition mean stays FP64-exact
     else:
         assert e == pytest.approx(e_ref, rel=etol)
+
+
+def test_bench_workload_to_end_time(pfg, params):
+    """The whole bench integration (t = 0 to 60 s, ARK4 adaptive at rtol 1e-4,
+    atol 1e-8, h0 = 1 s) in both forms at full size.  The oracle cannot follow
+    150 RHS evaluations of a 256^3 grid, so the end state is checked through
+    properties that hold at any size and against the FP64 GPU path (itself
+    pinned to the oracle step by step above and at smaller sizes): the
+    composition mean is the initial one bitwise in both forms; the free energy
+    has decreased; the two forms take the same accept/reject sequence within
+    one attempt and end within 2e-5 rel L2 per field of each other (the
+    tolerance-driven error of either form is ~2e-5 against a tight run)."""
+    y0 = synth.ic_spheres(N, 32, 4.0, 10.0, 2, params)
+    out = {}
+    for prec in ("fp64", "fp32bulk"):
+        with pfg.Simulation(y0.shape[1:], params, "ark4", prec) as s:
+            s.set_state(y0)
+            if prec == "fp32bulk":
+                s.autotune(reps=2)
+                s.set_state(y0)
+            dc = s.state_hat()[0, 0, 0, 0].item()
+            f0 = s.free_energy()
+            s.set_time(0.0, 1.0)
+            st = s.advance(60.0, 1e-4, 1e-8)
+            assert s.time()[0] == pytest.approx(60.0, abs=1e-9)
+            got_hat = s.state_hat()
+            assert got_hat[0, 0, 0, 0].item() == dc
+            assert s.free_energy() < f0
+            out[prec] = (s.get_state(), st["steps_accepted"], st["steps_rejected"])
+    (a, acc_a, rej_a), (b, acc_b, rej_b) = out["fp32bulk"], out["fp64"]
+    assert abs(acc_a - acc_b) <= 2 and abs(rej_a - rej_b) <= 2
+    err = relerr(a, b)
+    print("FP32-bulk vs FP64 at t = 60 s, rel L2 per field:", err)
+    assert np.all(err <= 2e-5), err
