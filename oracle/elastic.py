@@ -32,6 +32,16 @@ follows from <C (eps_bar + eps(u) - eps0)> = 0.  The loop stops when the
 largest change of eps(u) between iterations is <= el_tol times the largest
 |eps0| (or after el_max_iter iterations).
 
+Warm start (el_warm, the default): a solve starts from the strain field
+eps(u) of the previous solve of the same trajectory instead of the cold
+tau = C0 eps0, so its first iteration already measures a change; when the
+fields moved little since that solve, one iteration meets the tolerance.
+This is the reading of Sec. 2.3's remark that with the loose tolerance the
+solver exits after one iteration for nearly all steps (a cold start needs
+several iterations for any contrast, since the first one measures no
+change).  The carried field is part of the trajectory, not of the state: a
+solve without it starts cold.
+
 Tensors are handled as full 3x3x3x3 arrays and 3x3 matrices with einsum
 and numpy.linalg (Mandel 6x6 form only to invert fourth-order tensors).
 """
@@ -153,16 +163,16 @@ class HuChen:
                 out[i, j] = m.to_r(ek[i, j][None])[0]
         return out
 
-    def solve(self, h):
+    def solve(self, h, eps_u0=None):
         """Returns (e [3, ...] driving-force terms, sigma [3,3,...], eps_el
-        [3,3,...], eps_bar [3,3], iterations)."""
+        [3,3,...], eps_bar [3,3], iterations); the final eps(u) is kept in
+        self.last_eps_u.  eps_u0: the eps(u) to start from (warm start), or
+        None for the cold start."""
         C = self.stiffness(h)  # [..., 3,3,3,3]
         e0 = np.einsum("v...,vij->ij...", h, self.eps)  # eps0 [3,3,...]
         Cp = C - self.C0
         Cavg = C.reshape(-1, 3, 3, 3, 3).mean(axis=0)
         C0e0 = np.einsum("ijkl,kl...->ij...", self.C0, e0)
-        eps_u = self.green(C0e0)
-        it = 1
         scale = max(np.max(np.abs(e0)), 1e-300)
 
         def mean_strain(eu):
@@ -170,6 +180,12 @@ class HuChen:
             Sinv = invert4(Cavg)
             return np.einsum("ijkl,kl->ij", Sinv, rhs)
 
+        if eps_u0 is None:
+            eps_u = self.green(C0e0)
+            it = 1
+        else:
+            eps_u = eps_u0
+            it = 0
         ebar = mean_strain(eps_u)
         while it < self.max_iter:
             tot = ebar[:, :, None, None, None] + eps_u - e0
@@ -181,6 +197,7 @@ class HuChen:
             it += 1
             if change <= self.tol * scale:
                 break
+        self.last_eps_u = eps_u
         el = ebar[:, :, None, None, None] + eps_u - e0
         sig = np.einsum("...ijkl,kl...->ij...", C, el)
         e = np.empty((3,) + h.shape[1:])

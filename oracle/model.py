@@ -128,6 +128,8 @@ class Model:
         if self.inhom:
             from .elastic import HuChen
             self.hc = HuChen(self, p)
+            self.hc_warm = bool(p.get("el_warm", 1))
+            self.hc_prev = None  # eps(u) of the last solve (warm start)
 
     # --- transforms -------------------------------------------------------
     def to_k(self, real: np.ndarray) -> np.ndarray:
@@ -171,10 +173,20 @@ class Model:
         if not self.elastic_on:
             return np.zeros_like(h)
         if self.inhom:
-            return self.hc.solve(h)[0]
+            return self.hc_solve(h)[0]
         hk = self.to_k(h)
         ek = np.einsum("vq...,q...->v...", self.B, hk)
         return self.to_r(ek)
+
+    def hc_solve(self, h):
+        """Hu-Chen solve at interpolated fields h, started from the previous
+        solve's eps(u) when the warm start is on (every solve of the model,
+        right-hand side or free energy, continues the same sequence)."""
+        out = self.hc.solve(h, self.hc_prev if self.hc_warm else None)
+        if self.hc_warm:
+            self.hc_prev = self.hc.last_eps_u
+        self.hc_last_iters = out[4]
+        return out
 
     # --- right-hand sides -------------------------------------------------
     def rhs_explicit(self, yhat: np.ndarray) -> np.ndarray:
@@ -223,7 +235,7 @@ class Model:
         for v in range(3):
             F += 0.5 * V * np.sum(w * self.kk[v] * np.abs(yhat[1 + v]) ** 2)
         if self.inhom:
-            _, sig, el, _, _ = self.hc.solve(h)
+            _, sig, el, _, _ = self.hc_solve(h)
             F += 0.5 * float(np.sum(sig * el)) * self.dV
         elif self.elastic_on:
             hk = self.to_k(h)

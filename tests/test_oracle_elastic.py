@@ -129,3 +129,69 @@ def test_inhomogeneous_rhs_is_variational_derivative(params):
             d2 = F_at(1 + v, idx, 2 * eps) - F_at(1 + v, idx, -2 * eps)
             dF = (8 * d1 - d2) / (12 * eps * dV)
             assert tot[1 + v][idx] == pytest.approx(-p["L"] * dF, rel=1e-5, abs=1e-9)
+
+
+def _contrast(params, tol, it=200):
+    return dict(params, el_inhom=1, C11_v=1.3 * params["C11"], C12_v=1.1 * params["C12"], C44_v=1.2 * params["C44"],
+                el_tol=tol, el_max_iter=it)
+
+
+def test_warm_start_from_the_solution_stops_after_one_iteration(params):
+    """Started from the converged eps(u) of the same fields, one iteration
+    reproduces it (the fixed point of the iteration is the equilibrium), so
+    the warm-started solve stops after one solve with the same force."""
+    shape = (10, 12, 14)
+    p = _contrast(params, 1e-12)
+    y = synth.random_state(shape, 21)
+    y[1:] *= 0.4
+    h = oracle.h_interp(y[1:])
+    hc = HuChen(oracle.Model(shape, p), p)
+    e_cold, _, _, _, it_cold = hc.solve(h)
+    e_warm, _, _, _, it_warm = hc.solve(h, hc.last_eps_u)
+    assert it_cold > 5 and it_warm == 1
+    assert np.max(np.abs(e_warm - e_cold)) <= 1e-9 * np.max(np.abs(e_cold))
+
+
+def test_warm_start_after_a_small_change_meets_the_same_tolerance(params):
+    """Fields moved a little since the previous solve (as between the stages
+    of a step): the warm-started solve takes fewer iterations than the cold
+    one at the loose tolerance, and both forces lie within the tolerance's
+    reach of the converged one."""
+    shape = (10, 12, 14)
+    y0 = synth.random_state(shape, 22)
+    y0[1:] *= 0.4
+    rng = np.random.default_rng(3)
+    y1 = y0.copy()
+    y1[1:] += 1e-3 * rng.standard_normal(y0[1:].shape)
+    h0, h1 = oracle.h_interp(y0[1:]), oracle.h_interp(y1[1:])
+    tight = HuChen(oracle.Model(shape, _contrast(params, 1e-13)), _contrast(params, 1e-13))
+    e_ref = tight.solve(h1)[0]
+    p = _contrast(params, 1e-6)
+    hc = HuChen(oracle.Model(shape, p), p)
+    hc.solve(h0)
+    prev = hc.last_eps_u
+    e_warm, _, _, _, it_warm = hc.solve(h1, prev)
+    e_cold, _, _, _, it_cold = hc.solve(h1)
+    assert it_warm < it_cold
+    scale = np.max(np.abs(e_ref))
+    assert np.max(np.abs(e_warm - e_ref)) <= 1e-4 * scale
+    assert np.max(np.abs(e_cold - e_ref)) <= 1e-4 * scale
+
+
+def test_model_carries_the_warm_start_between_evaluations(params):
+    """The model's solves continue one sequence (right-hand sides and free
+    energy alike); el_warm = 0 restores independent cold solves."""
+    shape = (8, 8, 8)
+    y = synth.random_state(shape, 23)
+    y[1:] *= 0.4
+    p = _contrast(params, 1e-6)
+    m = oracle.Model(shape, p)
+    yh = m.to_k(y)
+    m.rhs_explicit(yh)
+    assert m.hc_prev is not None
+    first = m.hc_prev
+    m.rhs_explicit(yh)
+    assert m.hc_prev is not first
+    mc = oracle.Model(shape, dict(p, el_warm=0))
+    mc.rhs_explicit(yh)
+    assert mc.hc_prev is None
