@@ -97,11 +97,16 @@ typedef struct {
        reference medium (C^m + C^v)/2 with a stress-free mean strain; stop
        when max |eps(u)_n - eps(u)_{n-1}| <= el_tol max |eps0| or after
        el_max_iter solves.  el_inhom = 0: homogeneous modulus (closed-form
-       Green kernel, one solve). */
+       Green kernel, one solve).  el_warm = 1: each solve starts from the
+       eps(u) of the context's previous solve (warm start; one iteration
+       suffices when the fields moved little), which pf_set_state and
+       pf_set_state_hat discard; 0: every solve starts cold from
+       tau = C0:eps0. */
     int el_inhom;
     double C11_v, C12_v, C44_v;
     double el_tol;
     int el_max_iter;
+    int el_warm;
 } pf_params;
 
 typedef struct {
@@ -244,11 +249,13 @@ const char* pf_kernel_name(int kind);
  * built-in heuristic), the radix order of each axis (count + up to 10 radices
  * in {2,3,4,5,8,16}, for x, y, z: ints 4-36), the tile width of the forward
  * z pass (int 37), the compiled radix plan of the elastic pass (int 38;
- * 0 = the z axis's own plan, -1 = no fused stage: the forward transforms,
- * the contraction and the inverse transforms as separate steps of one
- * kernel) and whether the FP32 x passes run the staged
- * kernel instead of the fused one (int 39).  PF_TUNE_LEN ints. */
-#define PF_TUNE_LEN 40
+ * 0 = the z axis's own plan, -1 = no compiled elastic plan: the z axis's
+ * column transforms, one field after another), whether the FP32 x passes run the staged kernel instead of the
+ * fused one (int 39) and whether the compiled-plan elastic pass runs each
+ * transform stage and the contraction over the three fields in place instead
+ * of fusing the last forward and first inverse stage in registers (int 40).
+ * PF_TUNE_LEN ints. */
+#define PF_TUNE_LEN 41
 int pf_get_tuning(pf_ctx* ctx, int* cfg, int n);
 int pf_set_tuning(pf_ctx* ctx, const int* cfg, int n);
 /* Autotuner: times `reps` step attempts per candidate schedule on the

@@ -230,6 +230,8 @@ struct pf_ctx {
     double* hc_ebar = nullptr;     // eps_bar on the device [6]
     double* hc_host = nullptr;     // pinned: statistics [blocks][11] and eps_bar [6]
     int hc_iters = 0;              // iterations of the last solve
+    int hc_cur = 0;                // which of hc_eu holds the last solve's eps(u)
+    bool hc_prev = false;          // hc_eu[hc_cur] can start the next solve (warm start)
     double* d_scalar = nullptr;
     double* h_scalar = nullptr;  // pinned
     // integrator state
@@ -449,8 +451,10 @@ struct ProfScope {
 
 // Hu-Chen solve of the phase-dependent elasticity for the real fields R
 // ([4][N] of type TR: X, phi_1..3) on the context's stream: iteration 0 with
-// tau = C0:eps0, then tau from the previous iterate until the change of
-// eps(u) is <= el_tol max |eps0| or el_max_iter solves; writes the driving
+// tau = C0:eps0 (cold start) or, with el_warm and a previous solve since the
+// state was last set, no iteration 0 (the previous eps(u) takes its place),
+// then tau from the previous iterate until the change of eps(u) is
+// <= el_tol max |eps0| or el_max_iter solves; writes the driving
 // forces e_v into E ([3][N] of type TR, if not null) and the elastic energy
 // sum_r sigma:eps_el/2 (without the volume element) into *energy (if not
 // null).  Each transform is the FP64 four-field pipeline of set/get state.
@@ -506,12 +510,21 @@ int hc_solve(pf_ctx* c, const void* R, void* E, double* energy) {
         scale = sum[10];
         return PF_OK;
     };
-    int cur = 0;
-    launch_hc_tau<TR>(g, k, R, nullptr, nullptr, c->hc_tau, s);
-    green(c->hc_eu[cur]);
+    int cur = c->hc_cur;
     double change = 0.0, scale = 0.0;
-    if (int rc = stats(c->hc_eu[cur], nullptr, change, scale)) return rc;
-    int it = 1;
+    int it;
+    const bool warm = c->prm.el_warm && c->hc_prev;
+    c->hc_prev = false;  // set again once this solve has completed
+    if (warm) {
+        // warm start: eps_bar for the carried eps(u) under the current C(r)
+        if (int rc = stats(c->hc_eu[cur], nullptr, change, scale)) return rc;
+        it = 0;
+    } else {
+        launch_hc_tau<TR>(g, k, R, nullptr, nullptr, c->hc_tau, s);
+        green(c->hc_eu[cur]);
+        if (int rc = stats(c->hc_eu[cur], nullptr, change, scale)) return rc;
+        it = 1;
+    }
     const double tol = c->prm.el_tol * (scale > 0.0 ? scale : 1e-300);
     while (it < c->prm.el_max_iter) {
         const int prev = cur;
@@ -523,6 +536,8 @@ int hc_solve(pf_ctx* c, const void* R, void* E, double* energy) {
         if (!(change > tol)) break;  // also stops on a non-finite change
     }
     c->hc_iters = it;
+    c->hc_cur = cur;
+    c->hc_prev = c->prm.el_warm != 0;
     if (E) launch_hc_force<TR>(g, k, R, c->hc_eu[cur], c->hc_ebar, E, s);
     if (energy) {
         launch_hc_energy<TR>(g, k, R, c->hc_eu[cur], c->hc_ebar, c->hc_part, s);
@@ -845,7 +860,7 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     c->inhom = params->el_inhom != 0 && c->ph.elastic;
     if (c->inhom) {
         if (!(params->C11_v > params->C12_v) || !(params->C11_v + 2 * params->C12_v > 0) || !(params->C44_v > 0) ||
-            !(params->el_tol >= 0) || params->el_max_iter < 1) {
+            !(params->el_tol >= 0) || params->el_max_iter < 1 || (params->el_warm != 0 && params->el_warm != 1)) {
             delete c;
             return fail(nullptr, PF_EINVAL, "invalid precipitate stiffness or elastic-solver settings");
         }
@@ -1059,6 +1074,7 @@ int pf_set_state(pf_ctx* c, const double* fields, int on_device) {
     int rc = check_launch(c, "pf_set_state");
     if (rc) return rc;
     PF_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->hc_prev = false;  // a new trajectory: the next Hu-Chen solve starts cold
     return PF_OK;
 }
 
@@ -1091,6 +1107,7 @@ int pf_set_state_hat(pf_ctx* c, const void* y_hat, int on_device) {
     if (int rc = check_finite(c, reinterpret_cast<const double*>(c->ynew), 8 * c->g.NK, "pf_set_state_hat"))
         return rc;
     std::swap(c->y, c->ynew);
+    c->hc_prev = false;  // a new trajectory: the next Hu-Chen solve starts cold
     return PF_OK;
 }
 
@@ -1584,6 +1601,7 @@ int pf_get_tuning(pf_ctx* c, int* cfg, int n) {
     cfg[37] = c->g.tx_zf;
     cfg[38] = c->g.el_pid;
     cfg[39] = c->g.xf_off;
+    cfg[40] = c->g.el_unfused;
     plan_to_cfg(c->g.px, cfg + 4);
     plan_to_cfg(c->g.py, cfg + 4 + 11);
     plan_to_cfg(c->g.pz, cfg + 4 + 22);
@@ -1603,6 +1621,7 @@ int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
         return fail(c, PF_EINVAL, "pf_set_tuning: elastic plan %d does not have length nz", cfg[38]);
     g.el_pid = cfg[38];
     g.xf_off = cfg[39] != 0;
+    g.el_unfused = cfg[40] != 0;
     AxisPlan* pl[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
@@ -1719,6 +1738,13 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
             cfg[39] = v;
             trial(cfg);
         }
+        // elastic pass with the fused stage or with every stage over the three fields
+        if (c->ph.elastic && !c->inhom)
+            for (int v : {0, 1}) {
+                std::memcpy(cfg, best, sizeof cfg);
+                cfg[40] = v;
+                trial(cfg);
+            }
         // compiled plans of length nz for the fused elastic pass, or none (-1)
         for (int pid = -1; pid <= compiled_plan_count(); ++pid) {
             if (pid > 0 && compiled_plan_len(pid) != c->g.nz) continue;

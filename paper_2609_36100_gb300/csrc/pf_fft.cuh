@@ -651,6 +651,18 @@ struct RadInfo<Radices<>> {
     static constexpr int last = 1;
 };
 
+// largest radix of a list
+template <class R>
+struct RadMax;
+template <>
+struct RadMax<Radices<>> {
+    static constexpr int value = 1;
+};
+template <int R, int... Rs>
+struct RadMax<Radices<R, Rs...>> {
+    static constexpr int value = R > RadMax<Radices<Rs...>>::value ? R : RadMax<Radices<Rs...>>::value;
+};
+
 // the radix order reversed: the inverse transform of a tile whose forward
 // transform ended with radix R starts with radix R, so that the last forward
 // stage and the first inverse stage see the same element positions

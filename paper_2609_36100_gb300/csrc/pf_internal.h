@@ -58,6 +58,8 @@ struct Geo {
     int el_pid;              // compiled plan of the fused elastic pass (length nz), 0 = the z-axis plan,
                              // -1 = no fused stage (the one-kernel pass with the z-axis column transforms)
     int xf_off;              // 1: the FP32 x passes use the staged kernel instead of the fused one
+    int el_unfused;          // 1: the compiled-plan elastic pass runs every stage (and the contraction) over the
+                             // three fields in place instead of fusing the last forward / first inverse stage
     const float* btab;       // FP32 elastic kernel B(k) / N over kx >= 0, |ky| <= ny/2, |kz| <= nz/2 (six
                              // symmetric entries, [6][nz/2+1][ny/2+1][nx/2+1]), or null: computed per k
 };
@@ -198,6 +200,8 @@ int launch_x_pass(const Geo& g, const Phys& ph, int mode, const void* in, void* 
                   cudaStream_t s);
 template <typename T>
 void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s);
+template <typename T>
+bool launch_z_elastic_unfused(const Geo& g, const Phys& ph, void* H, int pid, cudaStream_t s);
 // forward z FFT; scale_mode 0: y = W/N to FP64 (set_state); 1: f^E scaling
 // into the compute type; 2: f^E scaling into FP64 (ABI output)
 template <typename T>

@@ -181,18 +181,35 @@ __global__ void __launch_bounds__(kThreads) k_z_elastic(Geo g, Phys ph, typename
     const T invN = std::is_same<T, float>::value ? (T)g.invN32 : (T)g.invN;
     const PhysT<T>& pt = phys_t<T>(ph);
     const T kyv = kval<T>(g, 1, ky);
+    // FP32 contexts with diagonal eigenstrains read B/N from the octant table
+    const float* bt = sizeof(T) == 4 ? g.btab : nullptr;
+    const int hy = g.ny / 2 + 1;
+    const long long tn = (long long)(g.nz / 2 + 1) * hy * g.nxh;
+    const long long trow = (long long)(ky <= g.ny / 2 ? ky : g.ny - ky) * g.nxh + kx0;
     for (int r = threadIdx.x; r < tile; r += blockDim.x) {
         const int col = r & (TX - 1), kz = r / TX;
         if (col >= ncol) continue;
         T Bm[3][3];
-        elastic_kernel<T>(pt, kval<T>(g, 0, kx0 + col), kyv, kval<T>(g, 2, kz), Bm);
+        T sc = invN;
+        if (bt) {
+            const long long ti = (long long)(kz <= g.nz / 2 ? kz : g.nz - kz) * hy * g.nxh + trow + col;
+            Bm[0][0] = (T)__ldg(bt + ti);
+            Bm[0][1] = Bm[1][0] = (T)__ldg(bt + tn + ti);
+            Bm[0][2] = Bm[2][0] = (T)__ldg(bt + 2 * tn + ti);
+            Bm[1][1] = (T)__ldg(bt + 3 * tn + ti);
+            Bm[1][2] = Bm[2][1] = (T)__ldg(bt + 4 * tn + ti);
+            Bm[2][2] = (T)__ldg(bt + 5 * tn + ti);
+            sc = (T)1;
+        } else {
+            elastic_kernel<T>(pt, kval<T>(g, 0, kx0 + col), kyv, kval<T>(g, 2, kz), Bm);
+        }
         const T2 h0 = slot[0][r], h1 = slot[1][r], h2 = slot[2][r];
-        slot[0][r] = T2{(Bm[0][0] * h0.x + Bm[0][1] * h1.x + Bm[0][2] * h2.x) * invN,
-                        (Bm[0][0] * h0.y + Bm[0][1] * h1.y + Bm[0][2] * h2.y) * invN};
-        slot[1][r] = T2{(Bm[1][0] * h0.x + Bm[1][1] * h1.x + Bm[1][2] * h2.x) * invN,
-                        (Bm[1][0] * h0.y + Bm[1][1] * h1.y + Bm[1][2] * h2.y) * invN};
-        slot[2][r] = T2{(Bm[2][0] * h0.x + Bm[2][1] * h1.x + Bm[2][2] * h2.x) * invN,
-                        (Bm[2][0] * h0.y + Bm[2][1] * h1.y + Bm[2][2] * h2.y) * invN};
+        slot[0][r] = T2{(Bm[0][0] * h0.x + Bm[0][1] * h1.x + Bm[0][2] * h2.x) * sc,
+                        (Bm[0][0] * h0.y + Bm[0][1] * h1.y + Bm[0][2] * h2.y) * sc};
+        slot[1][r] = T2{(Bm[1][0] * h0.x + Bm[1][1] * h1.x + Bm[1][2] * h2.x) * sc,
+                        (Bm[1][0] * h0.y + Bm[1][1] * h1.y + Bm[1][2] * h2.y) * sc};
+        slot[2][r] = T2{(Bm[2][0] * h0.x + Bm[2][1] * h1.x + Bm[2][2] * h2.x) * sc,
+                        (Bm[2][0] * h0.y + Bm[2][1] * h1.y + Bm[2][2] * h2.y) * sc};
     }
     __syncthreads();
     // inverse transforms: field slot -> global (stage 0 reads the slot and
@@ -355,6 +372,92 @@ __global__ void __launch_bounds__(NT, elastic_min_blocks<T, PID, NT>())
     }
 }
 
+// Elastic pass with a compile-time plan and no fused stage: the three h
+// fields of TX columns share one in-place tile, and every transform stage
+// runs over the three fields at once (one job per butterfly of any field,
+// NT threads: one per butterfly of the plan's largest radix), so a stage is
+// one load phase, one barrier and one store phase for all fields.  Forward
+// transform (the first stage reads global memory), the contraction
+// e^_v = sum_q (B_vq / N) h^_q in place, the inverse transform (the last
+// stage writes global memory).  Fewer registers per thread than the fused
+// stage, which holds three fields' values of its butterfly at once.
+template <typename T, int TX, int PID, int NT>
+__global__ void __launch_bounds__(NT) k_z_elastic_stages(Geo g, Phys ph, typename Cx<T>::t* __restrict__ H) {
+    PF_SKIP_INACTIVE(g);
+    using T2 = typename Cx<T>::t;
+    using Fwd = typename FixedPlan<PID>::Rad;
+    using Inv = Reversed<Fwd>;
+    constexpr int N = FixedPlan<PID>::N;
+    constexpr int RF = RadInfo<Fwd>::first, RL = RadInfo<Fwd>::last;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2* S = reinterpret_cast<T2*>(smraw);  // [3][N][TX]
+    const int ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    const int ncol = min(TX, g.nxh - kx0);
+    const long long rowoff = (long long)ky * g.nxh + kx0;
+    const long long zs = (long long)g.ny * g.nxh;
+    const T2* tw = twiddles<T2>(g.pz);
+    {
+        auto ld = [&](int f, int kz, int col) -> T2 {
+            return col < ncol ? H[(long long)f * g.NK + rowoff + kz * zs + col] : T2{0, 0};
+        };
+        auto st = [&](int f, int kz, int col, T2 v) { S[f * (N * TX) + kz * TX + col] = v; };
+        tile_stage_io<RF, -1, TX, N, 1, 3, NT>(tw, ld, st);
+    }
+    __syncthreads();
+    // the remaining forward stages, the last one included, in place
+    tile_stages_inplace<-1, TX, N, RF, 3, NT>(S, tw, typename DropFirst<Fwd>::type{});
+    {
+        const T invN = std::is_same<T, float>::value ? (T)g.invN32 : (T)g.invN;
+        const PhysT<T>& pt = phys_t<T>(ph);
+        const T kyv = kval<T>(g, 1, ky);
+        const float* bt = sizeof(T) == 4 ? g.btab : nullptr;
+        const int hy = g.ny / 2 + 1;
+        const long long tn = (long long)(g.nz / 2 + 1) * hy * g.nxh;
+        const long long trow = (long long)(ky <= g.ny / 2 ? ky : g.ny - ky) * g.nxh + kx0;
+        for (int e = threadIdx.x; e < N * TX; e += NT) {
+            const int kz = e / TX, col = e - kz * TX;
+            if (col >= ncol) continue;
+            T Bm[3][3];
+            T sc = invN;
+            if (bt) {
+                const long long ti = (long long)(kz <= g.nz / 2 ? kz : g.nz - kz) * hy * g.nxh + trow + col;
+                Bm[0][0] = (T)__ldg(bt + ti);
+                Bm[0][1] = Bm[1][0] = (T)__ldg(bt + tn + ti);
+                Bm[0][2] = Bm[2][0] = (T)__ldg(bt + 2 * tn + ti);
+                Bm[1][1] = (T)__ldg(bt + 3 * tn + ti);
+                Bm[1][2] = Bm[2][1] = (T)__ldg(bt + 4 * tn + ti);
+                Bm[2][2] = (T)__ldg(bt + 5 * tn + ti);
+                sc = (T)1;
+            } else {
+                elastic_kernel<T>(pt, kval<T>(g, 0, kx0 + col), kyv, kval<T>(g, 2, kz), Bm);
+            }
+            const T2 a = S[e], b = S[N * TX + e], c = S[2 * N * TX + e];
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+                S[v * N * TX + e] = T2{(Bm[v][0] * a.x + Bm[v][1] * b.x + Bm[v][2] * c.x) * sc,
+                                       (Bm[v][0] * a.y + Bm[v][1] * b.y + Bm[v][2] * c.y) * sc};
+        }
+    }
+    __syncthreads();
+    // inverse: the reversed radix order (its first stage has NS = 1), in place
+    // up to the last stage, which writes global memory
+    tile_stage_inplace<RL, +1, TX, N, 1, 3, NT>(S, tw);
+    tile_stages_inplace<+1, TX, N, RL, 3, NT>(S, tw, typename PlanInner<Inv>::type{});
+    {
+        auto ld = [&](int f, int kz, int col) -> T2 { return S[f * (N * TX) + kz * TX + col]; };
+        auto st = [&](int f, int kz, int col, T2 v) {
+            if (col < ncol) H[(long long)f * g.NK + rowoff + kz * zs + col] = v;
+        };
+        tile_stage_io<RF, +1, TX, N, N / RF, 3, NT>(tw, ld, st);
+    }
+}
+
+template <int PID, int TX>
+constexpr int elastic_stage_threads() {
+    constexpr int n = 3 * TX * FixedPlan<PID>::N / RadMax<typename FixedPlan<PID>::Rad>::value;
+    return n > 1024 ? 1024 : (n + 31) / 32 * 32;
+}
+
 // compiled plans of two or more stages run the fused elastic pass
 template <int PID>
 constexpr bool fused_elastic_ok() {
@@ -396,6 +499,65 @@ static bool launch_z_elastic_fused(const Geo& g, const Phys& ph, void* H, int tu
     }
 }
 
+#ifdef PF_ELASTIC_ALT_TU
+// the compiled-plan elastic pass with every stage over the three fields (no
+// fused stage): tile width as for the fused form
+template <typename T, int PID>
+static bool launch_z_elastic_unf(const Geo& g, const Phys& ph, void* H, int tuned, cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    if constexpr (!fused_elastic_ok<PID>()) {
+        return false;
+    } else {
+        constexpr int N = FixedPlan<PID>::N;
+        auto fits = [&](int tx) { return 3 * (size_t)tx * N * sizeof(T2) <= 100 * 1024; };
+        int TX = 0;
+        for (int tx : {16, 8, 4, 2})
+            if (fits(tx) && (TX == 0 || (tuned > 0 && tx == tuned))) TX = tx;
+        if (tuned <= 0)
+            for (int tx : {16, 8, 4, 2})
+                if (fits(tx) && tx / 2 < g.nxh) {
+                    TX = tx;
+                    break;
+                }
+        if (TX == 0) return false;
+        const size_t sm = 3 * (size_t)TX * N * sizeof(T2);
+        dim3 grid((g.nxh + TX - 1) / TX, g.ny, 1);
+#define PF_ELU(TXC)                                                                                   \
+    {                                                                                                 \
+        constexpr int NTU = elastic_stage_threads<PID, TXC>();                                        \
+        set_smem(k_z_elastic_stages<T, TXC, PID, NTU>, sm);                                           \
+        k_z_elastic_stages<T, TXC, PID, NTU><<<grid, NTU, sm, s>>>(g, ph, reinterpret_cast<T2*>(H));  \
+    }
+        switch (TX) {
+            case 16: PF_ELU(16); break;
+            case 8: PF_ELU(8); break;
+            case 4: PF_ELU(4); break;
+            default: PF_ELU(2); break;
+        }
+#undef PF_ELU
+        return true;
+    }
+}
+
+template <typename T>
+bool launch_z_elastic_unfused(const Geo& g, const Phys& ph, void* H, int pid, cudaStream_t s) {
+    switch (pid) {
+        case 1: return launch_z_elastic_unf<T, 1>(g, ph, H, g.tx_el, s);
+        case 2: return launch_z_elastic_unf<T, 2>(g, ph, H, g.tx_el, s);
+        case 3: return launch_z_elastic_unf<T, 3>(g, ph, H, g.tx_el, s);
+        case 4: return launch_z_elastic_unf<T, 4>(g, ph, H, g.tx_el, s);
+        case 5: return launch_z_elastic_unf<T, 5>(g, ph, H, g.tx_el, s);
+        case 6: return launch_z_elastic_unf<T, 6>(g, ph, H, g.tx_el, s);
+        case 7: return launch_z_elastic_unf<T, 7>(g, ph, H, g.tx_el, s);
+        case 8: return launch_z_elastic_unf<T, 8>(g, ph, H, g.tx_el, s);
+        case 9: return launch_z_elastic_unf<T, 9>(g, ph, H, g.tx_el, s);
+        case 10: return launch_z_elastic_unf<T, 10>(g, ph, H, g.tx_el, s);
+        case 11: return launch_z_elastic_unf<T, 11>(g, ph, H, g.tx_el, s);
+        default: return false;
+    }
+}
+#endif
+
 template <typename T>
 void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
@@ -404,6 +566,7 @@ void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     // axis (no fused stage), also where a compiled plan exists
     if (g.el_pid >= 0 && g.pz.n == g.nz && g.nz >= 32) {
         const int pid = (g.el_pid > 0 && fixed_plan_len(g.el_pid) == g.nz) ? g.el_pid : fixed_plan_id(g.pz);
+        if (g.el_unfused && launch_z_elastic_unfused<T>(g, ph, H, pid, s)) return;
         switch (pid) {
             case 1: done = launch_z_elastic_fused<T, 1>(g, ph, H, g.tx_el, s); break;
             case 2: done = launch_z_elastic_fused<T, 2>(g, ph, H, g.tx_el, s); break;

@@ -1,8 +1,9 @@
 """The fused elastic pass (last forward z stage, Green's contraction of
 Eq. u_gov and first inverse stage in registers; the inverse runs the forward
-radix order reversed) against the FP64 oracle's explicit right-hand side,
-for every compiled radix plan of each length and every tile width, on grids
-whose half-spectrum rows leave a ragged last tile."""
+radix order reversed) and its form without a fused stage (every stage over
+the three fields in place, tuning slot 40) against the FP64 oracle's explicit
+right-hand side, for every compiled radix plan of each length and every tile
+width, on grids whose half-spectrum rows leave a ragged last tile."""
 import numpy as np
 import pytest
 
@@ -42,14 +43,16 @@ def test_fused_elastic_plan_matches_oracle(pfg, params, pid, prec, tol):
     dev = torch.from_numpy(yh).to("cuda")
     with pfg.Simulation(shape, params, "ark4", prec) as s:
         for tx in (2, 4, 8, 16):
-            cfg = s.tuning()
-            cfg[2] = tx
-            cfg[38] = pid
-            s.set_tuning(cfg)
-            assert s.tuning()[38] == pid
-            got = s.rhs_explicit(dev).cpu().numpy()
-            err = relerr(got, ref)
-            assert np.all(err <= tol), (tx, err)
+            for unfused in (0, 1):
+                cfg = s.tuning()
+                cfg[2] = tx
+                cfg[38] = pid
+                cfg[40] = unfused
+                s.set_tuning(cfg)
+                assert s.tuning()[38] == pid
+                got = s.rhs_explicit(dev).cpu().numpy()
+                err = relerr(got, ref)
+                assert np.all(err <= tol), (tx, unfused, err)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32bulk", 2e-5)])

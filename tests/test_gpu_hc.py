@@ -79,8 +79,8 @@ def test_ark4_step_and_free_energy(pfg, params):
     p = contrast(params)
     y0 = synth.ic_spheres(16, 2, 2.5, 3.5, 7, p)
     m = oracle.Model(y0.shape[1:], p)
+    F0 = m.free_energy(m.to_k(y0))  # the same order of solves as below (warm start)
     yh, e, _ = oracle.ark_step(m, m.to_k(y0), 0.5, oracle.ark436l2sa(), p["rtol"], p["atol"])
-    F0 = m.free_energy(m.to_k(y0))
     with pfg.Simulation(y0.shape[1:], p, "ark4", "fp64") as s:
         s.set_state(y0)
         F = s.free_energy()
@@ -89,6 +89,35 @@ def test_ark4_step_and_free_energy(pfg, params):
     assert F == pytest.approx(F0, rel=1e-12)
     assert np.all(relerr(got, yh) <= 1e-11), relerr(got, yh)
     assert eg == pytest.approx(e, rel=1e-8)
+
+
+def test_warm_start_sequence_matches_oracle(pfg, params):
+    """Three ARK4 steps at the loose tolerance (1e-6): with the warm start
+    every solve continues from the previous one's eps(u) across stages and
+    steps, in the library as in the oracle; the iteration count of each
+    step's last solve and the state after each step agree, and the warm
+    start needs fewer iterations than cold solves (el_warm = 0), which the
+    library reproduces as well."""
+    y0 = synth.ic_spheres(16, 2, 2.5, 3.5, 7, params)
+    counts = {}
+    for warm in (1, 0):
+        p = dict(contrast(params, 1e-6), el_warm=warm)
+        m = oracle.Model(y0.shape[1:], p)
+        yh = m.to_k(y0)
+        its, states = [], []
+        for _ in range(3):
+            yh, _, _ = oracle.ark_step(m, yh, 0.5, oracle.ark436l2sa(), p["rtol"], p["atol"])
+            its.append(m.hc_last_iters)
+            states.append(yh)
+        with pfg.Simulation(y0.shape[1:], p, "ark4", "fp64") as s:
+            s.set_state(y0)
+            for i in range(3):
+                s.step(0.5)
+                assert s.elastic_iterations() == its[i], (warm, i)
+                got = s.state_hat().cpu().numpy()
+                assert np.all(relerr(got, states[i]) <= 1e-10), (warm, i, relerr(got, states[i]))
+        counts[warm] = its
+    assert all(w < c for w, c in zip(counts[1], counts[0])), counts
 
 
 def test_batch_refuses_phase_contrast(pfg, params):
