@@ -1008,6 +1008,14 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
         g.kx = c->d_kx;
         g.ky = c->d_ky;
         g.kz = c->d_kz;
+        // the phi fields share lambda when their gradient tensors are equal
+        g.lam2 = 0;
+        if (c->fp32) {
+            bool same = true;
+            for (int v = 1; v < 3; ++v)
+                for (int i = 0; i < 6; ++i) same = same && params->kappa[v][i] == params->kappa[0][i];
+            g.lam2 = same ? 1 : 0;
+        }
         launch_lambda_table(g, c->ph, c->lam, c->lamdf, c->stream);
         if (c->btab) launch_btab(g, c->ph, c->btab, c->stream);
         e = cudaGetLastError();

@@ -441,19 +441,26 @@ struct CoefSrc {
     __device__ __forceinline__ DF qgamma() const { return dev() ? DF{st.dc->qgh, st.dc->qgl} : DF{st.qgh, st.qgl}; }
 };
 
+// row of the double-float lambda and q tables for element gi = f NK + k:
+// gi itself, or with shared phi rows (g.lam2) k for X and NK + k for any phi
+__device__ __forceinline__ long long lam_row(const Geo& g, long long gi) {
+    return (g.lam2 && gi >= g.NK) ? g.NK + gi % g.NK : gi;
+}
+
 // at most MAXT earlier-stage terms (compile-time bound: fewer registers);
 // Idx: element index type (unsigned where 4 NK < 2^32: one-instruction
-// address arithmetic)
+// address arithmetic); ti: the element's row of the lambda and q tables
+// (lam_row)
 template <int MAXT = kMaxStages, int DC = -1, typename Idx = long long>
 __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms& st, const double2* __restrict__ y,
-                                                 Idx gi, float4* __restrict__ zout) {
+                                                 Idx gi, Idx ti, float4* __restrict__ zout) {
     const CoefSrc<DC> cs{st};
     // every load first (independent, all in flight together), then the sums
     const bool need_lam = st.mI != 0u || st.qout || st.has_gamma;
     const bool load_q = st.has_gamma && st.qin;
     const double2 yv = __ldg(y + gi);
-    const float2 lt = need_lam ? __ldg(g.lamdf + gi) : make_float2(0.f, 0.f);
-    const float2 qt = load_q ? __ldg(reinterpret_cast<const float2*>(st.qin) + gi) : make_float2(1.f, 0.f);
+    const float2 lt = need_lam ? __ldg(g.lamdf + ti) : make_float2(0.f, 0.f);
+    const float2 qt = load_q ? __ldg(reinterpret_cast<const float2*>(st.qin) + ti) : make_float2(1.f, 0.f);
     const unsigned mz = st.mI & ~st.mY;
     float4 zv[MAXT > 0 ? MAXT : 1];
     float2 fv[MAXT > 0 ? MAXT : 1];
@@ -488,9 +495,10 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
             rx = df_add(rx, df_mul(lam, I.x()));
             ry = df_add(ry, df_mul(lam, I.y()));
         }
-        if (st.qout) {
+        // (with shared phi rows the three phi fields would write the same row)
+        if (st.qout && (!g.lam2 || (long long)gi < 2 * g.NK)) {
             const DF q = df_rcp(df_one_minus(cs.qgamma(), lam));
-            reinterpret_cast<float2*>(st.qout)[gi] = make_float2(q.h, q.l);
+            reinterpret_cast<float2*>(st.qout)[ti] = make_float2(q.h, q.l);
         }
         if (st.has_gamma) {
             const DF q = load_q ? DF{qt.x, qt.y} : df_rcp(df_one_minus(cs.gamma(), lam));
@@ -509,14 +517,14 @@ __device__ __forceinline__ float2 stage_value_df(const Geo& g, const StageTerms&
 // DC and Idx as in stage_value_df.
 template <int MAXT = kMaxStages, int DC = -1, typename Idx = long long>
 __device__ __forceinline__ float2 final_value_df(const Geo& g, const StageTerms& bt, const StageTerms& dt,
-                                                 int want_lte, const double2* __restrict__ y, Idx gi,
+                                                 int want_lte, const double2* __restrict__ y, Idx gi, Idx ti,
                                                  double2* __restrict__ ynew) {
     const CoefSrc<DC> cb{bt}, cd{dt};
     const unsigned lmI = want_lte ? dt.mI : 0u, lmE = want_lte ? dt.mE : 0u;
     const unsigned mI = bt.mI | lmI, mE = bt.mE | lmE, mz = mI & ~bt.mY;
     // every load first, then the sums
     const double2 yv = __ldg(y + gi);
-    const float2 lt = mI != 0u ? __ldg(g.lamdf + gi) : make_float2(0.f, 0.f);
+    const float2 lt = mI != 0u ? __ldg(g.lamdf + ti) : make_float2(0.f, 0.f);
     float4 zv[MAXT];
     float2 fv[MAXT];
 #pragma unroll

@@ -43,7 +43,10 @@ struct Geo {
     const double* ky;  // [ny]
     const double* kz;  // [nz]
     const double* lam;  // [4][NK] lambda(k) per field (FP64), or null (computed on the fly)
-    const float2* lamdf;  // [4][NK] lambda(k) as double-float {h, l} (FP32-bulk contexts)
+    const float2* lamdf;  // [4][NK] lambda(k) as double-float {h, l} (FP32-bulk contexts); with lam2 only
+                          // [2][NK]: X, then the one lambda the three phi fields share
+    int lam2;             // 1: the phi fields share lambda (equal kappa_v), so the double-float lambda and q
+                          // tables hold two rows (X, phi) and the streams read each row once per k
     const float* kx32;  // FP32 copies of the wave-number tables (FP32-bulk kernels)
     const float* ky32;
     const float* kz32;

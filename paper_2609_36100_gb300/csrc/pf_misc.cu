@@ -47,7 +47,7 @@ __global__ void k_stage_pointwise_df(Geo g, const double2* __restrict__ y, Stage
     const long long total = 4LL * g.NK;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
          gi += (long long)gridDim.x * blockDim.x)
-        stage_value_df(g, st, y, gi, zout);
+        stage_value_df(g, st, y, gi, lam_row(g, gi), zout);
 }
 
 // FP32-bulk stage assembly, streaming: each element's loads all issued
@@ -56,21 +56,32 @@ __global__ void k_stage_pointwise_df(Geo g, const double2* __restrict__ y, Stage
 // z transform) written back.  Every array is read or written once.  DC: where
 // the coefficients live (0: kernel parameters, 1: the batch's device copy);
 // Idx: element index type.
+//
+// Element order: the grid strides over the wave vectors k, and each thread
+// takes the four fields of its k (U at a time, their loads in flight
+// together), so with shared phi rows (g.lam2) the lambda and q rows of the
+// three phi fields are read from DRAM once and then hit in L1.
 template <int MAXT, int U, int DC, typename Idx>
 __global__ void __launch_bounds__(256) k_stage_assemble_df(Geo g, const double2* __restrict__ y, StageTerms st,
                                                            float4* __restrict__ zout, float2* __restrict__ W) {
+    static_assert(4 % U == 0, "U divides the four fields");
     PF_SKIP_INACTIVE(g);
     if (y_swapped(g)) y = g.yother;
-    const Idx total = (Idx)(4LL * g.NK);
+    const Idx nk = (Idx)g.NK;
     const Idx stride = (Idx)gridDim.x * blockDim.x;
-    for (Idx gi = (Idx)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += stride * U) {
-        float2 r[U];
+    for (Idx k = (Idx)blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += stride) {
+#pragma unroll 1
+        for (int f0 = 0; f0 < 4; f0 += U) {
+            float2 r[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (gi + u * stride < total) r[u] = stage_value_df<MAXT, DC, Idx>(g, st, y, gi + u * stride, zout);
+            for (int u = 0; u < U; ++u) {
+                const Idx gi = (Idx)(f0 + u) * nk + k;
+                const Idx ti = (g.lam2 && f0 + u > 0) ? nk + k : gi;
+                r[u] = stage_value_df<MAXT, DC, Idx>(g, st, y, gi, ti, zout);
+            }
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (gi + u * stride < total) W[gi + u * stride] = r[u];
+            for (int u = 0; u < U; ++u) W[(Idx)(f0 + u) * nk + k] = r[u];
+        }
     }
 }
 
@@ -137,11 +148,17 @@ __global__ void __launch_bounds__(256) k_step_complete_df(Geo g, const double2* 
         y = ynew;
         ynew = other;
     }
-    const Idx total = (Idx)(4LL * g.NK);
+    // element order as in the stage assembly: the four fields of a k per thread
+    const Idx nk = (Idx)g.NK;
     const Idx stride = (Idx)gridDim.x * blockDim.x;
-    for (Idx gi = (Idx)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += stride) {
-        const float2 e = final_value_df<MAXT, DC, Idx>(g, bt, dt, want_lte, y, gi, ynew);
-        if (want_lte) W[gi] = e;
+    for (Idx k = (Idx)blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += stride) {
+#pragma unroll 1
+        for (int f = 0; f < 4; ++f) {
+            const Idx gi = (Idx)f * nk + k;
+            const Idx ti = (g.lam2 && f > 0) ? nk + k : gi;
+            const float2 e = final_value_df<MAXT, DC, Idx>(g, bt, dt, want_lte, y, gi, ti, ynew);
+            if (want_lte) W[gi] = e;
+        }
     }
 }
 
@@ -217,7 +234,7 @@ __global__ void k_lambda_table(Geo g, Phys ph, double* __restrict__ lam, float2*
         const int kz = (int)(q / ((long long)g.nxh * g.ny));
         const double l = lambda_k(ph, f, g.kx[kx], g.ky[ky], g.kz[kz]);
         lam[gi] = l;
-        if (lamdf) {
+        if (lamdf && (!g.lam2 || f <= 1)) {  // shared phi rows: row 1 serves every phi field
             const float h = (float)l;
             lamdf[gi] = make_float2(h, (float)(l - (double)h));
         }

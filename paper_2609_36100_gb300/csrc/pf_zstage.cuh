@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Ge
         if (col >= ncol) return T2{0, 0};
         const long long gi = base + kz * zs + col;
         if constexpr (sizeof(T) == 4) {
-            return stage_value_df<MAXT>(g, st, y, gi, reinterpret_cast<float4*>(zout));
+            return stage_value_df<MAXT>(g, st, y, gi, lam_row(g, gi), reinterpret_cast<float4*>(zout));
         } else {
         // every load first (independent, all in flight together), then the sums
         const double2 yv = __ldg(y + gi);
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_final(Ge
         if (col >= ncol) return T2{0, 0};
         const long long gi = base + kz * zs + col;
         if constexpr (sizeof(T) == 4) {
-            return final_value_df(g, bt, dt, want_lte, y, gi, ynew);
+            return final_value_df(g, bt, dt, want_lte, y, gi, lam_row(g, gi), ynew);
         } else {
         const unsigned lmI = want_lte ? dt.mI : 0u, lmE = want_lte ? dt.mE : 0u;
         const unsigned mI = bt.mI | lmI, mE = bt.mE | lmE, mz = mI & ~bt.mY;
