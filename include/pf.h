@@ -253,9 +253,11 @@ const char* pf_kernel_name(int kind);
  * column transforms, one field after another), whether the FP32 x passes run the staged kernel instead of the
  * fused one (int 39) and whether the compiled-plan elastic pass runs each
  * transform stage and the contraction over the three fields in place instead
- * of fusing the last forward and first inverse stage in registers (int 40).
+ * of fusing the last forward and first inverse stage in registers (int 40)
+ * and whether the FP32 fused x pass of the right-hand side copies its stored
+ * real fields into shared memory with its input rows (int 41).
  * PF_TUNE_LEN ints. */
-#define PF_TUNE_LEN 41
+#define PF_TUNE_LEN 42
 int pf_get_tuning(pf_ctx* ctx, int* cfg, int n);
 int pf_set_tuning(pf_ctx* ctx, const int* cfg, int n);
 /* Autotuner: times `reps` step attempts per candidate schedule on the

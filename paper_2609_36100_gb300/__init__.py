@@ -111,7 +111,7 @@ SIGNATURES = {
                                     C.POINTER(C.c_double)]),
 }
 NKERNELS = 11
-TUNE_LEN = 41
+TUNE_LEN = 42
 _DPTR_ARGS = {"pf_method_tableau"}
 
 _lib = None

@@ -1610,6 +1610,7 @@ int pf_get_tuning(pf_ctx* c, int* cfg, int n) {
     cfg[38] = c->g.el_pid;
     cfg[39] = c->g.xf_off;
     cfg[40] = c->g.el_unfused;
+    cfg[41] = c->g.xf_stg;
     plan_to_cfg(c->g.px, cfg + 4);
     plan_to_cfg(c->g.py, cfg + 4 + 11);
     plan_to_cfg(c->g.pz, cfg + 4 + 22);
@@ -1630,6 +1631,7 @@ int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
     g.el_pid = cfg[38];
     g.xf_off = cfg[39] != 0;
     g.el_unfused = cfg[40] != 0;
+    g.xf_stg = cfg[41] != 0;
     AxisPlan* pl[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
@@ -1746,6 +1748,13 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
             cfg[39] = v;
             trial(cfg);
         }
+        // real fields of the right-hand-side x pass read from global or staged
+        if (c->fp32 && c->ph.elastic)
+            for (int v : {0, 1}) {
+                std::memcpy(cfg, best, sizeof cfg);
+                cfg[41] = v;
+                trial(cfg);
+            }
         // elastic pass with the fused stage or with every stage over the three fields
         if (c->ph.elastic && !c->inhom)
             for (int v : {0, 1}) {

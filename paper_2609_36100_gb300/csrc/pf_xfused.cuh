@@ -19,10 +19,14 @@
 
 namespace pf {
 
-enum XFMode { XF_PHYS1_H = 0, XF_PHYS1_RHS = 1, XF_PHYS2 = 2, XF_WRMS = 3 };
+// XF_PHYS2_STG: XF_PHYS2 with the stored real fields the physics reads
+// copied into shared memory (cp.async) together with the input rows, so that
+// the physics does not wait on global loads
+enum XFMode { XF_PHYS1_H = 0, XF_PHYS1_RHS = 1, XF_PHYS2 = 2, XF_WRMS = 3, XF_PHYS2_STG = 4 };
 template <int MODE>
 struct XFIO {
-    static constexpr int FIN = MODE == XF_PHYS2 ? 3 : 4;  // input lines per row pair
+    static constexpr bool PHYS2 = MODE == XF_PHYS2 || MODE == XF_PHYS2_STG;
+    static constexpr int FIN = PHYS2 ? 3 : 4;  // input lines per row pair
     static constexpr int FOUT = MODE == XF_WRMS ? 0 : (MODE == XF_PHYS1_H ? 3 : 4);
 };
 
@@ -79,6 +83,20 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph,
             cp_async<8>(B + e, in + (long long)f * NK + (2LL * (rp0 + rp) + (r & 1)) * NXH + k);
         else
             B[e] = T2{0.f, 0.f};
+    }
+    // the real fields X, phi_v of the CTA's rows -> C ([row pair][field][2 rows][N]), 16-byte copies
+    constexpr bool STG = MODE == XF_PHYS2_STG;
+    float* C = reinterpret_cast<float*>(B + P * 4 * LS);
+    if constexpr (STG) {
+        constexpr int Q = N / 4;  // 16-byte chunks per row
+        for (int e = threadIdx.x; e < P * 8 * Q; e += NT) {
+            const int r = e / Q, q = e - r * Q;  // r = (rp 4 + f) 2 + (0: row y, 1: row y+1)
+            const int rp = r >> 3, f = (r >> 1) & 3;
+            if (rp0 + rp < npairs)
+                cp_async<16>(C + 4 * e, Rin + f * N3 + (2LL * (rp0 + rp) + (r & 1)) * N + 4 * q);
+            else
+                reinterpret_cast<float4*>(C)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -166,11 +184,19 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph,
         for (int t = 0; t < RM; ++t) {
             const int x = j + t * M;
             float Xr[2], pr[2][3], er[2][3];
-            if constexpr (MODE == XF_PHYS2) {
+            if constexpr (XFIO<MODE>::PHYS2) {
 #pragma unroll
                 for (int f = 0; f < 4; ++f) {
-                    const float* b = Rin + f * N3 + row * N + x;
-                    const float u0 = valid ? b[0] : 0.f, u1 = valid ? b[N] : 0.f;
+                    float u0, u1;
+                    if constexpr (STG) {
+                        const float* c = C + ((rp * 4 + f) * 2) * N + x;
+                        u0 = c[0];
+                        u1 = c[N];
+                    } else {
+                        const float* b = Rin + f * N3 + row * N + x;
+                        u0 = valid ? b[0] : 0.f;
+                        u1 = valid ? b[N] : 0.f;
+                    }
                     if (f == 0) {
                         Xr[0] = u0;
                         Xr[1] = u1;
@@ -274,7 +300,8 @@ static int launch_x_fused_n(const Geo& g, const Phys& ph, const void* in, void* 
                             double* partials, double rtol, double atol, cudaStream_t s) {
     using Pl = XFPlan<N>;
     using Sh = XFShape<typename Pl::Fwd, Pl::P>;
-    const size_t sm = 2 * (size_t)Pl::P * 4 * Sh::LS * sizeof(float2);
+    const size_t sm = 2 * (size_t)Pl::P * 4 * Sh::LS * sizeof(float2) +
+                      (MODE == XF_PHYS2_STG ? (size_t)Pl::P * 8 * N * sizeof(float) : 0);
     const int npairs = g.nz * g.ny / 2;
     const int nb = (npairs + Pl::P - 1) / Pl::P;
     auto k = k_x_fused<float, typename Pl::Fwd, Pl::P, MODE>;
@@ -296,7 +323,9 @@ static int launch_x_fused_modes(const Geo& g, const Phys& ph, int mode, const vo
                 return ph.elastic ? launch_x_fused_n<N, XF_PHYS1_H>(g, ph, in, out, R, Rin, partials, rtol, atol, s)
                                   : launch_x_fused_n<N, XF_PHYS1_RHS>(g, ph, in, out, R, Rin, partials, rtol, atol, s);
             case XM_PHYS2:
-                return ph.elastic ? launch_x_fused_n<N, XF_PHYS2>(g, ph, in, out, R, Rin, partials, rtol, atol, s) : 0;
+                if (!ph.elastic) return 0;
+                return g.xf_stg ? launch_x_fused_n<N, XF_PHYS2_STG>(g, ph, in, out, R, Rin, partials, rtol, atol, s)
+                                : launch_x_fused_n<N, XF_PHYS2>(g, ph, in, out, R, Rin, partials, rtol, atol, s);
             case XM_WRMS: return launch_x_fused_n<N, XF_WRMS>(g, ph, in, out, R, Rin, partials, rtol, atol, s);
             default: return 0;
         }

@@ -2,7 +2,8 @@
 forward stage in registers; C2R packing folded into the first inverse stage,
 R2C unpacking into the store) against the FP64 oracle, for every line length
 that has a fused plan, on grids whose row-pair count leaves a ragged last CTA;
-the staged kernel (tuning slot 39) must agree as well."""
+the staged kernel (tuning slot 39) and the right-hand-side pass with its
+real fields copied into shared memory (slot 41) must agree as well."""
 import numpy as np
 import pytest
 
@@ -40,13 +41,14 @@ def test_fused_x_rhs_matches_oracle(pfg, params, nx, elastic):
     ref = m.rhs_explicit(yh)
     dev = torch.from_numpy(yh).to("cuda")
     with pfg.Simulation(shape, p, "ark4", "fp32bulk") as s:
-        for off in (0, 1):
+        for off, stg in ((0, 0), (0, 1), (1, 0)):
             cfg = s.tuning()
             cfg[39] = off
+            cfg[41] = stg
             s.set_tuning(cfg)
             got = s.rhs_explicit(dev).cpu().numpy()
             err = relerr(got, ref)
-            assert np.all(err <= 2e-5), (off, err)
+            assert np.all(err <= 2e-5), (off, stg, err)
 
 
 @pytest.mark.parametrize("nx", [96, 256, 640])
