@@ -508,7 +508,7 @@ def run_ensemble(K, t_final, rank=0, world=1):
 def run_surrogate(ntraj, n=128, dt=1.0, nsnap=25, epochs=1):
     """FNO (4 spectral layers, 12 modes, width 32, BF16 spectral weights)
     trained with the library's kernels on `ntraj` solver trajectories of the
-    config-1 recipe scaled to n^3 (8 nuclei; ARK4 FP32-bulk, dt = 1 s,
+    8-ellipsoid recipe scaled to n^3 (8 nuclei; ARK4 FP32-bulk, dt = 1 s,
     snapshots every tau = 8 s, 0-200 s), then rollouts of two held-out seeds
     to 200 s in windows of tau: each window proposed by the network and
     judged by the method's own adaptive integration of the window (rtol
@@ -521,7 +521,7 @@ def run_surrogate(ntraj, n=128, dt=1.0, nsnap=25, epochs=1):
     from paper_2609_36100_gb300 import surrogate as S
 
     p = synth.load_params()
-    ics = [(synth.ic_config1(n, 1000 + i, p), p) for i in range(ntraj)]
+    ics = [(synth.ic_ellipsoids(n, 1000 + i, p), p) for i in range(ntraj)]
     w0 = time.perf_counter()
     traj = S.trajectories(ics, p, dt, nsnap)
     torch.cuda.synchronize()
@@ -537,7 +537,7 @@ def run_surrogate(ntraj, n=128, dt=1.0, nsnap=25, epochs=1):
     t_end = nsnap * tau
     rows = []
     for seed in (2000, 2001):
-        y0 = synth.ic_config1(n, seed, p)
+        y0 = synth.ic_ellipsoids(n, seed, p)
         ref, _, _, _, _ = S.rollout(y0, p, t_end, tau, None, precision="fp64", rtol=1e-8, atol=1e-12)
         plain, wp, _, _, _ = S.rollout(y0, p, t_end, tau, None)
         sur, ws, acc, off, dists = S.rollout(y0, p, t_end, tau, net)
@@ -633,7 +633,7 @@ def cpu_baseline(n, budget_s=15.0):
             break
     val = k * n ** 3 / el / 1e9
     return {"value": val, "unit": UNIT, "cores": om._WORKERS, "kind": "oracle",
-            "sample": "%d explicit RHS evaluation(s) of the %d^3 config-2 initial state (FP64 numpy/scipy, %.1f s)" % (k, n, el)}
+            "sample": "%d explicit RHS evaluation(s) of the %d^3 32-sphere initial state (FP64 numpy/scipy, %.1f s)" % (k, n, el)}
 
 
 def run_reference(args):

@@ -140,7 +140,7 @@ def _disc(a: float, c: float, v: int):
     return tuple(s)
 
 
-def ic_config1(n: int = 64, seed: int = 1, p: dict | None = None, count: int = 8) -> np.ndarray:
+def ic_ellipsoids(n: int = 64, seed: int = 1, p: dict | None = None, count: int = 8) -> np.ndarray:
     """8 ellipsoidal nuclei (semi-axes 3-6 cells, c-axis along the variant
     axis), uniform matrix composition plus N(0, 1e-3) noise."""
     p = p or load_params()
@@ -170,7 +170,7 @@ def ic_spheres(n: int, count: int, rmin: float, rmax: float, seed: int, p: dict 
     return nuclei_ic((n, n, n), p, nuc, x_inside=p["B_v"] if x_inside else None)
 
 
-def ic_config2(n: int = 256, seed: int = 2, p: dict | None = None) -> np.ndarray:
+def ic_spheres_32(n: int = 256, seed: int = 2, p: dict | None = None) -> np.ndarray:
     return ic_spheres(n, 32, 4.0, 10.0, seed, p)
 
 
@@ -192,7 +192,7 @@ def ensemble_member(index: int, p: dict | None = None, sides=(64, 96, 120, 128, 
     return nuclei_ic((n, n, n), p, nuc, x_inside=p["B_v"]), p
 
 
-def ic_config5(n: int = 640, seed: int = 5, p: dict | None = None) -> np.ndarray:
+def ic_spheres_300(n: int = 640, seed: int = 5, p: dict | None = None) -> np.ndarray:
     return ic_spheres(n, 300, 4.0, 12.0, seed, p)
 
 

@@ -93,7 +93,7 @@ def test_checkpoint_resume_bitwise(pfg, params, prec):
 
 
 def test_fixed_steps_resume_bitwise(pfg, params):
-    y0 = synth.ic_config1(32, 1, params, count=4)
+    y0 = synth.ic_ellipsoids(32, 1, params, count=4)
     with pfg.Simulation(y0.shape[1:], params, "euler", "fp64") as a:
         a.set_state(y0)
         for _ in range(10):

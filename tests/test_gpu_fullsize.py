@@ -1,4 +1,4 @@
-"""Full-size parity on the bench workload: the 256^3 config-2 initial state
+"""Full-size parity on the bench workload: the 256^3 32-sphere initial state
 (32 seeded spheres), one ARK4(3)6L[2]SA step of h = 1 s (the controller's
 first attempt in the bench), compared over the whole field with one FP64
 oracle step.  The FP32-bulk form runs in the launch configuration the bench

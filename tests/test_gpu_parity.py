@@ -97,10 +97,10 @@ def test_solve_implicit(pfg, params):
     assert np.max(np.abs(got - ref)) <= 1e-15 * np.max(np.abs(ref))
 
 
-def test_euler_config1_50_steps(pfg, params):
+def test_euler_ellipsoids_64_50_steps(pfg, params):
     """Plain method, FP64, 64^3, 8 ellipsoidal nuclei, ImEx Euler, 50 fixed
     steps of 0.25 s (rel L2 <= 1e-11 per field; composition mean bitwise)."""
-    y0 = synth.ic_config1(64, 1, params)
+    y0 = synth.ic_ellipsoids(64, 1, params)
     m = oracle.Model(y0.shape[1:], params)
     yh = m.to_k(y0)
     tab = oracle.euler()
@@ -167,7 +167,7 @@ def test_adaptive_advance_replayed(pfg, params):
 
 
 def test_free_energy(pfg, params):
-    y0 = synth.ic_config1(32, 1, params)
+    y0 = synth.ic_ellipsoids(32, 1, params)
     m = oracle.Model(y0.shape[1:], params)
     with pfg.Simulation(y0.shape[1:], params, "ark4", "fp64") as s:
         s.set_state(y0)

@@ -27,13 +27,13 @@ def pfg():
 def test_surrogate_gain_and_error(pfg, params):
     from paper_2609_36100_gb300 import surrogate as S
     n, dt = 32, 1.0
-    ics = [(synth.ic_config1(n, 1000 + i, params, count=3), params) for i in range(8)]
+    ics = [(synth.ic_ellipsoids(n, 1000 + i, params, count=3), params) for i in range(8)]
     traj = S.trajectories(ics, params, dt, 12)
     net = S.new_network((n, n, n), C=16, modes=6, H=64, L=4)
     try:
         losses = S.train(net, traj, 4, 1e-3)
         assert losses[-1] < losses[0]
-        y0 = synth.ic_config1(n, 2000, params, count=3)
+        y0 = synth.ic_ellipsoids(n, 2000, params, count=3)
         ref, _, _, _, _ = S.rollout(y0, params, 96.0, 8.0, None, precision="fp64", rtol=1e-8, atol=1e-12)
         plain, w_plain, _, _, _ = S.rollout(y0, params, 96.0, 8.0, None)
         sur, w_sur, acc, off, dists = S.rollout(y0, params, 96.0, 8.0, net)

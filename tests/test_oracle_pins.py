@@ -452,7 +452,7 @@ def test_rhs_is_variational_derivative_of_free_energy(params):
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("meth", ["euler", "ark4"])
 def test_composition_mean_conserved_bitwise(meth, params):
-    y = synth.ic_config1(16, 1, params, count=2)
+    y = synth.ic_ellipsoids(16, 1, params, count=2)
     m = oracle.Model(y.shape[1:], params)
     yh = m.to_k(y)
     dc = yh[0, 0, 0, 0]
@@ -463,7 +463,7 @@ def test_composition_mean_conserved_bitwise(meth, params):
 
 
 def test_free_energy_decreases_first_order(params):
-    y = synth.ic_config1(32, 1, params)
+    y = synth.ic_ellipsoids(32, 1, params)
     m = oracle.Model(y.shape[1:], params)
     yh = m.to_k(y)
     F = m.free_energy(yh)
@@ -478,7 +478,7 @@ def test_free_energy_decreases_first_order(params):
 def test_manual_chen_shen_equals_ark_euler(params):
     """Sec. 2.3: the hand-written first-order scheme and the ARK form of ImEx
     Euler give the same solution to rounding."""
-    y = synth.ic_config1(16, 1, params, count=2)
+    y = synth.ic_ellipsoids(16, 1, params, count=2)
     m = oracle.Model(y.shape[1:], params)
     a = b = m.to_k(y)
     for _ in range(10):
