@@ -1,10 +1,10 @@
 #!/usr/bin/env python
 """Throughput of the pseudospectral ImEx-ARK phase-field hot path on GB300.
 
-Workload (the configuration the metric is quoted on: "FP64 vs FP32-bulk,
-256^3 grid ... integrated to a fixed simulated time; error per field"):
-256^3 periodic grid, 4 fields (X, phi_1..3), 32 seeded spherical gamma''
-nuclei (radius 4-10 cells, composition at the precipitate value inside),
+Workload (FP64 against FP32-bulk integrated to a fixed simulated time, with
+the error per field): 256^3 periodic grid, 4 fields (X, phi_1..3), 32 seeded
+spherical gamma'' nuclei (radius 4-10 cells, composition at the precipitate
+value inside),
 ARK4(3)6L[2]SA with the embedded-error WRMS controller at rtol 1e-4,
 atol 1e-8, integrated from t = 0 (h0 = 1 s) to t_final = 60 s.  One bench
 step = one such integration: every controller-driven step attempt (6 stages,
