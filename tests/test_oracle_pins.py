@@ -410,13 +410,45 @@ def test_equilibrium_slab_is_stationary(params):
 # --------------------------------------------------------------------------
 # variational structure: the right-hand side is -L dF/dphi and div(M grad dF/dX)
 # --------------------------------------------------------------------------
-def test_rhs_is_variational_derivative_of_free_energy(params):
-    p = params
+def test_kks_with_unequal_curvatures(params):
+    """Eqs. x_sum and equal_mu with parabolic phases of different curvature
+    (A^v = 2.5 A^m, another reference composition): the oracle's closed form
+    gives phase compositions that satisfy both constraints exactly, and the
+    chemical potential is the derivative of the mixed free energy
+    (1 - H) f^m(X^m) + H f^v(X^v) with respect to X at fixed h (the KKS
+    identity), checked by finite differences."""
+    p = dict(params, A_v=2.5 * params["A_m"], B_v=0.2)
+    m = oracle.Model((4, 4, 4), p)
+    rng = np.random.default_rng(8)
+    X = rng.uniform(0.02, 0.25, size=(4, 4, 4))
+    h = rng.uniform(0.0, 0.3, size=(3, 4, 4, 4))
+    H, mu, Xm, Xv, fm, fv = m.kks(X, h)
+    assert np.allclose(2 * p["A_m"] * (Xm - m.Bm), mu, rtol=1e-13, atol=1e-13)
+    assert np.allclose(2 * p["A_v"] * (Xv - p["B_v"]), mu, rtol=1e-13, atol=1e-13)
+    assert np.allclose((1 - H) * Xm + H * Xv, X, rtol=1e-13, atol=1e-15)
+
+    def f_mix(Xs):
+        H_, _, Xm_, Xv_, fm_, fv_ = m.kks(Xs, h)
+        return (1 - H_) * fm_ + H_ * fv_
+
+    d = 1e-6
+    dfdX = (f_mix(X + d) - f_mix(X - d)) / (2 * d)
+    assert np.allclose(dfdX, mu, rtol=1e-7, atol=1e-9)
+
+
+@pytest.mark.parametrize("A_v_factor", [1.0, 2.5])
+def test_rhs_is_variational_derivative_of_free_energy(params, A_v_factor):
+    """-L dF/dphi_v and the composition's chemical potential against finite
+    differences of F; with unequal curvatures (A^v = 2.5 A^m) the fields
+    keep sum_v h(phi_v) <= 1, where the KKS mixture of the two parabolas is
+    well posed (beyond it the denominator H/(2A^v) + (1-H)/(2A^m) can
+    vanish)."""
+    p = dict(params, A_v=A_v_factor * params["A_m"])
     shape = (8, 8, 8)
     rng = np.random.default_rng(5)
     y = np.empty((4,) + shape)
     y[0] = 0.06 + 0.01 * rng.standard_normal(shape)
-    y[1:] = rng.uniform(0.05, 0.95, size=(3,) + shape)
+    y[1:] = rng.uniform(0.05, 0.95 if A_v_factor == 1.0 else 0.4, size=(3,) + shape)
     m = oracle.Model(shape, p)
     yh = m.to_k(y)
     tot = m.to_r(m.rhs_explicit(yh) + m.rhs_implicit(yh))
