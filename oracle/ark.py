@@ -258,7 +258,7 @@ def advance(model, yhat: np.ndarray, t0: float, t_final: float, tab: Tableau, p:
         log.append((t, h, e, ok))
         k += 1
         if ok:
-            y = ynew
+            y = model.project(ynew) if hasattr(model, "project") else ynew
             t = t + h
             nrej = 0
             hn = ctl.accept(h, e)

@@ -15,6 +15,11 @@ the readings:
 * composition stiff part lambda_X = -2 A^m M k^2, the rest explicit;
 * parabolic f^p = A0^p + A^p (X^p - B^p)^2 (Eq. f_ch_p read as squared);
 * barrier: omega_bar sum_v phi_v^2 (1 - phi_v)^2 (double-well reading of Eq. f_b);
+  with barrier = 1 the literal term of Eq. f_b instead, omega_bar S (1 - S)
+  with S = sum_v phi_v (derivative omega_bar (1 - 2 S)), an obstacle-type
+  potential that needs phi_v in [0, 1]: project() clamps the order parameters
+  in real space, applied after every completed step (the paper does not say
+  how the bound is kept);
 * the |x| of the pairwise barrier omega_vq |phi_v phi_q| is Huber-regularised
   with width eps (A(x) = x^2/(2 eps) for |x| < eps, |x| - eps/2 beyond), so
   d/dphi_v = omega_vq clip(phi_v phi_q / eps, -1, 1) phi_q is continuous;
@@ -97,6 +102,7 @@ class Model:
         self.A0m, self.A0v = p["A0_m"], p["A0_v"]
         self.L = p["L"]
         self.wbar = p["omega_bar"]
+        self.obstacle = int(p.get("barrier", 0)) == 1
         self.pair_eps = p["pair_eps"]
         w12, w13, w23 = p["omega_pair"]
         self.omega = np.array([[0.0, w12, w13], [w12, 0.0, w23], [w13, w23, 0.0]])
@@ -154,7 +160,11 @@ class Model:
     def dfb_dphi(self, phi):
         """Derivative of the local part of f_b: double well plus the
         (regularised) pairwise |phi_v phi_q| barrier."""
-        out = 2.0 * self.wbar * phi * (1.0 - phi) * (1.0 - 2.0 * phi)
+        if self.obstacle:
+            # d/dphi_v of omega_bar S (1 - S), S = sum_q phi_q
+            out = np.broadcast_to(self.wbar * (1.0 - 2.0 * phi.sum(axis=0)), phi.shape).copy()
+        else:
+            out = 2.0 * self.wbar * phi * (1.0 - phi) * (1.0 - 2.0 * phi)
         for v in range(3):
             for q in range(3):
                 if q != v:
@@ -186,6 +196,18 @@ class Model:
         if self.hc_warm:
             self.hc_prev = self.hc.last_eps_u
         self.hc_last_iters = out[4]
+        return out
+
+    def project(self, yhat: np.ndarray) -> np.ndarray:
+        """The obstacle barrier's bound: the order parameters clamped to
+        [0, 1] in real space; the composition's coefficients are kept as
+        they are (its mean stays exact).  The identity without the obstacle."""
+        if not self.obstacle:
+            return yhat
+        real = self.to_r(yhat)
+        real[1:] = np.clip(real[1:], 0.0, 1.0)
+        out = self.to_k(real)
+        out[0] = yhat[0]
         return out
 
     # --- right-hand sides -------------------------------------------------
@@ -220,7 +242,11 @@ class Model:
         X, phi = real[0], real[1:4]
         h = h_interp(phi)
         H, mu, Xm, Xv, fm, fv = self.kks(X, h)
-        local = self.wbar * (phi ** 2 * (1.0 - phi) ** 2).sum(axis=0)
+        if self.obstacle:
+            S = phi.sum(axis=0)
+            local = self.wbar * S * (1.0 - S)
+        else:
+            local = self.wbar * (phi ** 2 * (1.0 - phi) ** 2).sum(axis=0)
         for v in range(3):
             for q in range(v + 1, 3):
                 local = local + self.omega[v, q] * self.pair_abs(phi[v] * phi[q])

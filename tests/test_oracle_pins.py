@@ -436,14 +436,14 @@ def test_kks_with_unequal_curvatures(params):
     assert np.allclose(dfdX, mu, rtol=1e-7, atol=1e-9)
 
 
-@pytest.mark.parametrize("A_v_factor", [1.0, 2.5])
-def test_rhs_is_variational_derivative_of_free_energy(params, A_v_factor):
+@pytest.mark.parametrize("A_v_factor,barrier", [(1.0, 0), (2.5, 0), (1.0, 1)])
+def test_rhs_is_variational_derivative_of_free_energy(params, A_v_factor, barrier):
     """-L dF/dphi_v and the composition's chemical potential against finite
     differences of F; with unequal curvatures (A^v = 2.5 A^m) the fields
     keep sum_v h(phi_v) <= 1, where the KKS mixture of the two parabolas is
     well posed (beyond it the denominator H/(2A^v) + (1-H)/(2A^m) can
-    vanish)."""
-    p = dict(params, A_v=A_v_factor * params["A_m"])
+    vanish); barrier = 1: the literal obstacle term of Eq. f_b."""
+    p = dict(params, A_v=A_v_factor * params["A_m"], barrier=barrier)
     shape = (8, 8, 8)
     rng = np.random.default_rng(5)
     y = np.empty((4,) + shape)
@@ -477,6 +477,60 @@ def test_rhs_is_variational_derivative_of_free_energy(params, A_v_factor):
     mu = m.to_r(muh[None])[0]
     a, b = (1, 2, 3), (6, 0, 4)
     assert mu[a] - mu[b] == pytest.approx(dF(0, a) - dF(0, b), rel=1e-6)
+
+
+def test_obstacle_barrier_equilibrium_and_bound(params):
+    """Literal barrier of Eq. f_b for one variant, omega_bar phi (1 - phi),
+    with the gradient energy: the planar equilibrium between phi = 0 and 1
+    is phi = (1 - sin(d/l))/2 over |d| <= pi l/2, l = sqrt(kappa/(2 omega_bar))
+    (kappa phi'' = omega_bar (1 - 2 phi)); with the chemical drive zeroed
+    (X = B^m + H (B^v - B^m)) the oracle's order-parameter RHS vanishes inside
+    that interface (to the spectral error of the profile's kinks) but not for
+    the double well's tanh profile, and in the bulk phases it pushes against
+    the bound (+L omega_bar at phi = 1, -L omega_bar at phi = 0), which the
+    projection then holds."""
+    p = dict(params, barrier=1, eps_c=0.0, eps_a=0.0, dx=0.025)
+    nx = 512
+    m = oracle.Model((2, 2, nx), p)
+    ell = math.sqrt(p["kappa_iso"] / (2 * p["omega_bar"]))
+    x = (np.arange(nx) - nx / 2) * p["dx"]
+    d = np.abs(x) - 3.0
+    w = math.pi * ell / 2
+    sin_prof = np.where(d <= -w, 1.0, np.where(d >= w, 0.0, 0.5 * (1 - np.sin(d / ell))))
+    tanh_prof = 0.5 * (1 - np.tanh(d / (math.sqrt(2) * math.sqrt(p["kappa_iso"] / p["omega_bar"]))))
+    scale = p["L"] * p["omega_bar"]
+    inner = np.abs(d) < w - 0.1
+
+    def rhs(prof):
+        y = np.zeros((4, 2, 2, nx))
+        y[1] = prof[None, None, :]
+        y[0] = m.Bm + oracle.h_interp(y[1:]).sum(axis=0) * (p["B_v"] - m.Bm)
+        yh = m.to_k(y)
+        return m.to_r(m.rhs_explicit(yh) + m.rhs_implicit(yh))[1, 0, 0] / scale
+
+    r = rhs(sin_prof)
+    assert np.max(np.abs(r[inner])) < 2e-2
+    assert np.min(r[d < -w - 0.2]) > 0.9 and np.max(r[d > w + 0.2]) < -0.9
+    assert np.max(np.abs(rhs(tanh_prof)[inner])) > 0.2
+
+
+def test_obstacle_projection(params):
+    """project(): order parameters clamped to [0, 1] in real space, the
+    composition's coefficients untouched (bitwise), idempotent; the identity
+    with the double well."""
+    shape = (8, 10, 12)
+    y = synth.random_state(shape, 3)
+    y[1:] = 1.6 * y[1:] - 0.3  # values outside [0, 1]
+    m = oracle.Model(shape, dict(params, barrier=1))
+    yh = m.to_k(y)
+    pr = m.project(yh)
+    assert np.array_equal(pr[0], yh[0])
+    r = m.to_r(pr)[1:]
+    assert r.min() >= -1e-14 and r.max() <= 1 + 1e-14
+    assert np.allclose(r, np.clip(y[1:], 0.0, 1.0), atol=1e-14)
+    assert np.max(np.abs(m.project(pr) - pr)) <= 1e-15
+    m0 = oracle.Model(shape, params)
+    assert m0.project(yh) is yh
 
 
 # --------------------------------------------------------------------------
