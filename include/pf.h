@@ -107,6 +107,12 @@ typedef struct {
     double el_tol;
     int el_max_iter;
     int el_warm;
+    /* barrier term of Eq. f_b: 0 = the double well omega_bar sum_v
+       phi_v^2 (1 - phi_v)^2 (tanh interfaces); 1 = the literal obstacle
+       term omega_bar S (1 - S), S = sum_v phi_v, with the order parameters
+       clamped to [0, 1] in real space after every completed step (the
+       composition's coefficients untouched).  Batches refuse 1. */
+    int barrier;
 } pf_params;
 
 typedef struct {

@@ -44,6 +44,7 @@ class PFParams(C.Structure):
         ("eta_max", C.c_double), ("eta_min", C.c_double), ("eta_reject_min", C.c_double),
         ("el_inhom", C.c_int), ("C11_v", C.c_double), ("C12_v", C.c_double), ("C44_v", C.c_double),
         ("el_tol", C.c_double), ("el_max_iter", C.c_int), ("el_warm", C.c_int),
+        ("barrier", C.c_int),
     ]
 
 
@@ -168,6 +169,7 @@ def make_params(p: dict, method="ark4", precision="fp64") -> PFParams:
     q.el_tol = float(p.get("el_tol", 1e-6))
     q.el_max_iter = int(p.get("el_max_iter", 20))
     q.el_warm = int(p.get("el_warm", 1))
+    q.barrier = int(p.get("barrier", 0))
     q.method = METHODS[method] if isinstance(method, str) else int(method)
     q.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return q

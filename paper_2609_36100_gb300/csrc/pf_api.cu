@@ -215,6 +215,7 @@ struct pf_ctx {
     double* lam = nullptr;   // [4][NK] lambda(k), FP64
     float2* lamdf = nullptr;  // [4][NK] lambda(k), double-float (FP32-bulk contexts)
     float* btab = nullptr;    // FP32 elastic-kernel table (FP32-bulk contexts with diagonal eigenstrains)
+    double2* xsave = nullptr;  // the composition's k-space field across the obstacle projection (barrier = 1)
     double* qtab = nullptr;  // [4][NK] 1/(1 - dt gamma lambda) of the current step (ESDIRK diagonal)
     double gdiag = 0.0;      // common nonzero implicit diagonal entry, or 0
     double* partials = nullptr;
@@ -296,6 +297,8 @@ void typed_phys(const Phys& ph, double invN, PhysT<T>& o) {
     o.Am = (T)ph.Am;
     o.Av = (T)ph.Av;
     o.wb2 = (T)(2.0 * ph.wbar);
+    o.wb = (T)ph.wbar;
+    o.obst = ph.obst;
     o.ie = (T)(1.0 / ph.pair_eps);
     o.twoAm = (T)(2.0 * ph.Am);
     o.C44 = (T)ph.C44;
@@ -325,6 +328,7 @@ void derive_phys(const pf_params& p, Phys& ph) {
     ph.inv2Av = 1.0 / (2.0 * p.A_v);
     ph.L = p.L;
     ph.wbar = p.omega_bar;
+    ph.obst = p.barrier == 1 ? 1 : 0;
     ph.pair_eps = p.pair_eps;
     ph.w[0][1] = ph.w[1][0] = p.omega_pair[0];
     ph.w[0][2] = ph.w[2][0] = p.omega_pair[1];
@@ -381,6 +385,7 @@ void free_all(pf_ctx* c) {
     cudaFree(c->lam);
     cudaFree(c->lamdf);
     cudaFree(c->btab);
+    cudaFree(c->xsave);
     cudaFree(c->qtab);
     cudaFree(c->partials);
     cudaFree(c->hc_tau);
@@ -860,7 +865,8 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     c->inhom = params->el_inhom != 0 && c->ph.elastic;
     if (c->inhom) {
         if (!(params->C11_v > params->C12_v) || !(params->C11_v + 2 * params->C12_v > 0) || !(params->C44_v > 0) ||
-            !(params->el_tol >= 0) || params->el_max_iter < 1 || (params->el_warm != 0 && params->el_warm != 1)) {
+            !(params->el_tol >= 0) || params->el_max_iter < 1 || (params->el_warm != 0 && params->el_warm != 1) ||
+            (params->barrier != 0 && params->barrier != 1)) {
             delete c;
             return fail(nullptr, PF_EINVAL, "invalid precipitate stiffness or elastic-solver settings");
         }
@@ -951,6 +957,7 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     if (c->fp32 && c->ph.elastic && !c->inhom && diag && 6 * tabn * (long long)sizeof(float) <= (256LL << 20))
         rc = rc ? rc : dalloc(c, &c->btab, 6 * (size_t)tabn * sizeof(float));
     rc = rc ? rc : dalloc(c, &c->qtab, nk4 * sizeof(double));
+    if (params->barrier == 1) rc = rc ? rc : dalloc(c, &c->xsave, (size_t)g.NK * sizeof(double2));
     // worst case over any tuned rows-per-CTA setting (one row pair per CTA)
     c->npartials = g.nz * g.ny / 2;
     if (energy_k_blocks(g) > c->npartials) c->npartials = energy_k_blocks(g);
@@ -1153,6 +1160,28 @@ int pf_solve_implicit(pf_ctx* c, double gamma, const void* r_hat, void* z_hat) {
     return PF_OK;
 }
 
+// The obstacle barrier's bound after a completed step: the state to real
+// space (the FP64 pipeline of pf_get_state), the order parameters clamped to
+// [0, 1], back to k-space (that of pf_set_state); the composition's
+// coefficients are restored unchanged, so its mean stays exact.
+static int project_obstacle(pf_ctx* c) {
+    if (!c->ph.obst) return PF_OK;
+    const Geo& g = c->g;
+    cudaStream_t s = c->stream;
+    PF_CUDA(c, cudaMemcpyAsync(c->xsave, c->y, (size_t)g.NK * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    StageTerms none{};
+    double* real = reinterpret_cast<double*>(fp64_scratch(c));
+    launch_z_stage<double>(g, c->ph, c->y, none, nullptr, c->ynew, s);
+    launch_y_pass<double>(g, c->ynew, 4, +1, s);
+    launch_x_pass<double>(g, c->ph, XM_C2R_REAL, c->ynew, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr, real, s);
+    launch_clamp_phi(real, g.N, s);
+    launch_x_pass<double>(g, c->ph, XM_R2C_REAL, nullptr, c->ynew, nullptr, nullptr, nullptr, 0, 0, real, nullptr, s);
+    launch_y_pass<double>(g, c->ynew, 4, -1, s);
+    launch_z_fwd<double>(g, c->ph, c->ynew, c->y, 0, s);
+    PF_CUDA(c, cudaMemcpyAsync(c->y, c->xsave, (size_t)g.NK * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    return check_launch(c, "obstacle projection");
+}
+
 int pf_step(pf_ctx* c, double dt, double* lte_wrms_out) {
     if (!c) return fail(c, PF_EINVAL, "pf_step: NULL context");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(c, PF_EINVAL, "pf_step: dt must be positive");
@@ -1162,6 +1191,7 @@ int pf_step(pf_ctx* c, double dt, double* lte_wrms_out) {
     if (rc) return rc;
     if (lte_wrms_out == nullptr) PF_CUDA(c, cudaStreamSynchronize(c->stream));
     std::swap(c->y, c->ynew);
+    if (int prc = project_obstacle(c)) return prc;
     c->t += dt;
     c->st.steps_accepted += 1;
     c->st.t = c->t;
@@ -1203,6 +1233,7 @@ int pf_advance_attempts(pf_ctx* c, double t_final, double rtol, double atol, int
         double hn;
         if (ok) {
             std::swap(c->y, c->ynew);
+            if ((rc = project_obstacle(c))) break;
             c->t += h;
             nrej = 0;
             c->st.steps_accepted += 1;
@@ -1257,6 +1288,10 @@ int pf_batch_advance(pf_ctx* const* ctxs, int n, double t_final, double rtol, do
         if (!ctxs[i]) return fail(nullptr, PF_EINVAL, "pf_batch_advance: NULL context %d", i);
         if (ctxs[i]->prm.method != ctxs[0]->prm.method || ctxs[i]->fp32 != ctxs[0]->fp32)
             return fail(ctxs[i], PF_EINVAL, "pf_batch_advance: members differ in method or precision");
+        if (ctxs[i]->ph.obst)
+            return fail(ctxs[i], PF_EUNSUPPORTED,
+                        "pf_batch_advance: the obstacle barrier's projection after each step is not part of the "
+                        "batch graph");
         if (ctxs[i]->inhom)
             return fail(ctxs[i], PF_EUNSUPPORTED,
                         "pf_batch_advance: the Hu-Chen elastic solve reads its convergence on the host per iteration "

@@ -76,6 +76,8 @@ template <typename T>
 struct PhysT {
     T Bv, Bm, inv2Av, inv2Am, A0m, A0v, Am, Av;
     T wb2;    // 2 omega_bar
+    T wb;     // omega_bar
+    int obst; // 1: the literal obstacle barrier omega_bar S (1 - S)
     T ie;     // 1 / pair_eps
     T twoAm;  // 2 A^m
     T w[3][3];
@@ -91,6 +93,7 @@ struct Phys {
     double Am, Av, A0m, A0v, Bm, Bv;
     double inv2Am, inv2Av;  // 1/(2 A^p)
     double L, wbar;
+    int obst;             // 1: the literal obstacle barrier (projection after each step)
     double w[3][3];       // pairwise barrier omega_vq (zero diagonal)
     double pair_eps;      // Huber width of |phi_v phi_q|
     double kap[3][6];     // gradient tensors (Voigt)
@@ -224,6 +227,7 @@ void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamd
 // FP32 table of the elastic kernel B_vq(k)/N (diagonal eigenstrains: B is
 // even in each wave-number component, so |ky| and |kz| index it)
 void launch_btab(const Geo& g, const Phys& ph, float* btab, cudaStream_t s);
+void launch_clamp_phi(double* real, long long N, cudaStream_t s);
 // FP32-bulk stage assembly as a streaming pass (double-float z_i out, FP32
 // transform input W out); the inverse z transform follows as launch_z_pass
 void launch_stage_assemble(const Geo& g, const double2* y, const StageTerms& st, double2* zout, void* W,

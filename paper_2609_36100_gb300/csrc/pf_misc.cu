@@ -266,6 +266,16 @@ void launch_btab(const Geo& g, const Phys& ph, float* btab, cudaStream_t s) {
     k_btab<<<152 * 8, 256, 0, s>>>(g, ph, btab);
 }
 
+// the obstacle barrier's bound: real-space order parameters (fields 1-3 of a
+// [4][N] FP64 array) clamped to [0, 1]
+__global__ void k_clamp_phi(double* __restrict__ real, long long N) {
+    for (long long i = N + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 4 * N;
+         i += (long long)gridDim.x * blockDim.x)
+        real[i] = fmin(1.0, fmax(0.0, real[i]));
+}
+
+void launch_clamp_phi(double* real, long long N, cudaStream_t s) { k_clamp_phi<<<152 * 8, 256, 0, s>>>(real, N); }
+
 void launch_lambda_table(const Geo& g, const Phys& ph, double* lam, float2* lamdf, cudaStream_t s) {
     k_lambda_table<<<152 * 8, 256, 0, s>>>(g, ph, lam, lamdf);
 }

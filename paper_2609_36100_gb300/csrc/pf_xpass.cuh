@@ -42,10 +42,11 @@ struct Pt {
         const T fm = pt.A0m + pt.Am * (Xm - Bm) * (Xm - Bm);
         const T fv = pt.A0v + pt.Av * (Xv - Bv) * (Xv - Bv);
         const T drive = fv - fm - mu * (Xv - Xm);
+        const T dob = pt.wb * ((T)1 - (T)2 * (p[0] + p[1] + p[2]));  // obstacle: d/dphi_v of omega_bar S (1 - S)
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
             const T f = p[v];
-            T d = pt.wb2 * f * ((T)1 - f) * ((T)1 - (T)2 * f);
+            T d = pt.obst ? dob : pt.wb2 * f * ((T)1 - f) * ((T)1 - (T)2 * f);
 #pragma unroll
             for (int qq = 0; qq < 3; ++qq)
                 if (qq != v) {
@@ -358,7 +359,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
                     const double fm = ph.A0m + ph.Am * (Xm - ph.Bm) * (Xm - ph.Bm);
                     const double fv = ph.A0v + ph.Av * (Xv - ph.Bv) * (Xv - ph.Bv);
                     double loc = 0.0;
-                    for (int v = 0; v < 3; ++v) loc += ph.wbar * p[v] * p[v] * (1.0 - p[v]) * (1.0 - p[v]);
+                    if (ph.obst) {
+                        const double S = p[0] + p[1] + p[2];
+                        loc = ph.wbar * S * (1.0 - S);
+                    } else {
+                        for (int v = 0; v < 3; ++v) loc += ph.wbar * p[v] * p[v] * (1.0 - p[v]) * (1.0 - p[v]);
+                    }
                     const double e = ph.pair_eps;
                     const double pr[3] = {p[0] * p[1], p[0] * p[2], p[1] * p[2]};
                     const double wv[3] = {ph.w[0][1], ph.w[0][2], ph.w[1][2]};

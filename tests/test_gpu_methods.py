@@ -162,3 +162,45 @@ def test_unequal_curvature_kks_matches_oracle(pfg, params, prec, tol):
                 s.step(0.5)
             got_y = s.state_hat().cpu().numpy()
             assert np.all(relerr(got_y, ref_y) <= (1e-11 if prec == "fp64" else 1e-5)), (shape, relerr(got_y, ref_y))
+
+
+@pytest.mark.parametrize("prec,tol,stol", [("fp64", 1e-12, 1e-11), ("fp32bulk", 2e-5, 1e-5)])
+def test_obstacle_barrier_matches_oracle(pfg, params, prec, tol, stol):
+    """The literal obstacle term of Eq. f_b (barrier = 1): the explicit
+    right-hand side, then three ARK4 steps, each followed by the projection of
+    the order parameters onto [0, 1] in real space, against the oracle's
+    steps and projections; the composition mean stays exact and the real-space
+    order parameters end inside [0, 1] (to the transforms' rounding)."""
+    import torch
+    p = dict(params, barrier=1)
+    for shape in ((16, 12, 64), (10, 12, 20)):
+        y = synth.random_state(shape, 57)
+        y[1:] = np.clip(1.4 * y[1:] - 0.2, 0.0, 1.0)  # bulk regions at the bounds, where the force pushes out
+        m = oracle.Model(shape, p)
+        yh = m.to_k(y)
+        ref = m.rhs_explicit(yh)
+        with pfg.Simulation(shape, p, "ark4", prec) as s:
+            got = s.rhs_explicit(torch.from_numpy(yh).to("cuda")).cpu().numpy()
+            assert np.all(relerr(got, ref) <= tol), (shape, relerr(got, ref))
+            s.set_state(y)
+            dc = s.state_hat()[0, 0, 0, 0].item()
+            ref_y = yh
+            for _ in range(3):
+                ref_y, _, _ = oracle.ark_step(m, ref_y, 0.25, oracle.ark436l2sa(), p["rtol"], p["atol"])
+                ref_y = m.project(ref_y)
+                s.step(0.25)
+            got_y = s.state_hat().cpu().numpy()
+            assert np.all(relerr(got_y, ref_y) <= stol), (shape, relerr(got_y, ref_y))
+            assert got_y[0, 0, 0, 0] == dc
+            real = s.get_state()
+            assert real[1:].min() >= -1e-12 and real[1:].max() <= 1 + 1e-12
+
+
+def test_batch_refuses_obstacle(pfg, params):
+    p = dict(params, barrier=1)
+    y0 = synth.ic_spheres(16, 2, 2.5, 3.5, 7, p)
+    with pfg.Simulation(y0.shape[1:], p, "ark4", "fp32bulk") as s:
+        s.set_state(y0)
+        with pytest.raises(pfg.PFError) as ei:
+            pfg.batch_advance([s], 2.0)
+        assert ei.value.code == pfg.PF_EUNSUPPORTED
