@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph,
             } else {
                 float q[2], gv[2][3];
 #pragma unroll
-                for (int r = 0; r < 2; ++r) Pt::rhs<float>(pt, Xr[r], pr[r], er[r], q[r], gv[r]);
+                for (int r = 0; r < 2; ++r) Pt::rhs<float, false>(pt, Xr[r], pr[r], er[r], q[r], gv[r]);
                 vout[0][t] = T2{q[0], q[1]};
 #pragma unroll
                 for (int v = 0; v < 3; ++v) vout[1 + v][t] = T2{gv[0][v], gv[1][v]};
@@ -336,7 +336,8 @@ static int launch_x_fused_modes(const Geo& g, const Phys& ph, int mode, const vo
 // returns the number of CTAs launched, 0 if it does not apply
 int launch_x_fused(const Geo& g, const Phys& ph, int mode, const void* in, void* out, void* R, const void* Rin,
                           double* partials, double rtol, double atol, cudaStream_t s) {
-    if (g.xf_off) return 0;
+    // the obstacle barrier runs the staged passes (the fused ones carry only the double well)
+    if (g.xf_off || ph.obst) return 0;
     switch (g.nx) {
         case 64: return launch_x_fused_modes<64>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);
         case 96: return launch_x_fused_modes<96>(g, ph, mode, in, out, R, Rin, partials, rtol, atol, s);

@@ -23,8 +23,10 @@ __device__ __forceinline__ T xdiv(T a, T b) {
 }
 
 struct Pt {
-    // real-space physics at one point (Sec. 4.1); returns q and g_v
-    template <typename T>
+    // real-space physics at one point (Sec. 4.1); returns q and g_v.  OBST:
+    // the literal obstacle barrier instead of the double well (a compile-time
+    // choice, so that the default path carries none of its instructions)
+    template <typename T, bool OBST = false>
     __device__ __forceinline__ static void rhs(const PhysT<T>& pt, T X, const T* p, const T* e, T& q, T* gv) {
         T h[3], hp[3];
 #pragma unroll
@@ -42,11 +44,14 @@ struct Pt {
         const T fm = pt.A0m + pt.Am * (Xm - Bm) * (Xm - Bm);
         const T fv = pt.A0v + pt.Av * (Xv - Bv) * (Xv - Bv);
         const T drive = fv - fm - mu * (Xv - Xm);
-        const T dob = pt.wb * ((T)1 - (T)2 * (p[0] + p[1] + p[2]));  // obstacle: d/dphi_v of omega_bar S (1 - S)
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
             const T f = p[v];
-            T d = pt.obst ? dob : pt.wb2 * f * ((T)1 - f) * ((T)1 - (T)2 * f);
+            T d;
+            if constexpr (OBST)
+                d = pt.wb * ((T)1 - (T)2 * (p[0] + p[1] + p[2]));  // d/dphi_v of omega_bar S (1 - S)
+            else
+                d = pt.wb2 * f * ((T)1 - f) * ((T)1 - (T)2 * f);
 #pragma unroll
             for (int qq = 0; qq < 3; ++qq)
                 if (qq != v) {
@@ -335,7 +340,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_x_pass(Geo
         if (full_rhs) {
             T q[2], gv[2][3];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) Pt::rhs<T>(pt, Xr[r], pr[r], er[r], q[r], gv[r]);
+            for (int r = 0; r < 2; ++r) {
+                if (pt.obst)
+                    Pt::rhs<T, true>(pt, Xr[r], pr[r], er[r], q[r], gv[r]);
+                else
+                    Pt::rhs<T, false>(pt, Xr[r], pr[r], er[r], q[r], gv[r]);
+            }
             OS[(rp * 4 + 0) * ls + skew<true>(x)] = T2{q[0], q[1]};
 #pragma unroll
             for (int v = 0; v < 3; ++v) OS[(rp * 4 + 1 + v) * ls + skew<true>(x)] = T2{gv[0][v], gv[1][v]};

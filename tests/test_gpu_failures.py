@@ -149,3 +149,32 @@ def test_batch_round_cap_times_out_and_resumes(pfg, params, polled):
         assert s.time()[0] == pytest.approx(20.0, rel=1e-14)
         assert np.array_equal(to_np(s.state_hat()), w)
         s.close()
+
+
+def test_checkpoint_resume_with_hu_chen_warm_start(pfg, params):
+    """With the phase-dependent stiffness and its warm start the carried
+    eps(u) is not part of a checkpoint: a resumed context starts its first
+    solve cold.  The resumed run then continues within the elastic
+    tolerance's reach of the uninterrupted one, not bitwise; with el_warm = 0
+    it is bitwise again."""
+    base = dict(params, el_inhom=1, C11_v=1.3 * params["C11"], C12_v=1.1 * params["C12"],
+                C44_v=1.2 * params["C44"], el_tol=1e-8, el_max_iter=100)
+    y0 = synth.ic_spheres(16, 2, 2.5, 3.5, 7, params)
+    for warm in (1, 0):
+        p = dict(base, el_warm=warm)
+        with pfg.Simulation(y0.shape[1:], p, "ark4", "fp64") as a:
+            a.set_state(y0)
+            a.set_time(0.0, 0.5)
+            a.advance(2.0, 1e-4, 1e-8)
+            ck = a.checkpoint()
+            a.advance(4.0, 1e-4, 1e-8)
+            ya = to_np(a.state_hat())
+        with pfg.Simulation(y0.shape[1:], p, "ark4", "fp64") as b:
+            b.restore(ck)
+            b.advance(4.0, 1e-4, 1e-8)
+            yb = to_np(b.state_hat())
+        if warm:
+            d = np.linalg.norm((ya - yb).ravel()) / np.linalg.norm(ya.ravel())
+            assert d <= 1e-6, d
+        else:
+            assert np.array_equal(ya, yb)
