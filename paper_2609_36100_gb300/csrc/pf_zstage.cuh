@@ -16,12 +16,11 @@
 // Step completion (Eq. ARK_method), the embedded local error (Eq.
 // ARK_embedding) and its WRMS norm (Eqs. wrms_norm, wrms_weights) are three
 // more passes; this file holds the two that combine stages (stage assembly
-// and step completion) with the transform fused in.  The library instantiates
-// them for T = double; the FP32-bulk form runs the same combinations as
-// streams (k_stage_assemble_df, k_step_complete_df) followed by an in-place
-// inverse z pass, which keeps the memory stream and the transform apart.  The
-// state is always FP64, the stage vectors FP64 or, in the FP32-bulk form,
-// double-float.
+// and step completion) with the transform fused in, for the FP64 form; the
+// FP32-bulk form runs the same combinations as streams (k_stage_assemble_df,
+// k_step_complete_df) followed by an in-place inverse z pass, which keeps the
+// memory stream and the transform apart.  The state is always FP64, the stage
+// vectors FP64 or, in the FP32-bulk form, double-float.
 #pragma once
 #include "pf_common.cuh"
 
@@ -48,12 +47,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Ge
     const long long base = (long long)f * g.NK + (long long)ky * g.nxh + kx0;
     const long long zs = (long long)g.ny * g.nxh;
     const double kyv = g.ky[ky];
+    static_assert(sizeof(T) == 8, "the FP32-bulk form assembles its stages in k_stage_assemble_df");
     auto src = [&](int kz, int col) -> T2 {
         if (col >= ncol) return T2{0, 0};
         const long long gi = base + kz * zs + col;
-        if constexpr (sizeof(T) == 4) {
-            return stage_value_df<MAXT>(g, st, y, gi, lam_row(g, gi), reinterpret_cast<float4*>(zout));
-        } else {
         // every load first (independent, all in flight together), then the sums
         const double2 yv = __ldg(y + gi);
         const double lam = lam_at(g, ph, f, gi, g.kx[kx0 + col], kyv, g.kz[kz]);
@@ -86,7 +83,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_stage(Ge
         }
         if (zout) zout[gi] = r;
         return r;
-        }
     };
     auto dst = [&](int kz, int col, T2 v) {
         if (col < ncol) W[base + kz * zs + col] = v;
@@ -132,12 +128,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_final(Ge
     const long long base = (long long)f * g.NK + (long long)ky * g.nxh + kx0;
     const long long zs = (long long)g.ny * g.nxh;
     const double kyv = g.ky[ky];
+    static_assert(sizeof(T) == 8, "the FP32-bulk form completes its steps in k_step_complete_df");
     auto combine = [&](int kz, int col) -> T2 {
         if (col >= ncol) return T2{0, 0};
         const long long gi = base + kz * zs + col;
-        if constexpr (sizeof(T) == 4) {
-            return final_value_df(g, bt, dt, want_lte, y, gi, lam_row(g, gi), ynew);
-        } else {
         const unsigned lmI = want_lte ? dt.mI : 0u, lmE = want_lte ? dt.mE : 0u;
         const unsigned mI = bt.mI | lmI, mE = bt.mE | lmE, mz = mI & ~bt.mY;
         // every load first, then the sums
@@ -169,7 +163,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_z_final(Ge
         axpy(l, lam, zl);
         ynew[gi] = r;
         return l;
-        }
     };
     if (!want_lte) {
         for (int e = threadIdx.x; e < TX * g.nz; e += blockDim.x) combine(e / TX, e & (TX - 1));
