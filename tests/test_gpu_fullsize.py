@@ -91,3 +91,36 @@ def test_bench_workload_to_end_time(pfg, params):
     err = relerr(a, b)
     print("FP32-bulk vs FP64 at t = 60 s, rel L2 per field:", err)
     assert np.all(err <= 2e-5), err
+
+
+def test_largest_grid_first_step(pfg, params):
+    """The largest single-GPU workload (640^3, 300 seeded spheres of radius
+    4-12 cells), FP32-bulk in the bench's launch configuration (autotuned)
+    against the FP64 path, one ARK4 step of h = 1 s from the same state.  The
+    oracle cannot hold this grid, so the check is through properties that
+    hold at any size and the FP64 path (pinned to the oracle elsewhere): the
+    two forms agree to 1e-5 rel L2 per field, their error norms to 1e-3, the
+    composition mean is exact in both, and the free energy falls."""
+    import torch
+    n = 640
+    y0 = torch.from_numpy(synth.ic_spheres_300(n, 5, params)).to("cuda")
+    res = {}
+    for prec in ("fp32bulk", "fp64"):
+        with pfg.Simulation((n, n, n), params, "ark4", prec) as s:
+            s.set_state(y0)
+            if prec == "fp32bulk":
+                s.autotune(reps=1)
+                s.set_state(y0)
+            dc = s.state_hat()[0, 0, 0, 0].item()
+            f0 = s.free_energy()
+            e = s.step(1.0)
+            yh = s.state_hat()
+            assert yh[0, 0, 0, 0].item() == dc
+            assert s.free_energy() < f0
+            res[prec] = (yh, e)
+        torch.cuda.synchronize()
+    (a, ea), (b, eb) = res["fp32bulk"], res["fp64"]
+    err = [(torch.linalg.vector_norm(a[f] - b[f]) / torch.linalg.vector_norm(b[f])).item() for f in range(4)]
+    print("640^3 first step, FP32-bulk vs FP64 rel L2 per field:", err, "LTE", ea, eb)
+    assert max(err) <= 1e-5, err
+    assert abs(ea - eb) <= 1e-3 * max(1.0, abs(eb))
