@@ -260,10 +260,11 @@ const char* pf_kernel_name(int kind);
  * fused one (int 39) and whether the compiled-plan elastic pass runs each
  * transform stage and the contraction over the three fields in place instead
  * of fusing the last forward and first inverse stage in registers (int 40)
- * and whether the FP32 fused x pass of the right-hand side copies its stored
- * real fields into shared memory with its input rows (int 41).
+ * whether the FP32 fused x pass of the right-hand side copies its stored
+ * real fields into shared memory with its input rows (int 41) and whether the
+ * FP32 fused x passes run every stage in place in one shared buffer (int 42).
  * PF_TUNE_LEN ints. */
-#define PF_TUNE_LEN 42
+#define PF_TUNE_LEN 43
 int pf_get_tuning(pf_ctx* ctx, int* cfg, int n);
 int pf_set_tuning(pf_ctx* ctx, const int* cfg, int n);
 /* Autotuner: times `reps` step attempts per candidate schedule on the

@@ -112,7 +112,7 @@ SIGNATURES = {
                                     C.POINTER(C.c_double)]),
 }
 NKERNELS = 11
-TUNE_LEN = 42
+TUNE_LEN = 43
 _DPTR_ARGS = {"pf_method_tableau"}
 
 _lib = None

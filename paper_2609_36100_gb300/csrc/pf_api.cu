@@ -1646,6 +1646,7 @@ int pf_get_tuning(pf_ctx* c, int* cfg, int n) {
     cfg[39] = c->g.xf_off;
     cfg[40] = c->g.el_unfused;
     cfg[41] = c->g.xf_stg;
+    cfg[42] = c->g.xf_inpl;
     plan_to_cfg(c->g.px, cfg + 4);
     plan_to_cfg(c->g.py, cfg + 4 + 11);
     plan_to_cfg(c->g.pz, cfg + 4 + 22);
@@ -1667,6 +1668,7 @@ int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
     g.xf_off = cfg[39] != 0;
     g.el_unfused = cfg[40] != 0;
     g.xf_stg = cfg[41] != 0;
+    g.xf_inpl = cfg[42] != 0;
     AxisPlan* pl[3] = {&g.px, &g.py, &g.pz};
     const int ns[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
@@ -1783,6 +1785,13 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
             cfg[39] = v;
             trial(cfg);
         }
+        // fused x passes with two shared buffers or one (in place)
+        if (c->fp32)
+            for (int v : {0, 1}) {
+                std::memcpy(cfg, best, sizeof cfg);
+                cfg[42] = v;
+                trial(cfg);
+            }
         // real fields of the right-hand-side x pass read from global or staged
         if (c->fp32 && c->ph.elastic)
             for (int v : {0, 1}) {

@@ -61,6 +61,7 @@ struct Geo {
     int el_pid;              // compiled plan of the fused elastic pass (length nz), 0 = the z-axis plan,
                              // -1 = no fused stage (the one-kernel pass with the z-axis column transforms)
     int xf_off;              // 1: the FP32 x passes use the staged kernel instead of the fused one
+    int xf_inpl;             // 1: the FP32 fused x passes run every stage in one shared buffer (in place)
     int xf_stg;              // 1: the FP32 fused right-hand-side x pass stages the stored real fields in shared memory
     int el_unfused;          // 1: the compiled-plan elastic pass runs every stage (and the contraction) over the
                              // three fields in place instead of fusing the last forward / first inverse stage

@@ -44,6 +44,48 @@ __device__ __forceinline__ void xf_run(T2*& cur, T2*& oth, int nl, const T2* tw,
     xf_run<SIGN, N, NS * R>(cur, oth, nl, tw, Radices<Rest...>{});
 }
 
+// In-place stage of NL skewed lines (one shared buffer): every job's R
+// inputs are loaded into registers, the CTA synchronises, then the
+// butterflies are formed and stored, and the CTA synchronises again.
+template <int R, int SIGN, int N, int NS, int NL, int NT, typename T2>
+__device__ __forceinline__ void xf_stage_inplace(T2* S, const T2* __restrict__ tw) {
+    constexpr int M = N / R, TWS = N / (NS * R), JOBS = NL * M, JPT = (JOBS + NT - 1) / NT, LS = N + N / 16;
+    T2 v[JPT][R];
+#pragma unroll
+    for (int u = 0; u < JPT; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        if (JOBS % NT == 0 || idx < JOBS) {
+            const int line = idx / M, j = idx - line * M;
+            const T2* s = S + line * LS;
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[u][t] = s[skew<true>(j + t * M)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < JPT; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        if (JOBS % NT == 0 || idx < JOBS) {
+            const int line = idx / M, j = idx - line * M;
+            const int jq = j / NS, k = j - jq * NS;
+            if constexpr (NS > 1) apply_twiddles<R, SIGN>(v[u], tw, k * TWS);
+            Bfly<R, SIGN, T2>::run(v[u]);
+            T2* d = S + line * LS;
+            const int a = jq * NS * R;
+#pragma unroll
+            for (int t = 0; t < R; ++t) d[skew<true>(a + k + t * NS)] = v[u][t];
+        }
+    }
+    __syncthreads();
+}
+template <int SIGN, int N, int NS, int NL, int NT, typename T2>
+__device__ __forceinline__ void xf_run_inplace(T2*, const T2*, Radices<>) {}
+template <int SIGN, int N, int NS, int NL, int NT, typename T2, int R, int... Rest>
+__device__ __forceinline__ void xf_run_inplace(T2* S, const T2* tw, Radices<R, Rest...>) {
+    xf_stage_inplace<R, SIGN, N, NS, NL, NT>(S, tw);
+    xf_run_inplace<SIGN, N, NS * R, NL, NT>(S, tw, Radices<Rest...>{});
+}
+
 template <class Fwd, int P>
 struct XFShape {
     static constexpr int N = RadProd<Fwd>::value;
@@ -54,8 +96,15 @@ struct XFShape {
     static constexpr int LS = N + N / 16;            // skewed line stride
 };
 
-template <typename T, class Fwd, int P, int MODE>
-__global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph, const float2* __restrict__ in,
+// INPL: one shared buffer, every stage in place (half the shared memory, so
+// more CTAs per SM, for a barrier more per stage); registers bounded to 64 a
+// thread so that the registers do not cap the CTAs per SM first
+template <typename T, class Fwd, int P, int MODE, bool INPL>
+__global__ void __launch_bounds__(XFShape<Fwd, P>::NT, INPL ? (65536 / (XFShape<Fwd, P>::NT * 64) > 0
+                                                                     ? 65536 / (XFShape<Fwd, P>::NT * 64)
+                                                                     : 1)
+                                                              : 1)
+    k_x_fused(Geo g, Phys ph, const float2* __restrict__ in,
                                                                   float2* __restrict__ out, float* __restrict__ R,
                                                                   const float* __restrict__ Rin,
                                                                   double* __restrict__ partials, float rt, float at) {
@@ -68,7 +117,7 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph,
     constexpr int R1 = RadInfo<Inv>::first;  // first inverse stage
     extern __shared__ __align__(16) unsigned char smraw[];
     T2* A = reinterpret_cast<T2*>(smraw);
-    T2* B = A + P * 4 * LS;
+    T2* B = INPL ? A : A + P * 4 * LS;
     const int npairs = g.nz * g.ny / 2;
     const int rp0 = blockIdx.x * P;
     const long long NK = g.NK, N3 = g.N;
@@ -102,14 +151,13 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph,
     __syncthreads();
     // 2. first inverse stage (radix R1, no twiddles), packing Z = a + i b of
     //    the two rows' half spectra (Hermitian extension, imaginary parts of
-    //    DC and Nyquist dropped): B -> A
+    //    DC and Nyquist dropped): B -> A (in place: all loads, a barrier, the stores)
     {
-        constexpr int M1 = N / R1;
-        for (int idx = threadIdx.x; idx < P * FIN * M1; idx += NT) {
+        constexpr int M1 = N / R1, JOBS = P * FIN * M1, JPT = INPL ? (JOBS + NT - 1) / NT : 1;
+        auto load = [&](int idx, T2* v) {
             const int line = idx / M1, j = idx - line * M1;
             const T2* ra = B + line * 2 * NXH;
             const T2* rb = ra + NXH;
-            T2 v[R1];
 #pragma unroll
             for (int t = 0; t < R1; ++t) {
                 const int x = j + t * M1;
@@ -122,17 +170,39 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph,
                 }
                 v[t] = lo ? T2{a.x - b.y, a.y + b.x} : T2{a.x + b.y, b.x - a.y};
             }
+        };
+        auto store = [&](int idx, T2* v) {
+            const int line = idx / M1, j = idx - line * M1;
             Bfly<R1, +1, T2>::run(v);
             T2* d = A + line * LS;
 #pragma unroll
             for (int t = 0; t < R1; ++t) d[skew<true>(j * R1 + t)] = v[t];
+        };
+        if constexpr (INPL) {
+            T2 v[JPT][R1];
+#pragma unroll
+            for (int u = 0; u < JPT; ++u)
+                if (JOBS % NT == 0 || threadIdx.x + u * NT < JOBS) load(threadIdx.x + u * NT, v[u]);
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < JPT; ++u)
+                if (JOBS % NT == 0 || threadIdx.x + u * NT < JOBS) store(threadIdx.x + u * NT, v[u]);
+        } else {
+            for (int idx = threadIdx.x; idx < JOBS; idx += NT) {
+                T2 v[R1];
+                load(idx, v);
+                store(idx, v);
+            }
         }
     }
     __syncthreads();
     T2* cur = A;
     T2* oth = B;
     // 3. inverse stages between the first and the last
-    xf_run<+1, N, R1>(cur, oth, P * FIN, tw, typename PlanInner<Inv>::type{});
+    if constexpr (INPL)
+        xf_run_inplace<+1, N, R1, P * FIN, NT>(cur, tw, typename PlanInner<Inv>::type{});
+    else
+        xf_run<+1, N, R1>(cur, oth, P * FIN, tw, typename PlanInner<Inv>::type{});
     // 4. fused: last inverse stage, physics, first forward stage
     const int rp = threadIdx.x / M, j = threadIdx.x - (threadIdx.x / M) * M;
     const bool valid = rp0 + rp < npairs;
@@ -241,6 +311,7 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph,
                 for (int v = 0; v < 3; ++v) vout[1 + v][t] = T2{gv[0][v], gv[1][v]};
             }
         }
+        if constexpr (INPL) __syncthreads();  // every input of the fused stage read before the stores
 #pragma unroll
         for (int f = 0; f < FOUT; ++f) {
             Bfly<RM, -1, T2>::run(vout[f]);  // first forward stage: NS = 1, no twiddles
@@ -255,7 +326,10 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT) k_x_fused(Geo g, Phys ph,
             oth = t;
         }
         // 5. the remaining forward stages
-        xf_run<-1, N, RM>(cur, oth, P * FOUT, tw, typename DropFirst<Fwd>::type{});
+        if constexpr (INPL)
+            xf_run_inplace<-1, N, RM, P * FOUT, NT>(cur, tw, typename DropFirst<Fwd>::type{});
+        else
+            xf_run<-1, N, RM>(cur, oth, P * FOUT, tw, typename DropFirst<Fwd>::type{});
         // 6. R2C unpacking of the two rows of each line and the store
         for (int e = threadIdx.x; e < P * FOUT * NXH; e += NT) {
             const int line = e / NXH, k = e - line * NXH, lrp = line / FOUT, f = line - lrp * FOUT;
@@ -295,21 +369,28 @@ PF_XF_PLAN(256, 4, 4, 16, 4)
 PF_XF_PLAN(640, 2, 5, 16, 8)
 #undef PF_XF_PLAN
 
-template <int N, int MODE>
-static int launch_x_fused_n(const Geo& g, const Phys& ph, const void* in, void* out, void* R, const void* Rin,
+template <int N, int MODE, bool INPL>
+static int launch_x_fused_k(const Geo& g, const Phys& ph, const void* in, void* out, void* R, const void* Rin,
                             double* partials, double rtol, double atol, cudaStream_t s) {
     using Pl = XFPlan<N>;
     using Sh = XFShape<typename Pl::Fwd, Pl::P>;
-    const size_t sm = 2 * (size_t)Pl::P * 4 * Sh::LS * sizeof(float2) +
+    const size_t sm = (INPL ? 1 : 2) * (size_t)Pl::P * 4 * Sh::LS * sizeof(float2) +
                       (MODE == XF_PHYS2_STG ? (size_t)Pl::P * 8 * N * sizeof(float) : 0);
     const int npairs = g.nz * g.ny / 2;
     const int nb = (npairs + Pl::P - 1) / Pl::P;
-    auto k = k_x_fused<float, typename Pl::Fwd, Pl::P, MODE>;
+    auto k = k_x_fused<float, typename Pl::Fwd, Pl::P, MODE, INPL>;
     set_smem(k, sm);
     k<<<nb, Sh::NT, sm, s>>>(g, ph, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out),
                              reinterpret_cast<float*>(R), reinterpret_cast<const float*>(Rin), partials, (float)rtol,
                              (float)atol);
     return nb;
+}
+
+template <int N, int MODE>
+static int launch_x_fused_n(const Geo& g, const Phys& ph, const void* in, void* out, void* R, const void* Rin,
+                            double* partials, double rtol, double atol, cudaStream_t s) {
+    return g.xf_inpl ? launch_x_fused_k<N, MODE, true>(g, ph, in, out, R, Rin, partials, rtol, atol, s)
+                     : launch_x_fused_k<N, MODE, false>(g, ph, in, out, R, Rin, partials, rtol, atol, s);
 }
 
 template <int N>

@@ -2,8 +2,9 @@
 forward stage in registers; C2R packing folded into the first inverse stage,
 R2C unpacking into the store) against the FP64 oracle, for every line length
 that has a fused plan, on grids whose row-pair count leaves a ragged last CTA;
-the staged kernel (tuning slot 39) and the right-hand-side pass with its
-real fields copied into shared memory (slot 41) must agree as well."""
+the staged kernel (tuning slot 39), the right-hand-side pass with its real
+fields copied into shared memory (slot 41) and the passes with every stage in
+place in one buffer (slot 42) must agree as well."""
 import numpy as np
 import pytest
 
@@ -41,14 +42,15 @@ def test_fused_x_rhs_matches_oracle(pfg, params, nx, elastic):
     ref = m.rhs_explicit(yh)
     dev = torch.from_numpy(yh).to("cuda")
     with pfg.Simulation(shape, p, "ark4", "fp32bulk") as s:
-        for off, stg in ((0, 0), (0, 1), (1, 0)):
+        for off, stg, inpl in ((0, 0, 0), (0, 1, 0), (0, 0, 1), (0, 1, 1), (1, 0, 0)):
             cfg = s.tuning()
             cfg[39] = off
             cfg[41] = stg
+            cfg[42] = inpl
             s.set_tuning(cfg)
             got = s.rhs_explicit(dev).cpu().numpy()
             err = relerr(got, ref)
-            assert np.all(err <= 2e-5), (off, stg, err)
+            assert np.all(err <= 2e-5), (off, stg, inpl, err)
 
 
 @pytest.mark.parametrize("nx", [96, 256, 640])
@@ -60,9 +62,13 @@ def test_fused_x_step_and_error_norm(pfg, params, nx):
     y = synth.random_state(shape, 70 + nx, phi_scale=0.9)
     m = oracle.Model(shape, params)
     yh, e_ref, _ = oracle.ark_step(m, m.to_k(y), 0.5, oracle.ark436l2sa(), params["rtol"], params["atol"])
-    with pfg.Simulation(shape, params, "ark4", "fp32bulk") as s:
-        s.set_state(y)
-        e = s.step(0.5)
-        got = s.state_hat().cpu().numpy()
-    assert np.all(relerr(got, yh) <= 1e-5)
-    assert abs(e - e_ref) <= 1e-3 * e_ref, (e, e_ref)
+    for inpl in (0, 1):
+        with pfg.Simulation(shape, params, "ark4", "fp32bulk") as s:
+            cfg = s.tuning()
+            cfg[42] = inpl
+            s.set_tuning(cfg)
+            s.set_state(y)
+            e = s.step(0.5)
+            got = s.state_hat().cpu().numpy()
+        assert np.all(relerr(got, yh) <= 1e-5)
+        assert abs(e - e_ref) <= 1e-3 * e_ref, (inpl, e, e_ref)
