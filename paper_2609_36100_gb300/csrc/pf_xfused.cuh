@@ -124,14 +124,32 @@ __global__ void __launch_bounds__(XFShape<Fwd, P>::NT, INPL ? (65536 / (XFShape<
     const T2* tw = g.px.tw32;
     __shared__ double red[NT / 32 + 1];
 
-    // 1. the raw half-spectrum rows of the input fields -> B (cp.async)
-    for (int e = threadIdx.x; e < P * FIN * 2 * NXH; e += NT) {
-        const int r = e / NXH, k = e - r * NXH;  // raw row r = (rp FIN + f) 2 + (0: row y, 1: row y+1)
-        const int pf = r >> 1, rp = pf / FIN, f = pf - rp * FIN;
-        if (rp0 + rp < npairs)
-            cp_async<8>(B + e, in + (long long)f * NK + (2LL * (rp0 + rp) + (r & 1)) * NXH + k);
-        else
-            B[e] = T2{0.f, 0.f};
+    // 1. the raw half-spectrum rows of the input fields -> B (cp.async).  Raw
+    //    row r = (rp FIN + f) 2 + (0: row y, 1: row y+1) goes to B + r NXH.
+    //    NXH is odd and NK even, so row r starts 16-byte aligned in global and
+    //    shared memory alike when r is even and one element later when r is
+    //    odd: each row is NXH/2 16-byte copies from its first aligned element
+    //    and one 8-byte copy of the element left over (the last or the first)
+    {
+        static_assert(NXH % 2 == 1, "odd half-spectrum rows");
+        constexpr int NC = NXH / 2 + 1;  // copies per row: NXH/2 pairs and one single
+        for (int e = threadIdx.x; e < P * FIN * 2 * NC; e += NT) {
+            const int r = e / NC, c = e - r * NC;
+            const int pf = r >> 1, rp = pf / FIN, f = pf - rp * FIN;
+            const int head = r & 1;  // first element of the aligned pairs
+            const int k = c < NXH / 2 ? head + 2 * c : (head ? 0 : NXH - 1);
+            T2* dst = B + r * NXH + k;
+            if (rp0 + rp < npairs) {
+                const T2* src = in + (long long)f * NK + (2LL * (rp0 + rp) + head) * NXH + k;
+                if (c < NXH / 2)
+                    cp_async<16>(dst, src);
+                else
+                    cp_async<8>(dst, src);
+            } else {
+                dst[0] = T2{0.f, 0.f};
+                if (c < NXH / 2) dst[1] = T2{0.f, 0.f};
+            }
+        }
     }
     // the real fields X, phi_v of the CTA's rows -> C ([row pair][field][2 rows][N]), 16-byte copies
     constexpr bool STG = MODE == XF_PHYS2_STG;
