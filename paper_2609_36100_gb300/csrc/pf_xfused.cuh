@@ -57,8 +57,15 @@ __device__ __forceinline__ void xf_stage_inplace(T2* S, const T2* __restrict__ t
         if (JOBS % NT == 0 || idx < JOBS) {
             const int line = idx / M, j = idx - line * M;
             const T2* s = S + line * LS;
+            if constexpr (M % 16 == 0) {
+                // skew(j + t M) = skew(j) + t (M + M/16)
+                const T2* sj = s + skew<true>(j);
 #pragma unroll
-            for (int t = 0; t < R; ++t) v[u][t] = s[skew<true>(j + t * M)];
+                for (int t = 0; t < R; ++t) v[u][t] = sj[t * (M + M / 16)];
+            } else {
+#pragma unroll
+                for (int t = 0; t < R; ++t) v[u][t] = s[skew<true>(j + t * M)];
+            }
         }
     }
     __syncthreads();
@@ -71,9 +78,25 @@ __device__ __forceinline__ void xf_stage_inplace(T2* S, const T2* __restrict__ t
             if constexpr (NS > 1) apply_twiddles<R, SIGN>(v[u], tw, k * TWS);
             Bfly<R, SIGN, T2>::run(v[u]);
             T2* d = S + line * LS;
-            const int a = jq * NS * R;
+            const int a = jq * NS * R;  // outputs at a + k + t NS
+            if constexpr ((NS * R) % 16 == 0 && NS % 16 == 0) {
+                T2* dk = d + skew<true>(a) + skew<true>(k);
 #pragma unroll
-            for (int t = 0; t < R; ++t) d[skew<true>(a + k + t * NS)] = v[u][t];
+                for (int t = 0; t < R; ++t) dk[t * (NS + NS / 16)] = v[u][t];
+            } else if constexpr ((NS * R) % 16 == 0 && 16 % NS == 0) {
+                // k + t NS crosses a 16-block boundary only at multiples of 16
+                T2* dk = d + skew<true>(a) + k;
+#pragma unroll
+                for (int t = 0; t < R; ++t) dk[t * NS + ((t * NS) >> 4)] = v[u][t];
+            } else if constexpr (NS == 1 && 16 % R == 0) {
+                // a = j R and a + t stay inside one 16-block
+                T2* dk = d + skew<true>(a);
+#pragma unroll
+                for (int t = 0; t < R; ++t) dk[t] = v[u][t];
+            } else {
+#pragma unroll
+                for (int t = 0; t < R; ++t) d[skew<true>(a + k + t * NS)] = v[u][t];
+            }
         }
     }
     __syncthreads();
