@@ -511,7 +511,7 @@ def run_surrogate(ntraj, n=128, dt=1.0, nsnap=25, epochs=1):
     8-ellipsoid recipe scaled to n^3 (8 nuclei; ARK4 FP32-bulk, dt = 1 s,
     snapshots every tau = 8 s, 0-200 s), then rollouts of two held-out seeds
     to 200 s in windows of tau: each window proposed by the network and
-    judged by the method's own adaptive integration of the window (rtol
+    checked by the method's own adaptive integration of the window (rtol
     1e-4), against plain adaptive integration; final-state errors against an
     FP64 rtol 1e-8 reference."""
     import numpy as np
@@ -553,7 +553,7 @@ def run_surrogate(ntraj, n=128, dt=1.0, nsnap=25, epochs=1):
             "data_s": t_data, "train_s": t_train, "train_ms_per_pair": t_train / pairs * 1e3, "tau_s": tau,
             "t_end_s": t_end, "rollouts": rows,
             "wall_ratio_plain_over_surrogate": float(np.mean([r["wall_plain_s"] / r["wall_surrogate_s"] for r in rows])),
-            "judge": "the method integrates every window itself; a proposal counts as accepted when its WRMS "
+            "acceptance": "the method integrates every window itself; a proposal counts as accepted when its WRMS "
                      "distance to that verified state is <= 1, and the rollout always continues from the verified "
                      "state"}
 

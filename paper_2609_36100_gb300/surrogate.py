@@ -1,6 +1,6 @@
 """Surrogate workflow: trajectories from the solver, FNO training with the
 library's kernels, and surrogate-assisted integration with the integrator as
-judge.
+verifier.
 
 Everything numerical runs in libpf.so; this module only orchestrates calls.
 Training data are pairs (y(t), y(t + tau)) of real-space states taken every
@@ -65,7 +65,7 @@ def rollout(y0, params, t_end, tau, net=None, precision="fp32bulk", rtol=1e-4, a
     """Integrate to t_end adaptively (ARK4, rtol/atol).  Without a network:
     one pf_advance.  With a network: window by window of length tau, each
     window first proposed by the network and then integrated by the method,
-    which judges the proposal (accepted when its WRMS distance to the
+    which checks the proposal (accepted when its WRMS distance to the
     verified state is <= 1); the state always continues from the verified
     integration.  Returns (final real-space state, wall seconds, accepted,
     offered, proposal distances)."""
