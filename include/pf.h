@@ -257,10 +257,12 @@ const char* pf_kernel_name(int kind);
  * z pass (int 37), the compiled radix plan of the elastic pass (int 38;
  * 0 = the z axis's own plan, -1 = no compiled elastic plan: the z axis's
  * column transforms, one field after another), whether the FP32 x passes run the staged kernel instead of the
- * fused one (int 39) and whether the compiled-plan elastic pass runs each
- * transform stage and the contraction over the three fields in place instead
- * of fusing the last forward and first inverse stage in registers (int 40)
- * whether the FP32 fused x pass of the right-hand side copies its stored
+ * fused one (int 39), the form of the compiled-plan elastic pass (int 40:
+ * 0 fuses the last forward and first inverse stage in registers, 1 runs each
+ * transform stage and the contraction over the three fields in place, 2 runs
+ * a cluster of three CTAs, one h field each, sharing the contraction through
+ * distributed shared memory; FP32 contexts, FP64 contexts run 0 for 2;
+ * other values are refused with PF_EINVAL), whether the FP32 fused x pass of the right-hand side copies its stored
  * real fields into shared memory with its input rows (int 41) and whether the
  * FP32 fused x passes run every stage in place in one shared buffer (int 42).
  * PF_TUNE_LEN ints. */

@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpf.so")
 SOURCES = ["pf_zelastic.cu", "pf_zfwd.cu", "pf_ypass.cu", "pf_xpass_f32.cu", "pf_xpass_f64.cu",
            "pf_zfinal_f64.cu", "pf_zstage_f64.cu", "pf_fno.cu", "pf_api.cu", "pf_misc.cu",
-           "pf_plan.cu", "pf_noalloc.cu", "pf_hc.cu", "pf_zelastic_unf.cu"]
+           "pf_plan.cu", "pf_noalloc.cu", "pf_hc.cu", "pf_zelastic_unf.cu",
+           "pf_zelastic_cl.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

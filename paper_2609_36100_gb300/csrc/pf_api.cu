@@ -949,12 +949,13 @@ int pf_create(const pf_grid* grid, const pf_params* params, void* cuda_stream, p
     rc = rc ? rc : dalloc(c, &c->lam, nk4 * sizeof(double));
     if (c->fp32) rc = rc ? rc : dalloc(c, &c->lamdf, nk4 * sizeof(float2));
     // elastic-kernel table: FP32-bulk, homogeneous modulus, diagonal
-    // eigenstrains (B even in each wave-number component), at most 256 MB
+    // eigenstrains (B even in each wave-number component), at most 1 GB (794 MB
+    // at 640^3)
     bool diag = true;
     for (int v = 0; v < 3; ++v)
         for (int a = 3; a < 6; ++a) diag = diag && params->eps_star[v][a] == 0.0;
     const long long tabn = (long long)(g.nz / 2 + 1) * (g.ny / 2 + 1) * g.nxh;
-    if (c->fp32 && c->ph.elastic && !c->inhom && diag && 6 * tabn * (long long)sizeof(float) <= (256LL << 20))
+    if (c->fp32 && c->ph.elastic && !c->inhom && diag && 6 * tabn * (long long)sizeof(float) <= (1LL << 30))
         rc = rc ? rc : dalloc(c, &c->btab, 6 * (size_t)tabn * sizeof(float));
     rc = rc ? rc : dalloc(c, &c->qtab, nk4 * sizeof(double));
     if (params->barrier == 1) rc = rc ? rc : dalloc(c, &c->xsave, (size_t)g.NK * sizeof(double2));
@@ -1666,7 +1667,8 @@ int pf_set_tuning(pf_ctx* c, const int* cfg, int n) {
         return fail(c, PF_EINVAL, "pf_set_tuning: elastic plan %d does not have length nz", cfg[38]);
     g.el_pid = cfg[38];
     g.xf_off = cfg[39] != 0;
-    g.el_unfused = cfg[40] != 0;
+    if (cfg[40] < 0 || cfg[40] > 2) return fail(c, PF_EINVAL, "pf_set_tuning: bad elastic form %d", cfg[40]);
+    g.el_unfused = cfg[40];
     g.xf_stg = cfg[41] != 0;
     g.xf_inpl = cfg[42] != 0;
     AxisPlan* pl[3] = {&g.px, &g.py, &g.pz};
@@ -1799,9 +1801,11 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
                 cfg[41] = v;
                 trial(cfg);
             }
-        // elastic pass with the fused stage or with every stage over the three fields
+        // elastic pass with the fused stage, with every stage over the three
+        // fields, or as a three-CTA cluster (FP32)
         if (c->ph.elastic && !c->inhom)
-            for (int v : {0, 1}) {
+            for (int v : {0, 1, 2}) {
+                if (v == 2 && !c->fp32) continue;
                 std::memcpy(cfg, best, sizeof cfg);
                 cfg[40] = v;
                 trial(cfg);

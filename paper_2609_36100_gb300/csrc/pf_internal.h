@@ -63,8 +63,9 @@ struct Geo {
     int xf_off;              // 1: the FP32 x passes use the staged kernel instead of the fused one
     int xf_inpl;             // 1: the FP32 fused x passes run every stage in one shared buffer (in place)
     int xf_stg;              // 1: the FP32 fused right-hand-side x pass stages the stored real fields in shared memory
-    int el_unfused;          // 1: the compiled-plan elastic pass runs every stage (and the contraction) over the
-                             // three fields in place instead of fusing the last forward / first inverse stage
+    int el_unfused;          // form of the compiled-plan elastic pass: 0 fuses the last forward / first inverse
+                             // stage, 1 runs every stage (and the contraction) over the three fields in place,
+                             // 2 runs a cluster of three CTAs, one field each (FP32 contexts)
     const float* btab;       // FP32 elastic kernel B(k) / N over kx >= 0, |ky| <= ny/2, |kz| <= nz/2 (six
                              // symmetric entries, [6][nz/2+1][ny/2+1][nx/2+1]), or null: computed per k
 };
@@ -210,6 +211,10 @@ template <typename T>
 void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s);
 template <typename T>
 bool launch_z_elastic_unfused(const Geo& g, const Phys& ph, void* H, int pid, cudaStream_t s);
+// the three-CTA cluster form (one h field per CTA); false where it does not
+// apply (FP64 contexts, plans of one stage, tiles over 200 KB)
+template <typename T>
+bool launch_z_elastic_cluster(const Geo& g, const Phys& ph, void* H, int pid, cudaStream_t s);
 // forward z FFT; scale_mode 0: y = W/N to FP64 (set_state); 1: f^E scaling
 // into the compute type; 2: f^E scaling into FP64 (ABI output)
 template <typename T>

@@ -566,7 +566,8 @@ void launch_z_elastic(const Geo& g, const Phys& ph, void* H, cudaStream_t s) {
     // axis (no fused stage), also where a compiled plan exists
     if (g.el_pid >= 0 && g.pz.n == g.nz && g.nz >= 32) {
         const int pid = (g.el_pid > 0 && fixed_plan_len(g.el_pid) == g.nz) ? g.el_pid : fixed_plan_id(g.pz);
-        if (g.el_unfused && launch_z_elastic_unfused<T>(g, ph, H, pid, s)) return;
+        if (g.el_unfused == 2 && launch_z_elastic_cluster<T>(g, ph, H, pid, s)) return;
+        if (g.el_unfused == 1 && launch_z_elastic_unfused<T>(g, ph, H, pid, s)) return;
         switch (pid) {
             case 1: done = launch_z_elastic_fused<T, 1>(g, ph, H, g.tx_el, s); break;
             case 2: done = launch_z_elastic_fused<T, 2>(g, ph, H, g.tx_el, s); break;

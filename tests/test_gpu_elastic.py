@@ -1,9 +1,11 @@
 """The fused elastic pass (last forward z stage, Green's contraction of
 Eq. u_gov and first inverse stage in registers; the inverse runs the forward
-radix order reversed) and its form without a fused stage (every stage over
-the three fields in place, tuning slot 40) against the FP64 oracle's explicit
-right-hand side, for every compiled radix plan of each length and every tile
-width, on grids whose half-spectrum rows leave a ragged last tile."""
+radix order reversed), its form without a fused stage (every stage over the
+three fields in place) and its three-CTA cluster form (one h field per CTA,
+the contraction through distributed shared memory; tuning slot 40 = 0, 1, 2)
+against the FP64 oracle's explicit right-hand side, for every compiled radix
+plan of each length and every tile width, on grids whose half-spectrum rows
+leave a ragged last tile."""
 import numpy as np
 import pytest
 
@@ -43,7 +45,7 @@ def test_fused_elastic_plan_matches_oracle(pfg, params, pid, prec, tol):
     dev = torch.from_numpy(yh).to("cuda")
     with pfg.Simulation(shape, params, "ark4", prec) as s:
         for tx in (2, 4, 8, 16):
-            for unfused in (0, 1):
+            for unfused in (0, 1, 2):
                 cfg = s.tuning()
                 cfg[2] = tx
                 cfg[38] = pid
@@ -74,6 +76,48 @@ def test_generic_elastic_pass_selectable(pfg, params, prec, tol):
         assert s.tuning()[38] == -1
         got = s.rhs_explicit(dev).cpu().numpy()
         assert np.all(relerr(got, ref) <= tol)
+
+
+@pytest.mark.parametrize("shape", [(256, 10, 40), (64, 18, 90), (640, 6, 36)])
+@pytest.mark.parametrize("shear", [False, True])
+def test_cluster_elastic_pass(pfg, shape, shear):
+    """The cluster form over several ky rows (the launch order pairs ky with
+    ny - ky), several column tiles with a ragged last one, and 640-point
+    columns.  With
+    diagonal eigenstrains it reads B(k)/N from the octant table; with a shear
+    component the kernel is no longer even in each wave-number component, no
+    table is built and every wave number forms B itself."""
+    import torch
+    e = [[0.004, 0.004, 0.02, 0.0, 0.0, 0.0], [0.004, 0.02, 0.004, 0.0, 0.0, 0.0],
+         [0.02, 0.004, 0.004, 0.0, 0.0, 0.0]]
+    if shear:
+        e[0][5] = 0.003
+        e[2][3] = -0.002
+    p = synth.load_params(eps_star=e)
+    y = synth.random_state(shape, 7 + shape[1])
+    m = oracle.Model(shape, p)
+    yh = m.to_k(y)
+    ref = m.rhs_explicit(yh)
+    dev = torch.from_numpy(yh).to("cuda")
+    with pfg.Simulation(shape, p, "ark4", "fp32bulk") as s:
+        for tx in (8, 16):
+            cfg = s.tuning()
+            cfg[2] = tx
+            cfg[38] = {256: 1, 64: 5, 640: 11}[shape[0]]
+            cfg[40] = 2
+            s.set_tuning(cfg)
+            assert s.tuning()[40] == 2
+            got = s.rhs_explicit(dev).cpu().numpy()
+            err = relerr(got, ref)
+            assert np.all(err <= 2e-5), (tx, err)
+
+
+def test_elastic_form_out_of_range_refused(pfg, params):
+    with pfg.Simulation((64, 8, 8), params, "ark4", "fp32bulk") as s:
+        cfg = s.tuning()
+        cfg[40] = 3
+        with pytest.raises(pfg.PFError):
+            s.set_tuning(cfg)
 
 
 def test_elastic_plan_of_wrong_length_refused(pfg, params):
