@@ -1803,13 +1803,21 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
             }
         // elastic pass with the fused stage, with every stage over the three
         // fields, or as a three-CTA cluster (FP32)
-        if (c->ph.elastic && !c->inhom)
-            for (int v : {0, 1, 2}) {
-                if (v == 2 && !c->fp32) continue;
+        if (c->ph.elastic && !c->inhom) {
+            for (int v : {0, 1}) {
                 std::memcpy(cfg, best, sizeof cfg);
                 cfg[40] = v;
                 trial(cfg);
             }
+            // the cluster form with its own tile widths (16 or 8 columns)
+            if (c->fp32)
+                for (int tx : {16, 8}) {
+                    std::memcpy(cfg, best, sizeof cfg);
+                    cfg[40] = 2;
+                    cfg[2] = tx;
+                    trial(cfg);
+                }
+        }
         // compiled plans of length nz for the fused elastic pass, or none (-1)
         for (int pid = -1; pid <= compiled_plan_count(); ++pid) {
             if (pid > 0 && compiled_plan_len(pid) != c->g.nz) continue;
