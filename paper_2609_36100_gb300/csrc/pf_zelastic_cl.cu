@@ -70,30 +70,56 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, elastic_cluster_
         const int hy = g.ny / 2 + 1;
         const long long tn = (long long)(g.nz / 2 + 1) * hy * g.nxh;
         const long long trow = (long long)(ky <= g.ny / 2 ? ky : g.ny - ky) * g.nxh + kx0;
-        for (int e = f * NT + (int)threadIdx.x; e < E; e += 3 * NT) {
-            const int kz = e / TX, col = e - kz * TX;
-            if (col >= ncol) continue;
-            float Bm[3][3];
-            float sc = invN;
-            if (bt) {
-                const long long ti = (long long)(kz <= g.nz / 2 ? kz : g.nz - kz) * hy * g.nxh + trow + col;
-                Bm[0][0] = __ldg(bt + ti);
-                Bm[0][1] = Bm[1][0] = __ldg(bt + tn + ti);
-                Bm[0][2] = Bm[2][0] = __ldg(bt + 2 * tn + ti);
-                Bm[1][1] = __ldg(bt + 3 * tn + ti);
-                Bm[1][2] = Bm[2][1] = __ldg(bt + 4 * tn + ti);
-                Bm[2][2] = __ldg(bt + 5 * tn + ti);
-                sc = 1.f;
-            } else {
-                elastic_kernel<float>(pt, kval<float>(g, 0, kx0 + col), kyv, kval<float>(g, 2, kz), Bm);
+        // two wave numbers per iteration, every load of both issued first
+        // (the reads of the peers' tiles are the long-latency ones); one where
+        // the registers are bounded for two CTAs of 512 or more threads
+        constexpr int CU = NT >= 512 ? 1 : 2;
+        for (int e0 = f * NT + (int)threadIdx.x; e0 < E; e0 += 3 * NT * CU) {
+            T2 h[CU][3];
+            float bv[CU][6];
+            bool ok[CU];
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const int e = e0 + u * 3 * NT;
+                const int kz = e / TX, col = e - kz * TX;
+                ok[u] = e < E && col < ncol;
+                if (ok[u]) {
+                    h[u][0] = S0[e];
+                    h[u][1] = S1[e];
+                    h[u][2] = S2[e];
+                    if (bt) {
+                        const long long ti = (long long)(kz <= g.nz / 2 ? kz : g.nz - kz) * hy * g.nxh + trow + col;
+#pragma unroll
+                        for (int m = 0; m < 6; ++m) bv[u][m] = __ldg(bt + m * tn + ti);
+                    }
+                }
             }
-            const T2 a = S0[e], b = S1[e], c = S2[e];
-            S0[e] = T2{(Bm[0][0] * a.x + Bm[0][1] * b.x + Bm[0][2] * c.x) * sc,
-                       (Bm[0][0] * a.y + Bm[0][1] * b.y + Bm[0][2] * c.y) * sc};
-            S1[e] = T2{(Bm[1][0] * a.x + Bm[1][1] * b.x + Bm[1][2] * c.x) * sc,
-                       (Bm[1][0] * a.y + Bm[1][1] * b.y + Bm[1][2] * c.y) * sc};
-            S2[e] = T2{(Bm[2][0] * a.x + Bm[2][1] * b.x + Bm[2][2] * c.x) * sc,
-                       (Bm[2][0] * a.y + Bm[2][1] * b.y + Bm[2][2] * c.y) * sc};
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                if (!ok[u]) continue;
+                const int e = e0 + u * 3 * NT;
+                float Bm[3][3];
+                float sc = invN;
+                if (bt) {
+                    Bm[0][0] = bv[u][0];
+                    Bm[0][1] = Bm[1][0] = bv[u][1];
+                    Bm[0][2] = Bm[2][0] = bv[u][2];
+                    Bm[1][1] = bv[u][3];
+                    Bm[1][2] = Bm[2][1] = bv[u][4];
+                    Bm[2][2] = bv[u][5];
+                    sc = 1.f;
+                } else {
+                    const int kz = e / TX, col = e - kz * TX;
+                    elastic_kernel<float>(pt, kval<float>(g, 0, kx0 + col), kyv, kval<float>(g, 2, kz), Bm);
+                }
+                const T2 a = h[u][0], b = h[u][1], c = h[u][2];
+                S0[e] = T2{(Bm[0][0] * a.x + Bm[0][1] * b.x + Bm[0][2] * c.x) * sc,
+                           (Bm[0][0] * a.y + Bm[0][1] * b.y + Bm[0][2] * c.y) * sc};
+                S1[e] = T2{(Bm[1][0] * a.x + Bm[1][1] * b.x + Bm[1][2] * c.x) * sc,
+                           (Bm[1][0] * a.y + Bm[1][1] * b.y + Bm[1][2] * c.y) * sc};
+                S2[e] = T2{(Bm[2][0] * a.x + Bm[2][1] * b.x + Bm[2][2] * c.x) * sc,
+                           (Bm[2][0] * a.y + Bm[2][1] * b.y + Bm[2][2] * c.y) * sc};
+            }
         }
     }
     cl.sync();  // every wave number contracted: no CTA reads a peer's tile after this
