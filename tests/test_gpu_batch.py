@@ -143,3 +143,38 @@ def test_batch_device_looped_equals_polled(pfg, params, prec):
     for a, b, sa, sb in zip(states_l, states_p, stats_l, stats_p):
         assert np.array_equal(a, b)
         assert sa["steps_accepted"] == sb["steps_accepted"] and sa["steps_rejected"] == sb["steps_rejected"]
+
+
+def test_batch_with_cluster_elastic_pass(pfg, params):
+    """FP32-bulk members whose z length has a compiled plan, each running the
+    elastic pass as a three-CTA cluster (tuning slot 40 = 2): batched, with
+    members that finish early skipping their rounds (whole clusters return
+    together), they give what each member's own pf_advance gives."""
+    specs = [((64, 8, 12), 0), ((96, 10, 16), 1), ((64, 6, 20), 2)]
+    t_final = 6.0
+
+    def prepared(shape, k):
+        s = pfg.Simulation(shape, params, "ark4", "fp32bulk")
+        cfg = s.tuning()
+        cfg[38] = {64: 5, 96: 8}[shape[0]]  # compiled plans of length nz
+        cfg[40] = 2
+        s.set_tuning(cfg)
+        assert s.tuning()[40] == 2
+        s.set_state(synth.random_state(shape, 70 + k, phi_scale=0.9))
+        return s
+
+    singles = []
+    for shape, k in specs:
+        with prepared(shape, k) as s:
+            st = s.advance(t_final, 1e-4, 1e-8)
+            singles.append((s.state_hat().cpu().numpy(), st))
+    sims = [prepared(shape, k) for shape, k in specs]
+    try:
+        stats = pfg.batch_advance(sims, t_final, 1e-4, 1e-8)
+        for s, st, (ref, st1) in zip(sims, stats, singles):
+            assert st["steps_accepted"] == st1["steps_accepted"]
+            assert st["steps_rejected"] == st1["steps_rejected"]
+            assert relerr(s.state_hat().cpu().numpy(), ref) <= 1e-5
+    finally:
+        for s in sims:
+            s.close()
