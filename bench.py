@@ -68,9 +68,10 @@ def parse():
     ap.add_argument("--surrogate", type=int, default=24, help="training trajectories of the surrogate measurement (0: skip)")
     ap.add_argument("--sweep", action="store_true", help="add the work-precision sweep of the two-particle test")
     ap.add_argument("--hc", type=int, default=128, help="side of the phase-dependent-stiffness leg (0: skip)")
-    ap.add_argument("--elastic-form", type=int, default=-1,
+    ap.add_argument("--elastic-form", default="-1",
                     help="after autotuning, run this form of the elastic pass in the FP32-bulk main leg "
-                         "(0 fused stage, 1 stages over three fields, 2 three-CTA cluster; -1: the autotuner's)")
+                         "(0 fused stage, 1 stages over three fields, 2 three-CTA cluster; -1: the autotuner's), "
+                         "optionally with its tile width as FORM:COLUMNS")
     return ap.parse_args()
 
 
@@ -189,9 +190,12 @@ def run_ours(args, rank, world, dist):
         sim = pfg.Simulation((n, n, n), p, "ark4", prec)
         sim.set_state(y0_dev)
         tuning = sim.autotune(reps=2) if tune else None
-        if tune and prec == "fp32bulk" and args.elastic_form >= 0:
+        form, _, width = str(args.elastic_form).partition(":")
+        if tune and prec == "fp32bulk" and int(form) >= 0:
             cfg = sim.tuning()
-            cfg[40] = args.elastic_form
+            cfg[40] = int(form)
+            if width:
+                cfg[2] = int(width)
             sim.set_tuning(cfg)
             tuning = dict(tuning, cfg=sim.tuning(), elastic_form_forced=args.elastic_form)
         return sim, tuning, sim.state_hat()
