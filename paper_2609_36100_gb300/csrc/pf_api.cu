@@ -1804,11 +1804,15 @@ int pf_autotune(pf_ctx* c, int reps, double* ms_before, double* ms_after) {
         // elastic pass with the fused stage, with every stage over the three
         // fields, or as a three-CTA cluster (FP32)
         if (c->ph.elastic && !c->inhom) {
-            for (int v : {0, 1}) {
-                std::memcpy(cfg, best, sizeof cfg);
-                cfg[40] = v;
-                trial(cfg);
-            }
+            // each form at several tile widths: the best width depends on the
+            // form (registers and shared memory per column differ)
+            for (int v : {0, 1})
+                for (int tx : {16, 8, 4}) {
+                    std::memcpy(cfg, best, sizeof cfg);
+                    cfg[40] = v;
+                    cfg[2] = tx;
+                    trial(cfg);
+                }
             // the cluster form with its own tile widths (16 or 8 columns)
             if (c->fp32)
                 for (int tx : {16, 8}) {
